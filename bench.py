@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Throughput of the DGTD stage path: DOF-updates/s of the weight-adjusted
+PML nodal DGTD solver on a synthetic jittered-tetrahedron cube.
+
+One bench step = one full low-storage Runge-Kutta time step (five stages of
+the fused right-hand-side + update kernels for both element classes, probe
+readout) over the whole workload.  Default workload: 40^3 x 6 = 384,000
+jittered tets (+-0.2 h, seed 1), N = 4 (35 nodes), cubic PML (sigma_max 40,
+shell 0.2), one dipole and eight probes, FP32 state and arithmetic.
+
+DOF-updates per step = N_p * (6 K + 6 K_pml) * n_batch (all 12 fields of PML
+elements, 6 elsewhere), the counting used for the paper's Table I.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank advances its own replica of the workload (replicas
+only: the excitations are independent, there is no exchange between ranks).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (no measured figure available)
+
+
+def describe(w):
+    return (f"{w.name}: {w.n_hex}^3x6={w.K} jittered tets (+-{w.jitter}h, seed {w.mesh_seed}), "
+            f"N={w.N}, cubic PML sigma_max={w.pml.sigma_max} shell {w.pml.L} "
+            f"(u0={w.pml.u0}), kappa_max={w.pml.kappa_max}, {len(w.sources)} dipole(s), "
+            f"{len(w.probes)} probes, {w.n_batch} excitation(s)")
+
+
+def algorithmic_costs(N, Np, Nfp, Nq, rs, kappa):
+    """Per element per stage launch: (bytes, flops) of the non-PML and the PML
+    stage kernel (minimum traffic: each field read and written once)."""
+    meta = 9 * 8 + 3 * rs + 4 * 4 + 4          # metric (double), material, nbr, code
+    b_std = 4 * rs * 6 * Np + meta              # read q, res; write res, q
+    b_pml = 4 * rs * 12 * Np + meta + (6 if kappa else 3) * Nq * rs
+    f_std = 36 * Np * Np + 90 * Np + 240 * Nfp + 48 * Np * Nfp + 4 * 6 * Np
+    f_pml = f_std + 48 * Nq * Np + 24 * Nq + 12 * Np + 4 * 6 * Np
+    if kappa:
+        f_pml += 24 * Nq * Np + 6 * Nq
+    return dict(bytes_std=b_std, bytes_pml=b_pml, flops_std=f_std, flops_pml=f_pml)
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4)
+                          if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+def setup_solver(w, precision, stream, device):
+    from paper_2006_02551_gb300 import Solver
+    from synthetic import cube_tet_mesh
+    v, e = cube_tet_mesh(w.n_hex, w.jitter, w.mesh_seed)
+    s = Solver(w.N, precision, n_batch=w.n_batch, device=device, stream=stream)
+    s.set_mesh(v, e)
+    s.set_pml(w.pml)
+    s.set_sources(list(w.sources))
+    s.set_probes(list(w.probes))
+    s.set_state(None, 0.0)
+    return s
+
+
+def oracle_rate(w, n_hex, steps, warmup=1):
+    """The FP64 oracle (as it stands) on a smaller cube of the same recipe:
+    DOF-updates/s over `steps` LSERK steps after `warmup` steps."""
+    from dataclasses import replace
+    from oracle.solver import Simulation
+    from synthetic import cube_tet_mesh
+    ws = replace(w, n_hex=n_hex)
+    v, e = cube_tet_mesh(ws.n_hex, ws.jitter, ws.mesh_seed)
+    sim = Simulation(ws.N, v, e, profile=ws.pml, sources=ws.sources, probes=ws.probes,
+                     n_batch=ws.n_batch)
+    dt = sim.stable_dt(1.0)
+    st = sim.zero_state()
+    t = 0.0
+    if warmup:
+        st, t, _, _ = sim.run(st, warmup, dt, t=t)
+    # the oracle carries the PML fields on every element; count DOFs the same
+    # way as the library (12 fields on PML-class elements, 6 elsewhere)
+    vv = v[e]
+    pml = np.any(np.abs(vv) > ws.pml.u0, axis=(1, 2))
+    dofs = sim.Np * (6 * ws.K + 6 * int(pml.sum())) * ws.n_batch
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        st, t, _, _ = sim.run(st, 1, dt, t=t)
+        times.append(time.perf_counter() - t0)
+    return dofs, times, ws
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args, w):
+    dofs, times, ws = oracle_rate(w, args.ref_hex, args.steps, warmup=args.warmup)
+    tot = sum(times)
+    value = dofs * len(times) / tot
+    sample = (f"FP64 numpy oracle on {ws.n_hex}^3x6={ws.K} tets of the same recipe "
+              f"(N={ws.N}, same PML, sources, probes), {len(times)} steps after "
+              f"{args.warmup} warm-up steps")
+    line = {"impl": "reference", "metric": args.metric, "value": value,
+            "unit": "DOF-updates/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": describe(w), "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "DOF-updates/s", "cores": cpu_cores(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cube40_n4")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
+    ap.add_argument("--ref-hex", type=int, default=4,
+                    help="cube size of the oracle sample for --impl reference")
+    ap.add_argument("--cpu-hex", type=int, default=10,
+                    help="cube size of the oracle sample for the cpu_baseline entry")
+    args = ap.parse_args()
+    args.metric = "DOF-updates/s (WADG-PML DGTD, N=4), mixed-precision vs FP64 at stated L2 error"
+    if args.warmup < 3:
+        args.warmup = 3
+
+    from synthetic import workload
+    w = workload(args.workload)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, w)
+        return
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2006_02551_gb300 import build as _b
+    if rank == 0 or world == 1:
+        _b.build()
+    if dist:
+        dist.barrier()
+    stream = torch.cuda.Stream(device=local)
+    sh = stream.cuda_stream
+
+    s = setup_solver(w, args.precision, sh, local)
+    info = s.info()
+    K, K1, Np, Nq = info["K"], info["K_pml"], info["Np"], info["Nq"]
+    N = w.N
+    Nfp = (N + 1) * (N + 2) // 2
+    dofs = Np * (6 * K + 6 * K1) * w.n_batch
+    dt = s.stable_dt(1.0)
+    rs = 8 if args.precision == "fp64" else 4
+
+    # warm-up (graph capture happens here)
+    s.run_steps(args.warmup, dt, record=False)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    s.run_steps(args.steps, dt, record=False)
+    ev1.record(stream)
+    ev1.synchronize()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        tt = torch.tensor([ms], device=f"cuda:{local}")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * dofs * args.steps / (ms * 1e-3)
+
+    # per-kernel durations (CUDA events on the library stream, eager launches)
+    kms = s.profile_stage(50, dt)
+    cost = algorithmic_costs(N, Np, Nfp, Nq, rs, w.pml.kappa_max != 1.0)
+    per = {"std": (kms[0], cost["bytes_std"] * (K - K1) * w.n_batch,
+                   cost["flops_std"] * (K - K1) * w.n_batch),
+           "pml": (kms[1], cost["bytes_pml"] * K1 * w.n_batch,
+                   cost["flops_pml"] * K1 * w.n_batch)}
+    dom = max(per, key=lambda k: per[k][0])
+    d_ms, d_bytes, d_flops = per[dom]
+    if args.precision == "fp64":
+        peak = FP64_PEAK_TFLOPS
+        peak_note = "nominal GB300 FP64 (1.25 TFLOP/s)"
+    else:
+        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        peak_note = "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
+    achieved = d_flops / (d_ms * 1e-3) / 1e12
+    hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": f"stage_kernel<{dom}>",
+                "peak_source": peak_note,
+                "hbm": {"achieved_gbs": d_bytes / (d_ms * 1e-3) / 1e9, "peak_gbs": hbm,
+                        "frac": d_bytes / (d_ms * 1e-3) / 1e9 / hbm},
+                "kernel_ms": {"std": kms[0], "pml": kms[1]},
+                "bytes_per_launch": d_bytes, "flops_per_launch": d_flops}
+
+    # end to end through the public API with host buffers
+    rec_bytes = len(w.probes) * 6 * w.n_batch * 8
+    q_host = np.zeros((w.n_batch, K, 12, Np))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.set_state(q_host, 0.0)
+    s.run_steps(args.steps, dt, record=True)
+    t1 = time.perf_counter()
+    e2e_val = world * dofs * args.steps / (t1 - t0)
+    h2d = (w.n_batch * (K + K1) * 6 * Np * rs) / args.steps
+    e2e = {"value": e2e_val, "unit": "DOF-updates/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": rec_bytes}
+
+    mem = s.memory_report()
+    out_extra = {}
+    # accuracy of this precision against the FP64 path, and the FP64 rate
+    if args.precision != "fp64" and not args.no_fp64 and rank == 0:
+        nst = 20
+        s.set_state(None, 0.0)
+        s.run_steps(nst, dt, record=False)
+        q32, _ = s.get_state()
+        s.close()
+        s64 = setup_solver(w, "fp64", sh, local)
+        s64.run_steps(3, dt, record=False)
+        s64.set_state(None, 0.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s64.run_steps(nst, dt, record=False)
+        e1.record(stream)
+        e1.synchronize()
+        q64, _ = s64.get_state()
+        ms64 = e0.elapsed_time(e1) / nst
+        s64.close()
+        sel = (slice(None), slice(None), slice(0, 6))
+        l2 = float(np.linalg.norm(q32[sel] - q64[sel]) / np.linalg.norm(q64[sel]))
+        out_extra["accuracy"] = {"l2_rel_vs_fp64": l2, "fields": "E,H", "steps": nst}
+        out_extra["fp64"] = {"value": dofs / (ms64 * 1e-3), "ms_per_step": ms64}
+    else:
+        s.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cdofs, ctimes, ws = oracle_rate(w, args.cpu_hex, 2, warmup=1)
+        cpu = {"value": cdofs * len(ctimes) / sum(ctimes), "unit": "DOF-updates/s",
+               "cores": cpu_cores(), "kind": "oracle",
+               "sample": (f"FP64 numpy oracle on {ws.n_hex}^3x6={ws.K} tets of the same "
+                          f"recipe (N={ws.N}, same PML/source/probes), 2 steps after 1 "
+                          f"warm-up step")}
+
+    launches_per_step = 5 * (1 + (1 if K1 else 0)) + (1 if len(w.probes) else 0) + 1
+    if rank == 0:
+        line = {"metric": args.metric, "value": value, "unit": "DOF-updates/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32" if rs == 4 else "f64",
+                "data": "synthetic",
+                "config": {"workload": describe(w), "K": K, "K_pml": K1, "N": N, "Np": Np,
+                           "Nq": Nq, "dofs_per_step": dofs, "precision": args.precision,
+                           "l2_flush": f"inputs larger than L2 (state {mem['state'] / 1e9:.2f} GB)",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": launches_per_step * args.steps + 1,
+                "memory": {"state_bytes": mem["state"], "pml_coeff_bytes": mem["pml_coeff"],
+                           "pml_coeff_bytes_per_pml_element": mem["pml_coeff"] / max(K1, 1),
+                           "stored_scheme_bytes_per_pml_element": 15 * Np * Np * rs,
+                           "operator_bytes": mem["operators"],
+                           "geometry_bytes": mem["geometry"]}}
+        line.update(out_extra)
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,201 @@
+/*
+ * wadg.h -- C ABI of the GB300 library for nodal discontinuous Galerkin
+ * time-domain (DGTD) Maxwell solves on tetrahedra with a stretched-coordinate
+ * perfectly matched layer (SC-PML) whose conductivity varies inside elements,
+ * applied through the weight-adjusted approximation (WAA) of the PML mass
+ * matrices (Chen, Ozakin, Ahmed, Bagci: "A memory-efficient implementation
+ * of perfectly matched layer with smoothly-varying coefficients in
+ * discontinuous Galerkin time-domain method", Section II).
+ *
+ * Conventions (all entry points):
+ *  - Every call returns a wadg_status; nothing aborts or exits.  On failure
+ *    wadg_last_error(ctx) holds a one-line message until the next call.
+ *  - Caller arrays are borrowed for the duration of the call and copied;
+ *    the library keeps no caller pointer.
+ *  - All device work is issued on the CUDA stream given to wadg_create (the
+ *    legacy default stream when NULL).  Calls that return host data
+ *    synchronise that stream first.
+ *  - Element ids in and out of the library are the caller's (the row of
+ *    etov); the internal reordering (PML class, then space-filling-curve
+ *    order) is hidden.
+ *  - Within an element, nodal values follow the equispaced node order:
+ *    node (i,j,k), i+j+k <= N, at reference coordinates
+ *    (r,s,t) = (-1 + 2i/N, -1 + 2j/N, -1 + 2k/N), enumerated with k
+ *    outermost, then j, then i; the reference tetrahedron has vertices
+ *    v1=(-1,-1,-1), v2=(1,-1,-1), v3=(-1,1,-1), v4=(-1,-1,1) mapped to the
+ *    four vertices of the element in etov order.
+ *  - Units are normalised: the background has eps = mu = 1 (so c0 = 1) and
+ *    eps0 of the PML profile is a parameter (1 in normalised units).
+ */
+#ifndef WADG_H
+#define WADG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wadg_ctx wadg_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  WADG_OK = 0,
+  WADG_EINVAL = 1,       /* bad argument, malformed mesh, unsupported size */
+  WADG_ENOMEM = 2,       /* a device or host allocation failed */
+  WADG_ECUDA = 3,        /* a CUDA runtime call failed */
+  WADG_ESTATE = 4,       /* call out of order (e.g. stepping before set_mesh) */
+  WADG_ENOTFOUND = 5,    /* a source or probe point lies outside the mesh */
+  WADG_ETIMEOUT = 6,     /* a bounded device-side wait gave up */
+  WADG_ENONFINITE = 7,   /* the state holds NaN or Inf after stepping */
+  WADG_EUNSUPPORTED = 8  /* valid request that this build does not provide */
+} wadg_status;
+
+/* Arithmetic of the stage kernels.  FP64: fields, operators and coefficients
+ * in double.  FP32: fields, operators, coefficient samples in float; the
+ * geometric factors stay double on the device and the source waveform, the
+ * coefficient sampling and the objective sums are evaluated in double. */
+typedef enum { WADG_FP64 = 0, WADG_FP32 = 1, WADG_TF32 = 2, WADG_BF16 = 3 } wadg_precision;
+
+/* PML implementation.  WAA: eqs. 26-29 (the paper's method).  STORED: the
+ * per-element mass matrices of eqs. 10-15 (reserved).  EC: element-constant
+ * coefficients (reserved). */
+typedef enum { WADG_PML_WAA = 0, WADG_PML_STORED = 1, WADG_PML_EC = 2 } wadg_pml_scheme;
+
+/* Stretching profiles of Section III, per axis u in {x, y, z}:
+ *   d = max(0, (|u| - u0[u]) / L[u]),
+ *   sigma_u = sigma_max[u] * d^p_sigma[u],
+ *   kappa_u = 1 + (kappa_max[u] - 1) * d^p_sigma[u],
+ * entering s_u = kappa_u + sigma_u / (j w eps0) (eq. 4) and the CPML tensors
+ * a, b, c, d, kappa of eq. 9. */
+typedef struct {
+  double u0[3], L[3], sigma_max[3], p_sigma[3], kappa_max[3];
+  double eps0;
+} wadg_pml_profile;
+
+/* Point electric dipole of moment amplitude * G(t) along unit vector dir at
+ * point x, G(t) = exp(-(t - t0)^2 / (4 width^2)) (Section III's base-band
+ * Gaussian pulse, with the minus sign the printed formula lacks); it drives
+ * the current J = amplitude * G'(t) * dir * delta(x - x_s) in excitation
+ * `batch` (0 <= batch < n_batch). */
+typedef struct {
+  double x[3], dir[3], t0, width, amplitude;
+  int32_t batch;
+} wadg_dipole;
+
+/* Create a context for polynomial order N (1..5) with n_batch independent
+ * excitations advanced together on CUDA device `device`, issuing work on
+ * `cuda_stream` (a cudaStream_t, may be NULL).  EINVAL on bad N, precision
+ * or n_batch; ECUDA if the device cannot be used. */
+wadg_status wadg_create(int N, wadg_precision prec, int32_t n_batch, int device,
+                        void* cuda_stream, wadg_ctx** out);
+
+/* Release every host and device resource of ctx (NULL is accepted). */
+wadg_status wadg_destroy(wadg_ctx* ctx);
+
+/* Mesh: nv vertices vxyz[nv][3] (double) and K tetrahedra etov[K][4]
+ * (int64, 0-based).  The library computes in double the affine maps, J_k,
+ * the metric terms, normals and surface Jacobians (Section II.A: straight-
+ * sided elements, M_k = J_k M) and the face connectivity; faces with no
+ * neighbour carry the perfect-electric-conductor condition.  EINVAL for an
+ * index out of range, a non-positive Jacobian, or a face shared by more than
+ * two elements.  Resets materials, PML, sources, probes and the state. */
+wadg_status wadg_set_mesh(wadg_ctx* ctx, int64_t nv, const double* vxyz, int64_t K,
+                          const int64_t* etov);
+
+/* Per-element relative permittivity and permeability eps_r[K], mu_r[K]
+ * (caller element order, must be > 0); NULL means 1.  Enters the update
+ * equations as eps_k, mu_k (eqs. 10, 11) and the upwind flux impedances. */
+wadg_status wadg_set_materials(wadg_ctx* ctx, const double* eps_r, const double* mu_r);
+
+/* PML profile (eq. 4 with the profiles of Section III).  An element belongs
+ * to the PML class when any of its vertices has |u| > u0[u] on an axis whose
+ * profile is active (sigma_max > 0 or kappa_max != 1); only PML elements
+ * carry P^E, P^H.  The coefficients are sampled in double at the volume
+ * quadrature nodes of each PML element (eq. 20 samples alpha_k(r_q)) and
+ * stored per element as sigma_u (and kappa_u when kappa_max != 1).  Pass
+ * NULL to remove the PML.  Only WADG_PML_WAA is implemented (EUNSUPPORTED
+ * otherwise).  Resets the state and re-maps sources and probes. */
+wadg_status wadg_set_pml_profile(wadg_ctx* ctx, const wadg_pml_profile* prof,
+                                 wadg_pml_scheme scheme);
+
+/* n point dipoles (copied).  ENOTFOUND if a point lies outside the mesh,
+ * EINVAL for a batch index out of range or a non-positive width.  A point on
+ * a shared face or vertex belongs to the lowest caller element id whose
+ * barycentric coordinates are all >= -1e-12. */
+wadg_status wadg_set_sources(wadg_ctx* ctx, int32_t n, const wadg_dipole* src);
+
+/* n probe points xyz[n][3]; E and H there are recorded after every full
+ * time step by wadg_run_steps.  ENOTFOUND if a point is outside the mesh. */
+wadg_status wadg_set_probes(wadg_ctx* ctx, int32_t n, const double* xyz);
+
+/* State exchange (host memory, double): q[n_batch][K][12][Np] with the 12
+ * components (Ex,Ey,Ez,Hx,Hy,Hz,PEx,PEy,PEz,PHx,PHy,PHz), caller element
+ * order.  set_state ignores the P components of non-PML elements (they are
+ * not stored) and sets the solution time to t; get_state writes zeros there.
+ * q == NULL in set_state zeros the state.  set_state also clears the probe
+ * objective. */
+wadg_status wadg_set_state(wadg_ctx* ctx, const double* q, double t);
+wadg_status wadg_get_state(wadg_ctx* ctx, double* q, double* t);
+
+/* One stage i (0..4) of the five-stage fourth-order low-storage Runge-Kutta
+ * scheme: res <- A_i res + dt * f(q, t + c_i dt); q <- q + B_i res, where f
+ * is the semi-discrete right-hand side (the curl with upwind flux of the
+ * equation after eq. 15, and eqs. 26-29 in PML elements).  Does not change
+ * the solution time held by the context. */
+wadg_status wadg_rk_stage(wadg_ctx* ctx, int stage, double t, double dt);
+
+/* Advance every excitation by nsteps full steps of size dt from the current
+ * solution time.  If probe_out is not NULL it receives
+ * probe_out[nsteps][nprobe][6][n_batch] (double; Ex..Hz after each step).
+ * The FP64 objective sum over probes and steps of |E|^2 accumulates per
+ * excitation (wadg_objective).  ENONFINITE if the state became non-finite. */
+wadg_status wadg_run_steps(wadg_ctx* ctx, int64_t nsteps, double dt, double* probe_out);
+
+/* Measurement aid: run `reps` eager Runge-Kutta stages (stage index cycling
+ * 0..4, time = current solution time) and return in ms_out[2] the average
+ * device duration of one launch of the non-PML stage kernel (ms_out[0]) and
+ * of the PML stage kernel (ms_out[1]), timed with CUDA events on the
+ * context's stream.  Advances the state like wadg_rk_stage. */
+wadg_status wadg_profile_stage(wadg_ctx* ctx, int reps, double dt, double* ms_out);
+
+/* Largest step for the given CFL number:
+ * dt = cfl * 2 / ((N+1)^2 * max_{k,f} Fscale_{k,f}), Fscale = sJ/J. */
+wadg_status wadg_stable_dt(const wadg_ctx* ctx, double cfl, double* dt_out);
+
+/* Objective J_b = sum over probes and recorded steps of |E|^2 for each
+ * excitation b: J_out[n_batch]. */
+wadg_status wadg_objective(wadg_ctx* ctx, double* J_out);
+
+/* Device bytes held for the field state (q, res and the P fields), for the
+ * per-element PML coefficient samples, for the reference operators, and for
+ * the per-element geometry and connectivity.  Any pointer may be NULL. */
+wadg_status wadg_memory_report(const wadg_ctx* ctx, size_t* bytes_state,
+                               size_t* bytes_pml_coeff, size_t* bytes_operators,
+                               size_t* bytes_geometry);
+
+/* Mesh sizes after set_mesh / set_pml_profile: elements, PML elements,
+ * nodes per element, volume quadrature nodes per element. */
+wadg_status wadg_mesh_info(const wadg_ctx* ctx, int64_t* K, int64_t* K_pml, int32_t* Np,
+                           int32_t* Nq);
+
+/* Block until all work issued by ctx has finished. */
+wadg_status wadg_synchronize(wadg_ctx* ctx);
+
+/* Reference-element operator of order N (host only, no device needed), for
+ * checking the library's set-up against an independent construction.
+ * which: 0 Dr, 1 Ds, 2 Dt ([Np][Np]), 3 LIFT ([Np][4 Nfp]), 4 V_q ([Nq][Np]),
+ * 5 P_q ([Np][Nq]), 6 quadrature nodes and weights ([Nq][4] = r,s,t,w),
+ * 7 M^{-1} ([Np][Np]).  `cap` is the capacity of out in doubles; *n_out
+ * receives the count.  EINVAL for a bad N or which, or a too small cap. */
+wadg_status wadg_reference_operator(int N, int which, double* out, int64_t cap,
+                                    int64_t* n_out);
+
+/* Message of the last failed call on ctx (or of the last failed
+ * wadg_create / wadg_reference_operator when ctx is NULL). */
+const char* wadg_last_error(const wadg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WADG_H */

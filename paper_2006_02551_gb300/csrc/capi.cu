@@ -1,0 +1,1031 @@
+// C ABI: context, host set-up (FP64 geometry, face connectivity, element
+// classing and ordering), device uploads and the stepping loop.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/wadg.h"
+#include "kernels.cuh"
+#include "refelem.hpp"
+
+using namespace wadg;
+
+namespace {
+thread_local std::string g_err;
+
+// LSERK(5,4) coefficients (Carpenter & Kennedy); the stage times are the
+// times at which each stage samples the right-hand side, obtained by running
+// the recursion on y' = 1.
+const double kRkA[5] = {0.0, -567301805773.0 / 1357537059087.0,
+                        -2404267990393.0 / 2016746695238.0,
+                        -3550918686646.0 / 2091501179385.0,
+                        -1275806237668.0 / 842570457699.0};
+const double kRkB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                        1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                        2277821191437.0 / 14882151754819.0};
+struct RkC {
+  double c[5];
+  RkC() {
+    double y = 0.0, res = 0.0;
+    for (int i = 0; i < 5; ++i) {
+      c[i] = y;
+      res = kRkA[i] * res + 1.0;
+      y += kRkB[i] * res;
+    }
+  }
+};
+const RkC kRkC;
+
+struct DevPtr {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct wadg_ctx {
+  int N = 0;
+  wadg_precision prec = WADG_FP64;
+  int nb = 1;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  RefOps ref;
+  size_t rs = 8;  // bytes per Real
+
+  // user-order host mesh data
+  bool has_mesh = false;
+  int64_t K = 0, nv = 0;
+  std::vector<double> vxyz;
+  std::vector<int64_t> etov;
+  std::vector<double> eps_r, mu_r;
+  std::vector<int64_t> nbr_u;   // [K][4] neighbour (user id) or -1
+  std::vector<int> code_u;      // [K][4] neighbour face*6 + rotation
+  std::vector<double> metric_u; // [K][9]
+  std::vector<double> J_u;
+  double fscale_max = 0.0;
+
+  bool has_prof = false;
+  wadg_pml_profile prof{};
+  bool kappa = false;
+
+  std::vector<int64_t> perm, iperm;  // internal -> user, user -> internal
+  int64_t K0 = 0, K1 = 0;
+
+  // device
+  DevPtr q[2], rq, p, rp, geo, mat, nbr, code, sig, kap, ops, tabs, verts;
+  DevPtr src, srcw, pr_elem, pr_ell, pr_out, obj, tdev, stepdev, flag;
+  int cur = 0;
+  int nsrc = 0, nprobe = 0;
+  std::vector<wadg_dipole> src_user;
+  std::vector<double> probe_user;
+  double t = 0.0;
+
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  double graph_dt = 0.0;
+  bool graph_valid = false;
+};
+
+namespace {
+
+wadg_status fail(wadg_ctx* c, wadg_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf; else g_err = buf;
+  return s;
+}
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? WADG_ENOMEM : WADG_ECUDA,      \
+                  "%s: %s", #call, cudaGetErrorString(e_));                             \
+  } while (0)
+
+void dfree(DevPtr& d) {
+  if (d.p) cudaFree(d.p);
+  d.p = nullptr;
+  d.bytes = 0;
+}
+
+cudaError_t dalloc(DevPtr& d, size_t bytes) {
+  dfree(d);
+  if (bytes == 0) return cudaSuccess;
+  cudaError_t e = cudaMalloc(&d.p, bytes);
+  if (e == cudaSuccess) d.bytes = bytes;
+  else d.p = nullptr;
+  return e;
+}
+
+void invalidate_graphs(wadg_ctx* c) {
+  for (auto& g : c->graph)
+    if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+  c->graph_valid = false;
+}
+
+// barycentric coordinates of x in user element k (lambda[4])
+void barycentric(const wadg_ctx* c, int64_t k, const double* x, double* lam) {
+  const double* v[4];
+  for (int a = 0; a < 4; ++a) v[a] = &c->vxyz[3 * c->etov[4 * k + a]];
+  double A[3][3], bvec[3];
+  for (int d = 0; d < 3; ++d) {
+    A[d][0] = v[1][d] - v[0][d];
+    A[d][1] = v[2][d] - v[0][d];
+    A[d][2] = v[3][d] - v[0][d];
+    bvec[d] = x[d] - v[0][d];
+  }
+  double det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
+               A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+               A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+  double sol[3];
+  for (int j = 0; j < 3; ++j) {  // Cramer's rule
+    double M[3][3];
+    for (int r = 0; r < 3; ++r)
+      for (int cc = 0; cc < 3; ++cc) M[r][cc] = (cc == j) ? bvec[r] : A[r][cc];
+    sol[j] = (M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+              M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+              M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0])) / det;
+  }
+  lam[1] = sol[0]; lam[2] = sol[1]; lam[3] = sol[2];
+  lam[0] = 1.0 - sol[0] - sol[1] - sol[2];
+}
+
+int64_t locate(const wadg_ctx* c, const double* x, double* rst) {
+  for (int64_t k = 0; k < c->K; ++k) {
+    double lam[4];
+    barycentric(c, k, x, lam);
+    if (lam[0] >= -1e-12 && lam[1] >= -1e-12 && lam[2] >= -1e-12 && lam[3] >= -1e-12) {
+      rst[0] = -1.0 + 2.0 * lam[1];
+      rst[1] = -1.0 + 2.0 * lam[2];
+      rst[2] = -1.0 + 2.0 * lam[3];
+      return k;
+    }
+  }
+  return -1;
+}
+
+uint64_t spread3(uint64_t x) {  // 21 bits -> every third bit
+  x &= 0x1fffff;
+  x = (x | x << 32) & 0x1f00000000ffffULL;
+  x = (x | x << 16) & 0x1f0000ff0000ffULL;
+  x = (x | x << 8) & 0x100f00f00f00f00fULL;
+  x = (x | x << 4) & 0x10c30c30c30c30c3ULL;
+  x = (x | x << 2) & 0x1249249249249249ULL;
+  return x;
+}
+
+template <typename Real>
+std::vector<Real> cvt(const std::vector<double>& a) {
+  return std::vector<Real>(a.begin(), a.end());
+}
+
+template <typename Real>
+wadg_status upload_ops(wadg_ctx* ctx) {
+  const RefOps& R = ctx->ref;
+  const int Np = R.Np, Nfp = R.Nfp, Nq = R.Nq, NF = 4 * Nfp;
+  std::vector<double> h;
+  h.reserve(3 * Np * Np + NF * Np + 2 * Np * Nq);
+  for (const std::vector<double>* D : {&R.Dr, &R.Ds, &R.Dt})
+    for (int j = 0; j < Np; ++j)
+      for (int i = 0; i < Np; ++i) h.push_back((*D)[i * Np + j]);
+  for (int fm = 0; fm < NF; ++fm)
+    for (int i = 0; i < Np; ++i) h.push_back(R.LIFT[(size_t)i * NF + fm]);
+  for (int j = 0; j < Np; ++j)
+    for (int q = 0; q < Nq; ++q) h.push_back(R.Vq[(size_t)q * Np + j]);
+  for (int q = 0; q < Nq; ++q)
+    for (int i = 0; i < Np; ++i) h.push_back(R.Pq[(size_t)i * Nq + q]);
+  std::vector<Real> hr = cvt<Real>(h);
+  CK(dalloc(ctx->ops, hr.size() * sizeof(Real)));
+  CK(cudaMemcpy(ctx->ops.p, hr.data(), hr.size() * sizeof(Real), cudaMemcpyHostToDevice));
+  std::vector<unsigned char> t(NF + 4 * 24 * Nfp);
+  for (int i = 0; i < NF; ++i) t[i] = (unsigned char)R.Fmask[i];
+  for (int i = 0; i < 4 * 24 * Nfp; ++i) t[NF + i] = (unsigned char)std::max(R.fperm[i], 0);
+  CK(dalloc(ctx->tabs, t.size()));
+  CK(cudaMemcpy(ctx->tabs.p, t.data(), t.size(), cudaMemcpyHostToDevice));
+  return WADG_OK;
+}
+
+template <typename Real>
+wadg_status rebuild_typed(wadg_ctx* ctx) {
+  const int64_t K = ctx->K;
+  const int Np = ctx->ref.Np, Nq = ctx->ref.Nq;
+  invalidate_graphs(ctx);
+  // ---- classing: an element is in the PML when a vertex lies beyond u0 on
+  // an active axis
+  std::vector<char> is_pml(K, 0);
+  if (ctx->has_prof) {
+    for (int64_t k = 0; k < K; ++k)
+      for (int a = 0; a < 4 && !is_pml[k]; ++a)
+        for (int u = 0; u < 3; ++u) {
+          bool active = ctx->prof.sigma_max[u] > 0.0 || ctx->prof.kappa_max[u] != 1.0;
+          double x = ctx->vxyz[3 * ctx->etov[4 * k + a] + u];
+          if (active && std::fabs(x) > ctx->prof.u0[u]) { is_pml[k] = 1; break; }
+        }
+  }
+  // ---- order: class, then Morton code of the centroid
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int64_t i = 0; i < ctx->nv; ++i)
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = std::min(lo[d], ctx->vxyz[3 * i + d]);
+      hi[d] = std::max(hi[d], ctx->vxyz[3 * i + d]);
+    }
+  std::vector<uint64_t> key(K);
+  for (int64_t k = 0; k < K; ++k) {
+    uint64_t m = 0;
+    for (int d = 0; d < 3; ++d) {
+      double cnt = 0.0;
+      for (int a = 0; a < 4; ++a) cnt += 0.25 * ctx->vxyz[3 * ctx->etov[4 * k + a] + d];
+      double s = (hi[d] > lo[d]) ? (cnt - lo[d]) / (hi[d] - lo[d]) : 0.0;
+      uint64_t qd = (uint64_t)std::min(2097151.0, std::max(0.0, s * 2097151.0));
+      m |= spread3(qd) << d;
+    }
+    key[k] = m;
+  }
+  ctx->perm.resize(K);
+  for (int64_t k = 0; k < K; ++k) ctx->perm[k] = k;
+  std::stable_sort(ctx->perm.begin(), ctx->perm.end(), [&](int64_t a, int64_t b) {
+    if (is_pml[a] != is_pml[b]) return is_pml[a] < is_pml[b];
+    return key[a] < key[b];
+  });
+  ctx->iperm.resize(K);
+  for (int64_t e = 0; e < K; ++e) ctx->iperm[ctx->perm[e]] = e;
+  ctx->K1 = 0;
+  for (int64_t k = 0; k < K; ++k) ctx->K1 += is_pml[k];
+  ctx->K0 = K - ctx->K1;
+  // ---- per-element arrays in internal order
+  std::vector<double> geo(K * 9), verts(K * 12);
+  std::vector<Real> mat(K * 3);
+  std::vector<int> nbr(K * 4);
+  std::vector<unsigned char> code(K * 4);
+  for (int64_t e = 0; e < K; ++e) {
+    const int64_t k = ctx->perm[e];
+    for (int i = 0; i < 9; ++i) geo[e * 9 + i] = ctx->metric_u[k * 9 + i];
+    for (int a = 0; a < 4; ++a)
+      for (int d = 0; d < 3; ++d) verts[e * 12 + a * 3 + d] = ctx->vxyz[3 * ctx->etov[4 * k + a] + d];
+    double er = ctx->eps_r.empty() ? 1.0 : ctx->eps_r[k];
+    double mr = ctx->mu_r.empty() ? 1.0 : ctx->mu_r[k];
+    mat[e * 3 + 0] = (Real)(1.0 / er);
+    mat[e * 3 + 1] = (Real)(1.0 / mr);
+    mat[e * 3 + 2] = (Real)std::sqrt(mr / er);
+    for (int f = 0; f < 4; ++f) {
+      int64_t nk = ctx->nbr_u[k * 4 + f];
+      nbr[e * 4 + f] = nk < 0 ? -1 : (int)ctx->iperm[nk];
+      code[e * 4 + f] = (unsigned char)(nk < 0 ? 0 : ctx->code_u[k * 4 + f]);
+    }
+  }
+  CK(dalloc(ctx->geo, geo.size() * 8));
+  CK(cudaMemcpy(ctx->geo.p, geo.data(), geo.size() * 8, cudaMemcpyHostToDevice));
+  CK(dalloc(ctx->verts, verts.size() * 8));
+  CK(cudaMemcpy(ctx->verts.p, verts.data(), verts.size() * 8, cudaMemcpyHostToDevice));
+  CK(dalloc(ctx->mat, mat.size() * sizeof(Real)));
+  CK(cudaMemcpy(ctx->mat.p, mat.data(), mat.size() * sizeof(Real), cudaMemcpyHostToDevice));
+  CK(dalloc(ctx->nbr, nbr.size() * 4));
+  CK(cudaMemcpy(ctx->nbr.p, nbr.data(), nbr.size() * 4, cudaMemcpyHostToDevice));
+  CK(dalloc(ctx->code, code.size()));
+  CK(cudaMemcpy(ctx->code.p, code.data(), code.size(), cudaMemcpyHostToDevice));
+  // ---- state
+  const size_t qbytes = (size_t)ctx->nb * K * 6 * Np * sizeof(Real);
+  const size_t pbytes = (size_t)ctx->nb * ctx->K1 * 6 * Np * sizeof(Real);
+  for (int i = 0; i < 2; ++i) {
+    CK(dalloc(ctx->q[i], qbytes));
+    if (qbytes) CK(cudaMemsetAsync(ctx->q[i].p, 0, qbytes, ctx->stream));
+  }
+  CK(dalloc(ctx->rq, qbytes));
+  if (qbytes) CK(cudaMemsetAsync(ctx->rq.p, 0, qbytes, ctx->stream));
+  CK(dalloc(ctx->p, pbytes));
+  CK(dalloc(ctx->rp, pbytes));
+  if (pbytes) {
+    CK(cudaMemsetAsync(ctx->p.p, 0, pbytes, ctx->stream));
+    CK(cudaMemsetAsync(ctx->rp.p, 0, pbytes, ctx->stream));
+  }
+  ctx->cur = 0;
+  ctx->t = 0.0;
+  // ---- PML samples at the quadrature nodes (double evaluation on device)
+  dfree(ctx->sig);
+  dfree(ctx->kap);
+  if (ctx->K1 > 0) {
+    std::vector<double> rq(3 * Nq);
+    for (int q = 0; q < Nq; ++q) {
+      rq[3 * q] = ctx->ref.rq[q];
+      rq[3 * q + 1] = ctx->ref.sq[q];
+      rq[3 * q + 2] = ctx->ref.tq[q];
+    }
+    double prof[16];
+    for (int u = 0; u < 3; ++u) {
+      prof[u] = ctx->prof.u0[u];
+      prof[3 + u] = ctx->prof.L[u];
+      prof[6 + u] = ctx->prof.sigma_max[u];
+      prof[9 + u] = ctx->prof.p_sigma[u];
+      prof[12 + u] = ctx->prof.kappa_max[u];
+    }
+    prof[15] = ctx->prof.eps0;
+    DevPtr drq, dprof;
+    CK(dalloc(drq, rq.size() * 8));
+    CK(dalloc(dprof, sizeof prof));
+    CK(cudaMemcpy(drq.p, rq.data(), rq.size() * 8, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(dprof.p, prof, sizeof prof, cudaMemcpyHostToDevice));
+    const size_t sb = (size_t)ctx->K1 * 3 * Nq * sizeof(Real);
+    CK(dalloc(ctx->sig, sb));
+    if (ctx->kappa) CK(dalloc(ctx->kap, sb));
+    CK((launch_pml_samples<Real>(Nq, (int)ctx->K1, (int)ctx->K0, (const double*)ctx->verts.p,
+                                 (const double*)drq.p, (const double*)dprof.p,
+                                 (Real*)ctx->sig.p, (Real*)ctx->kap.p, ctx->stream)));
+    CK(cudaStreamSynchronize(ctx->stream));
+    dfree(drq);
+    dfree(dprof);
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return WADG_OK;
+}
+
+wadg_status rebuild(wadg_ctx* ctx) {
+  return ctx->rs == 8 ? rebuild_typed<double>(ctx) : rebuild_typed<float>(ctx);
+}
+
+template <typename Real>
+wadg_status upload_sources(wadg_ctx* ctx) {
+  const int Np = ctx->ref.Np;
+  invalidate_graphs(ctx);
+  std::vector<SrcDev> sd;
+  std::vector<Real> w;
+  for (const wadg_dipole& d : ctx->src_user) {
+    double rst[3];
+    int64_t k = locate(ctx, d.x, rst);
+    if (k < 0)
+      return fail(ctx, WADG_ENOTFOUND, "source point (%g, %g, %g) is outside the mesh", d.x[0],
+                  d.x[1], d.x[2]);
+    std::vector<double> ell = ctx->ref.lagrange_at(rst[0], rst[1], rst[2]);
+    SrcDev s{};
+    s.elem = (int)ctx->iperm[k];
+    s.batch = d.batch;
+    for (int u = 0; u < 3; ++u) s.dir[u] = d.dir[u];
+    s.t0 = d.t0;
+    s.width = d.width;
+    s.amp = d.amplitude;
+    sd.push_back(s);
+    for (int i = 0; i < Np; ++i) {  // M_k^{-1} l(r_s) = M^{-1} l / J_k
+      double a = 0.0;
+      for (int j = 0; j < Np; ++j) a += ctx->ref.Minv[i * Np + j] * ell[j];
+      w.push_back((Real)(a / ctx->J_u[k]));
+    }
+  }
+  ctx->nsrc = (int)sd.size();
+  CK(dalloc(ctx->src, sd.size() * sizeof(SrcDev)));
+  CK(dalloc(ctx->srcw, w.size() * sizeof(Real)));
+  if (!sd.empty()) {
+    CK(cudaMemcpy(ctx->src.p, sd.data(), sd.size() * sizeof(SrcDev), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->srcw.p, w.data(), w.size() * sizeof(Real), cudaMemcpyHostToDevice));
+  }
+  return WADG_OK;
+}
+
+wadg_status upload_probes(wadg_ctx* ctx) {
+  const int Np = ctx->ref.Np;
+  invalidate_graphs(ctx);
+  const int n = (int)(ctx->probe_user.size() / 3);
+  std::vector<int> el;
+  std::vector<double> ell;
+  for (int i = 0; i < n; ++i) {
+    double rst[3];
+    int64_t k = locate(ctx, &ctx->probe_user[3 * i], rst);
+    if (k < 0)
+      return fail(ctx, WADG_ENOTFOUND, "probe point %d is outside the mesh", i);
+    el.push_back((int)ctx->iperm[k]);
+    std::vector<double> l = ctx->ref.lagrange_at(rst[0], rst[1], rst[2]);
+    ell.insert(ell.end(), l.begin(), l.end());
+  }
+  ctx->nprobe = n;
+  CK(dalloc(ctx->pr_elem, el.size() * 4));
+  CK(dalloc(ctx->pr_ell, ell.size() * 8));
+  if (n) {
+    CK(cudaMemcpy(ctx->pr_elem.p, el.data(), el.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->pr_ell.p, ell.data(), ell.size() * 8, cudaMemcpyHostToDevice));
+  }
+  (void)Np;
+  return WADG_OK;
+}
+
+wadg_status remap_points(wadg_ctx* ctx) {
+  wadg_status s = ctx->rs == 8 ? upload_sources<double>(ctx) : upload_sources<float>(ctx);
+  if (s != WADG_OK) return s;
+  return upload_probes(ctx);
+}
+
+template <typename Real>
+StageParams<Real> stage_params(wadg_ctx* ctx, int stage, double dt, double t, bool use_tdev,
+                               bool pml) {
+  StageParams<Real> P{};
+  const int Np = ctx->ref.Np;
+  P.qin = (const Real*)ctx->q[ctx->cur].p;
+  P.qout = (Real*)ctx->q[ctx->cur ^ 1].p;
+  P.resq = (Real*)ctx->rq.p;
+  P.p = (Real*)ctx->p.p;
+  P.resp = (Real*)ctx->rp.p;
+  P.geo = (const double*)ctx->geo.p;
+  P.mat = (const Real*)ctx->mat.p;
+  P.nbr = (const int*)ctx->nbr.p;
+  P.code = (const unsigned char*)ctx->code.p;
+  P.sig = (const Real*)ctx->sig.p;
+  P.kap = (const Real*)ctx->kap.p;
+  P.ops = (const Real*)ctx->ops.p;
+  P.tabs = (const unsigned char*)ctx->tabs.p;
+  P.strideQ = ctx->K * 6 * Np;
+  P.strideP = ctx->K1 * 6 * Np;
+  P.K0 = (int)ctx->K0;
+  P.e_begin = pml ? (int)ctx->K0 : 0;
+  P.n_elem = pml ? (int)ctx->K1 : (int)ctx->K0;
+  P.nsrc = ctx->nsrc;
+  P.src = (const SrcDev*)ctx->src.p;
+  P.src_w = (const Real*)ctx->srcw.p;
+  P.rk_a = kRkA[stage];
+  P.rk_b = kRkB[stage];
+  P.rk_c = kRkC.c[stage];
+  P.dt = dt;
+  P.t = t;
+  P.t_dev = use_tdev ? (const double*)ctx->tdev.p : nullptr;
+  P.eps0 = ctx->has_prof ? ctx->prof.eps0 : 1.0;
+  P.alpha = 1.0;
+  return P;
+}
+
+template <typename Real>
+wadg_status issue_stage(wadg_ctx* ctx, int stage, double dt, double t, bool use_tdev) {
+  StageParams<Real> A = stage_params<Real>(ctx, stage, dt, t, use_tdev, false);
+  CK(launch_stage<Real>(ctx->N, false, false, A, ctx->nb, ctx->stream));
+  if (ctx->K1 > 0) {
+    StageParams<Real> B = stage_params<Real>(ctx, stage, dt, t, use_tdev, true);
+    CK(launch_stage<Real>(ctx->N, true, ctx->kappa, B, ctx->nb, ctx->stream));
+  }
+  ctx->cur ^= 1;
+  return WADG_OK;
+}
+
+wadg_status issue_step(wadg_ctx* ctx, double dt) {
+  for (int s = 0; s < 5; ++s) {
+    wadg_status st = ctx->rs == 8 ? issue_stage<double>(ctx, s, dt, 0.0, true)
+                                  : issue_stage<float>(ctx, s, dt, 0.0, true);
+    if (st != WADG_OK) return st;
+  }
+  if (ctx->nprobe > 0) {
+    ProbeParams pp{};
+    pp.q = ctx->q[ctx->cur].p;
+    pp.strideQ = ctx->K * 6 * ctx->ref.Np;
+    pp.nprobe = ctx->nprobe;
+    pp.nb = ctx->nb;
+    pp.Np = ctx->ref.Np;
+    pp.elem = (const int*)ctx->pr_elem.p;
+    pp.ell = (const double*)ctx->pr_ell.p;
+    pp.out = (double*)ctx->pr_out.p;
+    pp.obj = (double*)ctx->obj.p;
+    pp.step = (const int64_t*)ctx->stepdev.p;
+    CK(launch_probes(ctx->rs == 8, pp, ctx->stream));
+  }
+  CK(launch_advance((double*)ctx->tdev.p, (int64_t*)ctx->stepdev.p, dt, ctx->stream));
+  return WADG_OK;
+}
+
+wadg_status capture_graphs(wadg_ctx* ctx, double dt) {
+  invalidate_graphs(ctx);
+  const int start = ctx->cur;
+  for (int g = 0; g < 2; ++g) {
+    ctx->cur = g;
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    wadg_status st = issue_step(ctx, dt);
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+    if (st != WADG_OK) return st;
+    CK(e);
+    e = cudaGraphInstantiate(&ctx->graph[g], graph, 0);
+    cudaGraphDestroy(graph);
+    CK(e);
+  }
+  ctx->cur = start;
+  ctx->graph_dt = dt;
+  ctx->graph_valid = true;
+  return WADG_OK;
+}
+
+wadg_status need_mesh(wadg_ctx* ctx) {
+  if (!ctx) return fail(nullptr, WADG_EINVAL, "null context");
+  if (!ctx->has_mesh) return fail(ctx, WADG_ESTATE, "no mesh set");
+  return WADG_OK;
+}
+
+template <typename Real>
+static wadg_status set_state_t(wadg_ctx* ctx, const double* q) {
+  const int Np = ctx->ref.Np;
+  const int64_t K = ctx->K;
+  std::vector<Real> hq((size_t)ctx->nb * K * 6 * Np, Real(0));
+  std::vector<Real> hp((size_t)ctx->nb * ctx->K1 * 6 * Np, Real(0));
+  if (q) {
+    for (int b = 0; b < ctx->nb; ++b)
+      for (int64_t e = 0; e < K; ++e) {
+        const int64_t k = ctx->perm[e];
+        const double* src = q + (((size_t)b * K + k) * 12) * Np;
+        Real* dq = &hq[(((size_t)b * K + e) * 6) * Np];
+        for (int i = 0; i < 6 * Np; ++i) dq[i] = (Real)src[i];
+        if (e >= ctx->K0) {
+          Real* dp = &hp[(((size_t)b * ctx->K1 + (e - ctx->K0)) * 6) * Np];
+          for (int i = 0; i < 6 * Np; ++i) dp[i] = (Real)src[6 * Np + i];
+        }
+      }
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->cur = 0;
+  if (!hq.empty())
+    CK(cudaMemcpy(ctx->q[0].p, hq.data(), hq.size() * sizeof(Real), cudaMemcpyHostToDevice));
+  if (!hp.empty())
+    CK(cudaMemcpy(ctx->p.p, hp.data(), hp.size() * sizeof(Real), cudaMemcpyHostToDevice));
+  CK(cudaMemset(ctx->rq.p, 0, ctx->rq.bytes));
+  if (ctx->rp.bytes) CK(cudaMemset(ctx->rp.p, 0, ctx->rp.bytes));
+  CK(cudaMemset(ctx->obj.p, 0, ctx->obj.bytes));
+  return WADG_OK;
+}
+
+template <typename Real>
+static wadg_status get_state_t(wadg_ctx* ctx, double* q) {
+  const int Np = ctx->ref.Np;
+  const int64_t K = ctx->K;
+  std::vector<Real> hq((size_t)ctx->nb * K * 6 * Np);
+  std::vector<Real> hp((size_t)ctx->nb * ctx->K1 * 6 * Np);
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaMemcpy(hq.data(), ctx->q[ctx->cur].p, hq.size() * sizeof(Real), cudaMemcpyDeviceToHost));
+  if (!hp.empty())
+    CK(cudaMemcpy(hp.data(), ctx->p.p, hp.size() * sizeof(Real), cudaMemcpyDeviceToHost));
+  for (int b = 0; b < ctx->nb; ++b)
+    for (int64_t e = 0; e < K; ++e) {
+      const int64_t k = ctx->perm[e];
+      double* dst = q + (((size_t)b * K + k) * 12) * Np;
+      const Real* sq = &hq[(((size_t)b * K + e) * 6) * Np];
+      for (int i = 0; i < 6 * Np; ++i) dst[i] = (double)sq[i];
+      if (e >= ctx->K0) {
+        const Real* sp = &hp[(((size_t)b * ctx->K1 + (e - ctx->K0)) * 6) * Np];
+        for (int i = 0; i < 6 * Np; ++i) dst[6 * Np + i] = (double)sp[i];
+      } else {
+        for (int i = 0; i < 6 * Np; ++i) dst[6 * Np + i] = 0.0;
+      }
+    }
+  return WADG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+wadg_status wadg_create(int N, wadg_precision prec, int32_t n_batch, int device,
+                        void* cuda_stream, wadg_ctx** out) {
+  wadg_ctx* ctx = nullptr;
+  if (!out) return fail(nullptr, WADG_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (N < 1 || N > 5) return fail(nullptr, WADG_EINVAL, "N must be in 1..5 (got %d)", N);
+  if (prec != WADG_FP64 && prec != WADG_FP32) {
+    if (prec == WADG_TF32 || prec == WADG_BF16)
+      return fail(nullptr, WADG_EUNSUPPORTED, "precision %d not available in this build", prec);
+    return fail(nullptr, WADG_EINVAL, "unknown precision %d", prec);
+  }
+  if (n_batch < 1) return fail(nullptr, WADG_EINVAL, "n_batch must be >= 1");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+    return fail(nullptr, WADG_ECUDA, "CUDA device %d not available", device);
+  if (cudaSetDevice(device) != cudaSuccess)
+    return fail(nullptr, WADG_ECUDA, "cudaSetDevice(%d) failed", device);
+  ctx = new wadg_ctx();
+  ctx->N = N;
+  ctx->prec = prec;
+  ctx->nb = n_batch;
+  ctx->device = device;
+  ctx->rs = prec == WADG_FP64 ? 8 : 4;
+  const char* e = nullptr;
+  if (!build_ref_ops(N, ctx->ref, &e)) {
+    delete ctx;
+    return fail(nullptr, WADG_EINVAL, "%s", e);
+  }
+  if (cuda_stream) {
+    ctx->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete ctx;
+      return fail(nullptr, WADG_ECUDA, "cannot create a stream");
+    }
+    ctx->own_stream = true;
+  }
+  wadg_status s = ctx->rs == 8 ? upload_ops<double>(ctx) : upload_ops<float>(ctx);
+  if (s == WADG_OK) {
+    cudaError_t ce = ctx->rs == 8 ? configure_stage_kernels<double>(N)
+                                  : configure_stage_kernels<float>(N);
+    if (ce != cudaSuccess) s = fail(ctx, WADG_ECUDA, "kernel set-up: %s", cudaGetErrorString(ce));
+  }
+  if (s == WADG_OK) {
+    cudaError_t ce = cudaSuccess;
+    if (ce == cudaSuccess) ce = dalloc(ctx->tdev, 8);
+    if (ce == cudaSuccess) ce = dalloc(ctx->stepdev, 8);
+    if (ce == cudaSuccess) ce = dalloc(ctx->flag, 4);
+    if (ce == cudaSuccess) ce = dalloc(ctx->obj, 8 * (size_t)n_batch);
+    if (ce == cudaSuccess) ce = cudaMemset(ctx->obj.p, 0, 8 * (size_t)n_batch);
+    if (ce != cudaSuccess) s = fail(nullptr, WADG_ECUDA, "%s", cudaGetErrorString(ce));
+  } else {
+    g_err = ctx->err;
+  }
+  if (s != WADG_OK) {
+    wadg_destroy(ctx);
+    return s;
+  }
+  *out = ctx;
+  return WADG_OK;
+}
+
+wadg_status wadg_destroy(wadg_ctx* ctx) {
+  if (!ctx) return WADG_OK;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  invalidate_graphs(ctx);
+  for (DevPtr* d : {&ctx->q[0], &ctx->q[1], &ctx->rq, &ctx->p, &ctx->rp, &ctx->geo, &ctx->mat,
+                    &ctx->nbr, &ctx->code, &ctx->sig, &ctx->kap, &ctx->ops, &ctx->tabs,
+                    &ctx->verts, &ctx->src, &ctx->srcw, &ctx->pr_elem, &ctx->pr_ell,
+                    &ctx->pr_out, &ctx->obj, &ctx->tdev, &ctx->stepdev, &ctx->flag})
+    dfree(*d);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return WADG_OK;
+}
+
+wadg_status wadg_set_mesh(wadg_ctx* ctx, int64_t nv, const double* vxyz, int64_t K,
+                          const int64_t* etov) {
+  if (!ctx) return fail(nullptr, WADG_EINVAL, "null context");
+  if (nv < 4 || K < 1 || !vxyz || !etov) return fail(ctx, WADG_EINVAL, "empty mesh");
+  if (K > (int64_t)1 << 30) return fail(ctx, WADG_EINVAL, "too many elements");
+  cudaSetDevice(ctx->device);
+  for (int64_t i = 0; i < 4 * K; ++i)
+    if (etov[i] < 0 || etov[i] >= nv)
+      return fail(ctx, WADG_EINVAL, "etov[%lld] = %lld out of range", (long long)i,
+                  (long long)etov[i]);
+  ctx->has_mesh = false;
+  ctx->K = K;
+  ctx->nv = nv;
+  ctx->vxyz.assign(vxyz, vxyz + 3 * nv);
+  ctx->etov.assign(etov, etov + 4 * K);
+  ctx->eps_r.clear();
+  ctx->mu_r.clear();
+  ctx->has_prof = false;
+  ctx->kappa = false;
+  ctx->src_user.clear();
+  ctx->probe_user.clear();
+  // ---- affine geometry in double
+  ctx->metric_u.assign(9 * K, 0.0);
+  ctx->J_u.assign(K, 0.0);
+  ctx->fscale_max = 0.0;
+  for (int64_t k = 0; k < K; ++k) {
+    const double* v[4];
+    for (int a = 0; a < 4; ++a) v[a] = &vxyz[3 * etov[4 * k + a]];
+    double A[3][3];  // columns dx/dr, dx/ds, dx/dt
+    for (int d = 0; d < 3; ++d) {
+      A[d][0] = 0.5 * (v[1][d] - v[0][d]);
+      A[d][1] = 0.5 * (v[2][d] - v[0][d]);
+      A[d][2] = 0.5 * (v[3][d] - v[0][d]);
+    }
+    double c00 = A[1][1] * A[2][2] - A[1][2] * A[2][1];
+    double c01 = A[1][2] * A[2][0] - A[1][0] * A[2][2];
+    double c02 = A[1][0] * A[2][1] - A[1][1] * A[2][0];
+    double J = A[0][0] * c00 + A[0][1] * c01 + A[0][2] * c02;
+    if (!(J > 0.0))
+      return fail(ctx, WADG_EINVAL, "element %lld has non-positive Jacobian %g", (long long)k, J);
+    double inv[3][3];  // inverse: rows grad r, grad s, grad t
+    inv[0][0] = c00 / J;
+    inv[1][0] = c01 / J;
+    inv[2][0] = c02 / J;
+    inv[0][1] = (A[0][2] * A[2][1] - A[0][1] * A[2][2]) / J;
+    inv[1][1] = (A[0][0] * A[2][2] - A[0][2] * A[2][0]) / J;
+    inv[2][1] = (A[0][1] * A[2][0] - A[0][0] * A[2][1]) / J;
+    inv[0][2] = (A[0][1] * A[1][2] - A[0][2] * A[1][1]) / J;
+    inv[1][2] = (A[0][2] * A[1][0] - A[0][0] * A[1][2]) / J;
+    inv[2][2] = (A[0][0] * A[1][1] - A[0][1] * A[1][0]) / J;
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) ctx->metric_u[9 * k + 3 * r + c] = inv[r][c];
+    ctx->J_u[k] = J;
+    double g[4][3];
+    for (int d = 0; d < 3; ++d) {
+      g[0][d] = -inv[2][d];
+      g[1][d] = -inv[1][d];
+      g[2][d] = inv[0][d] + inv[1][d] + inv[2][d];
+      g[3][d] = -inv[0][d];
+    }
+    for (int f = 0; f < 4; ++f)
+      ctx->fscale_max = std::max(
+          ctx->fscale_max, std::sqrt(g[f][0] * g[f][0] + g[f][1] * g[f][1] + g[f][2] * g[f][2]));
+  }
+  // ---- face connectivity by sorted vertex triples
+  struct FaceKey {
+    int64_t a, b, c, id;
+  };
+  std::vector<FaceKey> fk(4 * K);
+  for (int64_t k = 0; k < K; ++k)
+    for (int f = 0; f < 4; ++f) {
+      int64_t v3[3];
+      for (int i = 0; i < 3; ++i) v3[i] = etov[4 * k + kFaceVerts[f][i]];
+      std::sort(v3, v3 + 3);
+      fk[4 * k + f] = {v3[0], v3[1], v3[2], 4 * k + f};
+    }
+  std::sort(fk.begin(), fk.end(), [](const FaceKey& x, const FaceKey& y) {
+    if (x.a != y.a) return x.a < y.a;
+    if (x.b != y.b) return x.b < y.b;
+    if (x.c != y.c) return x.c < y.c;
+    return x.id < y.id;
+  });
+  ctx->nbr_u.assign(4 * K, -1);
+  ctx->code_u.assign(4 * K, 0);
+  auto same = [](const FaceKey& x, const FaceKey& y) { return x.a == y.a && x.b == y.b && x.c == y.c; };
+  for (size_t i = 0; i < fk.size();) {
+    size_t j = i + 1;
+    while (j < fk.size() && same(fk[i], fk[j])) ++j;
+    if (j - i > 2)
+      return fail(ctx, WADG_EINVAL, "face (%lld,%lld,%lld) shared by %d elements",
+                  (long long)fk[i].a, (long long)fk[i].b, (long long)fk[i].c, (int)(j - i));
+    if (j - i == 2) {
+      for (int side = 0; side < 2; ++side) {
+        int64_t me = fk[i + side].id, ot = fk[i + 1 - side].id;
+        int64_t k = me / 4, f = me % 4, k2 = ot / 4, f2 = ot % 4;
+        int64_t gv[3], hv[3];
+        for (int a = 0; a < 3; ++a) {
+          gv[a] = etov[4 * k + kFaceVerts[f][a]];
+          hv[a] = etov[4 * k2 + kFaceVerts[f2][a]];
+        }
+        int rot = -1;
+        for (int r = 0; r < 6 && rot < 0; ++r)
+          if (hv[0] == gv[kFacePerm[r][0]] && hv[1] == gv[kFacePerm[r][1]] &&
+              hv[2] == gv[kFacePerm[r][2]])
+            rot = r;
+        if (rot < 0) return fail(ctx, WADG_EINVAL, "degenerate face in element %lld", (long long)k);
+        ctx->nbr_u[me] = k2;
+        ctx->code_u[me] = (int)(f2 * 6 + rot);
+      }
+    }
+    i = j;
+  }
+  ctx->has_mesh = true;
+  return rebuild(ctx);
+}
+
+wadg_status wadg_set_materials(wadg_ctx* ctx, const double* eps_r, const double* mu_r) {
+  wadg_status s = need_mesh(ctx);
+  if (s != WADG_OK) return s;
+  cudaSetDevice(ctx->device);
+  for (int64_t k = 0; k < ctx->K; ++k)
+    if ((eps_r && !(eps_r[k] > 0)) || (mu_r && !(mu_r[k] > 0)))
+      return fail(ctx, WADG_EINVAL, "material of element %lld not positive", (long long)k);
+  if (eps_r) ctx->eps_r.assign(eps_r, eps_r + ctx->K); else ctx->eps_r.clear();
+  if (mu_r) ctx->mu_r.assign(mu_r, mu_r + ctx->K); else ctx->mu_r.clear();
+  s = rebuild(ctx);
+  if (s != WADG_OK) return s;
+  return remap_points(ctx);
+}
+
+wadg_status wadg_set_pml_profile(wadg_ctx* ctx, const wadg_pml_profile* prof,
+                                 wadg_pml_scheme scheme) {
+  wadg_status s = need_mesh(ctx);
+  if (s != WADG_OK) return s;
+  cudaSetDevice(ctx->device);
+  if (scheme != WADG_PML_WAA)
+    return fail(ctx, WADG_EUNSUPPORTED, "only the weight-adjusted PML scheme is built");
+  if (prof) {
+    for (int u = 0; u < 3; ++u) {
+      if (!(prof->L[u] > 0) || prof->sigma_max[u] < 0 || !(prof->kappa_max[u] >= 1.0) ||
+          !(prof->p_sigma[u] >= 0))
+        return fail(ctx, WADG_EINVAL, "bad PML profile on axis %d", u);
+    }
+    if (!(prof->eps0 > 0)) return fail(ctx, WADG_EINVAL, "eps0 must be positive");
+    ctx->has_prof = true;
+    ctx->prof = *prof;
+    ctx->kappa = false;
+    for (int u = 0; u < 3; ++u)
+      if (prof->kappa_max[u] != 1.0) ctx->kappa = true;
+  } else {
+    ctx->has_prof = false;
+    ctx->kappa = false;
+  }
+  s = rebuild(ctx);
+  if (s != WADG_OK) return s;
+  return remap_points(ctx);
+}
+
+wadg_status wadg_set_sources(wadg_ctx* ctx, int32_t n, const wadg_dipole* src) {
+  wadg_status s = need_mesh(ctx);
+  if (s != WADG_OK) return s;
+  cudaSetDevice(ctx->device);
+  if (n < 0 || (n > 0 && !src)) return fail(ctx, WADG_EINVAL, "bad source list");
+  for (int i = 0; i < n; ++i) {
+    if (src[i].batch < 0 || src[i].batch >= ctx->nb)
+      return fail(ctx, WADG_EINVAL, "source %d: batch %d out of range", i, src[i].batch);
+    if (!(src[i].width > 0)) return fail(ctx, WADG_EINVAL, "source %d: width must be > 0", i);
+  }
+  ctx->src_user.assign(src, src + n);
+  return ctx->rs == 8 ? upload_sources<double>(ctx) : upload_sources<float>(ctx);
+}
+
+wadg_status wadg_set_probes(wadg_ctx* ctx, int32_t n, const double* xyz) {
+  wadg_status s = need_mesh(ctx);
+  if (s != WADG_OK) return s;
+  cudaSetDevice(ctx->device);
+  if (n < 0 || (n > 0 && !xyz)) return fail(ctx, WADG_EINVAL, "bad probe list");
+  ctx->probe_user.assign(xyz, xyz + 3 * (size_t)n);
+  return upload_probes(ctx);
+}
+
+wadg_status wadg_set_state(wadg_ctx* ctx, const double* q, double t) {
+  wadg_status s = need_mesh(ctx);
+  if (s != WADG_OK) return s;
+  cudaSetDevice(ctx->device);
+  s = ctx->rs == 8 ? set_state_t<double>(ctx, q) : set_state_t<float>(ctx, q);
+  if (s == WADG_OK) ctx->t = t;
+  return s;
+}
+
+wadg_status wadg_get_state(wadg_ctx* ctx, double* q, double* t) {
+  wadg_status s = need_mesh(ctx);
+  if (s != WADG_OK) return s;
+  cudaSetDevice(ctx->device);
+  if (q) {
+    s = ctx->rs == 8 ? get_state_t<double>(ctx, q) : get_state_t<float>(ctx, q);
+    if (s != WADG_OK) return s;
+  }
+  if (t) *t = ctx->t;
+  return WADG_OK;
+}
+
+wadg_status wadg_rk_stage(wadg_ctx* ctx, int stage, double t, double dt) {
+  wadg_status s = need_mesh(ctx);
+  if (s != WADG_OK) return s;
+  if (stage < 0 || stage > 4) return fail(ctx, WADG_EINVAL, "stage must be 0..4");
+  cudaSetDevice(ctx->device);
+  return ctx->rs == 8 ? issue_stage<double>(ctx, stage, dt, t, false)
+                      : issue_stage<float>(ctx, stage, dt, t, false);
+}
+
+wadg_status wadg_run_steps(wadg_ctx* ctx, int64_t nsteps, double dt, double* probe_out) {
+  wadg_status s = need_mesh(ctx);
+  if (s != WADG_OK) return s;
+  if (nsteps < 0 || !(dt > 0)) return fail(ctx, WADG_EINVAL, "bad nsteps or dt");
+  if (nsteps == 0) return WADG_OK;
+  cudaSetDevice(ctx->device);
+  const int64_t chunk = std::min<int64_t>(nsteps, 4096);
+  const size_t need = (size_t)chunk * ctx->nprobe * 6 * ctx->nb * 8;
+  if (ctx->nprobe > 0 && ctx->pr_out.bytes < need) {
+    invalidate_graphs(ctx);
+    CK(dalloc(ctx->pr_out, need));
+  }
+  if (!ctx->graph_valid || ctx->graph_dt != dt) {
+    s = capture_graphs(ctx, dt);
+    if (s != WADG_OK) return s;
+  }
+  const size_t rec = (size_t)ctx->nprobe * 6 * ctx->nb;
+  int64_t done = 0;
+  while (done < nsteps) {
+    const int64_t n = std::min(chunk, nsteps - done);
+    double tt = ctx->t + done * dt;
+    CK(cudaMemcpyAsync(ctx->tdev.p, &tt, 8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(ctx->stepdev.p, 0, 8, ctx->stream));
+    for (int64_t i = 0; i < n; ++i) {
+      CK(cudaGraphLaunch(ctx->graph[ctx->cur], ctx->stream));
+      ctx->cur ^= 1;
+    }
+    if (probe_out && rec) {
+      CK(cudaMemcpyAsync(probe_out + (size_t)done * rec, ctx->pr_out.p, (size_t)n * rec * 8,
+                         cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    done += n;
+  }
+  ctx->t += nsteps * dt;
+  // non-finite check of the E,H state
+  CK(cudaMemsetAsync(ctx->flag.p, 0, 4, ctx->stream));
+  const int64_t nq = ctx->nb * ctx->K * 6 * ctx->ref.Np;
+  if (ctx->rs == 8) CK(launch_check_finite<double>((const double*)ctx->q[ctx->cur].p, nq, (int*)ctx->flag.p, ctx->stream));
+  else CK(launch_check_finite<float>((const float*)ctx->q[ctx->cur].p, nq, (int*)ctx->flag.p, ctx->stream));
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, ctx->flag.p, 4, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (flag) return fail(ctx, WADG_ENONFINITE, "state became non-finite");
+  return WADG_OK;
+}
+
+wadg_status wadg_profile_stage(wadg_ctx* ctx, int reps, double dt, double* ms_out) {
+  wadg_status s = need_mesh(ctx);
+  if (s != WADG_OK) return s;
+  if (reps < 1 || !ms_out) return fail(ctx, WADG_EINVAL, "bad arguments");
+  cudaSetDevice(ctx->device);
+  cudaEvent_t ev[4];
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  float tot[2] = {0.f, 0.f};
+  for (int r = 0; r < reps; ++r) {
+    const int stage = r % 5;
+    for (int cls = 0; cls < 2; ++cls) {
+      if (cls == 1 && ctx->K1 == 0) continue;
+      CK(cudaEventRecord(ev[2 * cls], ctx->stream));
+      if (ctx->rs == 8) {
+        StageParams<double> P = stage_params<double>(ctx, stage, dt, ctx->t, false, cls == 1);
+        CK(launch_stage<double>(ctx->N, cls == 1, ctx->kappa, P, ctx->nb, ctx->stream));
+      } else {
+        StageParams<float> P = stage_params<float>(ctx, stage, dt, ctx->t, false, cls == 1);
+        CK(launch_stage<float>(ctx->N, cls == 1, ctx->kappa, P, ctx->nb, ctx->stream));
+      }
+      CK(cudaEventRecord(ev[2 * cls + 1], ctx->stream));
+    }
+    ctx->cur ^= 1;
+    CK(cudaEventSynchronize(ev[3]));
+    CK(cudaEventSynchronize(ev[1]));
+    for (int cls = 0; cls < 2; ++cls) {
+      if (cls == 1 && ctx->K1 == 0) continue;
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, ev[2 * cls], ev[2 * cls + 1]));
+      tot[cls] += ms;
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  ms_out[0] = tot[0] / reps;
+  ms_out[1] = tot[1] / reps;
+  return WADG_OK;
+}
+
+wadg_status wadg_stable_dt(const wadg_ctx* ctx, double cfl, double* dt_out) {
+  if (!ctx || !dt_out) return fail(nullptr, WADG_EINVAL, "null argument");
+  if (!ctx->has_mesh) return fail(const_cast<wadg_ctx*>(ctx), WADG_ESTATE, "no mesh set");
+  *dt_out = cfl * 2.0 / ((ctx->N + 1.0) * (ctx->N + 1.0) * ctx->fscale_max);
+  return WADG_OK;
+}
+
+wadg_status wadg_objective(wadg_ctx* ctx, double* J_out) {
+  if (!ctx || !J_out) return fail(nullptr, WADG_EINVAL, "null argument");
+  cudaSetDevice(ctx->device);
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaMemcpy(J_out, ctx->obj.p, 8 * (size_t)ctx->nb, cudaMemcpyDeviceToHost));
+  return WADG_OK;
+}
+
+wadg_status wadg_memory_report(const wadg_ctx* ctx, size_t* bytes_state, size_t* bytes_pml_coeff,
+                               size_t* bytes_operators, size_t* bytes_geometry) {
+  if (!ctx) return fail(nullptr, WADG_EINVAL, "null context");
+  if (bytes_state) *bytes_state = ctx->q[0].bytes + ctx->q[1].bytes + ctx->rq.bytes + ctx->p.bytes + ctx->rp.bytes;
+  if (bytes_pml_coeff) *bytes_pml_coeff = ctx->sig.bytes + ctx->kap.bytes;
+  if (bytes_operators) *bytes_operators = ctx->ops.bytes + ctx->tabs.bytes;
+  if (bytes_geometry)
+    *bytes_geometry = ctx->geo.bytes + ctx->mat.bytes + ctx->nbr.bytes + ctx->code.bytes;
+  return WADG_OK;
+}
+
+wadg_status wadg_mesh_info(const wadg_ctx* ctx, int64_t* K, int64_t* K_pml, int32_t* Np,
+                           int32_t* Nq) {
+  if (!ctx) return fail(nullptr, WADG_EINVAL, "null context");
+  if (K) *K = ctx->K;
+  if (K_pml) *K_pml = ctx->K1;
+  if (Np) *Np = ctx->ref.Np;
+  if (Nq) *Nq = ctx->ref.Nq;
+  return WADG_OK;
+}
+
+wadg_status wadg_synchronize(wadg_ctx* ctx) {
+  if (!ctx) return fail(nullptr, WADG_EINVAL, "null context");
+  cudaSetDevice(ctx->device);
+  CK(cudaStreamSynchronize(ctx->stream));
+  return WADG_OK;
+}
+
+wadg_status wadg_reference_operator(int N, int which, double* out, int64_t cap, int64_t* n_out) {
+  RefOps R;
+  const char* e = nullptr;
+  if (!build_ref_ops(N, R, &e)) return fail(nullptr, WADG_EINVAL, "%s", e);
+  std::vector<double> v;
+  switch (which) {
+    case 0: v = R.Dr; break;
+    case 1: v = R.Ds; break;
+    case 2: v = R.Dt; break;
+    case 3: v = R.LIFT; break;
+    case 4: v = R.Vq; break;
+    case 5: v = R.Pq; break;
+    case 6:
+      for (int q = 0; q < R.Nq; ++q) v.insert(v.end(), {R.rq[q], R.sq[q], R.tq[q], R.wq[q]});
+      break;
+    case 7: v = R.Minv; break;
+    default: return fail(nullptr, WADG_EINVAL, "unknown operator %d", which);
+  }
+  if (n_out) *n_out = (int64_t)v.size();
+  if (!out) return WADG_OK;
+  if (cap < (int64_t)v.size()) return fail(nullptr, WADG_EINVAL, "capacity %lld < %zu", (long long)cap, v.size());
+  std::memcpy(out, v.data(), v.size() * 8);
+  return WADG_OK;
+}
+
+const char* wadg_last_error(const wadg_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_err.c_str();
+}
+
+}  // extern "C"

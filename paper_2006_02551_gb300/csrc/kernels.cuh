@@ -1,0 +1,83 @@
+// Device-side data layout and kernel entry points of the DGTD stage.
+//
+// Layout in HBM (internal element order: non-PML elements first, then PML
+// elements, each class in space-filling-curve order of the centroids):
+//   E,H      q[b][e][6][Np]        two copies (stage input / output)
+//   res      rq[b][e][6][Np]       LSERK register for E,H
+//   P^E,P^H  p[b][e'][6][Np]       PML elements only (e' = e - K0), updated in place
+//   res      rp[b][e'][6][Np]
+//   geometry geo[e][9]             double: r_x r_y r_z s_x s_y s_z t_x t_y t_z
+//   material mat[e][3]             1/eps, 1/mu, Z = sqrt(mu/eps)
+//   faces    nbr[e][4] (-1: PEC), code[e][4] = neighbour face * 6 + rotation
+//   PML      sig[e'][3][Nq] (and kap[e'][3][Nq])  sigma_u, kappa_u at the
+//            quadrature nodes of each PML element
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace wadg {
+
+struct SrcDev {
+  int elem;     // internal element id
+  int batch;
+  double dir[3];
+  double t0, width, amp;
+};
+
+template <typename Real>
+struct StageParams {
+  const Real* qin;
+  Real* qout;
+  Real* resq;
+  Real* p;
+  Real* resp;
+  const double* geo;
+  const Real* mat;
+  const int* nbr;
+  const unsigned char* code;
+  const Real* sig;
+  const Real* kap;
+  const Real* ops;          // DrT | DsT | DtT | LIFTT | VqT | PqT
+  const unsigned char* tabs;  // Fmask[4 Nfp] | fperm[4*24*Nfp]
+  int64_t strideQ;          // elements*6*Np per batch (all elements)
+  int64_t strideP;          // K1*6*Np per batch
+  int K0;                   // first PML element (internal id)
+  int e_begin;              // first element of this launch's class
+  int n_elem;               // elements of this launch's class
+  int nsrc;
+  const SrcDev* src;
+  const Real* src_w;        // [nsrc][Np]: M_k^{-1} l(r_s)
+  double rk_a, rk_b, rk_c, dt;
+  double t;                 // base time if t_dev == nullptr
+  const double* t_dev;      // device base time (graph replays)
+  double eps0;
+  double alpha;             // flux upwinding (1 upwind, 0 central)
+};
+
+struct ProbeParams {
+  const void* q;            // current E,H
+  int64_t strideQ;
+  int nprobe, nb, Np;
+  const int* elem;          // [nprobe]
+  const double* ell;        // [nprobe][Np]
+  double* out;              // [nsteps][nprobe][6][nb]
+  double* obj;              // [nb]
+  const int64_t* step;      // device step counter since run start
+};
+
+// launchers (return cudaError_t of the launch)
+template <typename Real>
+cudaError_t configure_stage_kernels(int N);  // once per device, outside graph capture
+template <typename Real>
+cudaError_t launch_stage(int N, bool pml, bool kappa, const StageParams<Real>& P, int nb,
+                         cudaStream_t s);
+cudaError_t launch_probes(bool fp64, const ProbeParams& P, cudaStream_t s);
+cudaError_t launch_advance(double* t_dev, int64_t* step_dev, double dt, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_pml_samples(int Nq, int K1, int K0, const double* verts,
+                               const double* rq /*[Nq][3]*/, const double* prof /*16*/,
+                               Real* sig, Real* kap, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_check_finite(const Real* a, int64_t n, int* flag, cudaStream_t s);
+
+}  // namespace wadg

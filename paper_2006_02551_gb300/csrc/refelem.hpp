@@ -1,0 +1,38 @@
+// Reference-tetrahedron operators for nodal DG of order N, built in FP64 on
+// the host (Section II.A: reference matrices M, S, F of eqs. 14, 16, 17;
+// V_q, P_q of eqs. 20, 21).
+#pragma once
+#include <vector>
+
+namespace wadg {
+
+int n_nodes(int N);
+int n_face_nodes(int N);
+
+struct RefOps {
+  int N = 0, Np = 0, Nfp = 0, Nq = 0;
+  std::vector<double> r, s, t;        // nodes [Np]
+  std::vector<int> bary;              // integer barycentrics [Np][4] (sum N)
+  std::vector<double> V, Vinv, Minv;  // [Np][Np] row-major
+  std::vector<double> Dr, Ds, Dt;     // [Np][Np]
+  std::vector<int> Fmask;             // [4][Nfp] volume node of face node
+  std::vector<double> LIFT;           // [Np][4 Nfp]
+  std::vector<double> rq, sq, tq, wq; // quadrature [Nq]
+  std::vector<double> Vq;             // [Nq][Np]
+  std::vector<double> Pq;             // [Np][Nq]
+  // face-node permutation table: for local face f, neighbour face nf and
+  // vertex rotation rot (code = nf*6 + rot), the neighbour's volume node
+  // that coincides with face node m of face f: [4][24][Nfp]
+  std::vector<int> fperm;
+  std::vector<double> lagrange_at(double r, double s, double t) const;  // [Np]
+};
+
+// Builds all operators; returns false (and a message) on failure.
+bool build_ref_ops(int N, RefOps& out, const char** err);
+
+// the six permutations of three face vertices used to encode rotations
+extern const int kFacePerm[6][3];
+// local vertex triples of the four faces (t=-1, s=-1, r+s+t=-1, r=-1)
+extern const int kFaceVerts[4][3];
+
+}  // namespace wadg

@@ -1,0 +1,237 @@
+"""Thin ctypes binding of the C ABI declared in ``include/wadg.h``.
+
+Argument marshalling only: every step of the solver runs in the library's
+CUDA kernels.  The functions keep the C names; ``Solver`` is a small
+convenience wrapper that owns one context.  If the shared library is missing
+the import fails loudly (there is no fallback implementation).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libwadg.so")
+
+WADG_OK, WADG_EINVAL, WADG_ENOMEM, WADG_ECUDA, WADG_ESTATE = 0, 1, 2, 3, 4
+WADG_ENOTFOUND, WADG_ETIMEOUT, WADG_ENONFINITE, WADG_EUNSUPPORTED = 5, 6, 7, 8
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESTATE",
+                5: "ENOTFOUND", 6: "ETIMEOUT", 7: "ENONFINITE", 8: "EUNSUPPORTED"}
+PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3}
+SCHEME = {"waa": 0, "stored": 1, "ec": 2}
+
+
+class WadgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class wadg_pml_profile(C.Structure):
+    _fields_ = [("u0", C.c_double * 3), ("L", C.c_double * 3),
+                ("sigma_max", C.c_double * 3), ("p_sigma", C.c_double * 3),
+                ("kappa_max", C.c_double * 3), ("eps0", C.c_double)]
+
+
+class wadg_dipole(C.Structure):
+    _fields_ = [("x", C.c_double * 3), ("dir", C.c_double * 3), ("t0", C.c_double),
+                ("width", C.c_double), ("amplitude", C.c_double), ("batch", C.c_int32)]
+
+
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_I64 = C.POINTER(C.c_int64)
+_SIG = {
+    "wadg_create": [C.c_int, C.c_int, C.c_int32, C.c_int, _P, C.POINTER(_P)],
+    "wadg_destroy": [_P],
+    "wadg_set_mesh": [_P, C.c_int64, _D, C.c_int64, _I64],
+    "wadg_set_materials": [_P, _D, _D],
+    "wadg_set_pml_profile": [_P, C.POINTER(wadg_pml_profile), C.c_int],
+    "wadg_set_sources": [_P, C.c_int32, C.POINTER(wadg_dipole)],
+    "wadg_set_probes": [_P, C.c_int32, _D],
+    "wadg_set_state": [_P, _D, C.c_double],
+    "wadg_get_state": [_P, _D, _D],
+    "wadg_rk_stage": [_P, C.c_int, C.c_double, C.c_double],
+    "wadg_run_steps": [_P, C.c_int64, C.c_double, _D],
+    "wadg_stable_dt": [_P, C.c_double, _D],
+    "wadg_profile_stage": [_P, C.c_int, C.c_double, _D],
+    "wadg_objective": [_P, _D],
+    "wadg_memory_report": [_P, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t),
+                           C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)],
+    "wadg_mesh_info": [_P, _I64, _I64, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
+    "wadg_synchronize": [_P],
+    "wadg_reference_operator": [C.c_int, C.c_int, _D, C.c_int64, _I64],
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libwadg.so not built at {path}; run "
+                          "paper_2006_02551_gb300.build.build()")
+    lib = C.CDLL(path)
+    for name, args in _SIG.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    lib.wadg_last_error.argtypes = [_P]
+    lib.wadg_last_error.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_SIG) + ["wadg_last_error"]
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_D) if a is not None else None
+
+
+def _check(st, ctx=None):
+    if st != WADG_OK:
+        msg = load().wadg_last_error(ctx)
+        raise WadgError(st, (msg or b"").decode())
+
+
+def reference_operator(N: int, which: int) -> np.ndarray:
+    lib = load()
+    n = C.c_int64(0)
+    _check(lib.wadg_reference_operator(N, which, None, 0, C.byref(n)))
+    out = np.empty(n.value)
+    _check(lib.wadg_reference_operator(N, which, _ptr(out), n.value, C.byref(n)))
+    return out
+
+
+def make_profile(u0, L, sigma_max, p_sigma, kappa_max=1.0, eps0=1.0):
+    p = wadg_pml_profile()
+    for name, v in (("u0", u0), ("L", L), ("sigma_max", sigma_max),
+                    ("p_sigma", p_sigma), ("kappa_max", kappa_max)):
+        arr = getattr(p, name)
+        vals = v if np.ndim(v) else (v, v, v)
+        for i in range(3):
+            arr[i] = float(vals[i])
+    p.eps0 = eps0
+    return p
+
+
+class Solver:
+    """One library context (one device, one stream)."""
+
+    def __init__(self, N, precision="fp64", n_batch=1, device=0, stream=None):
+        lib = load()
+        self.lib = lib
+        self.N, self.n_batch, self.precision = N, n_batch, precision
+        ctx = _P()
+        _check(lib.wadg_create(N, PRECISION[precision], n_batch, device,
+                               _P(stream) if stream else None, C.byref(ctx)))
+        self.ctx = ctx
+
+    def close(self):
+        if self.ctx:
+            self.lib.wadg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _c(self, st):
+        _check(st, self.ctx)
+
+    def set_mesh(self, vxyz, etov):
+        v = np.ascontiguousarray(vxyz, dtype=np.float64)
+        e = np.ascontiguousarray(etov, dtype=np.int64)
+        self._c(self.lib.wadg_set_mesh(self.ctx, v.shape[0], _ptr(v), e.shape[0],
+                                       e.ctypes.data_as(_I64)))
+        self.K = e.shape[0]
+
+    def set_materials(self, eps_r=None, mu_r=None):
+        er = None if eps_r is None else np.ascontiguousarray(eps_r, np.float64)
+        mr = None if mu_r is None else np.ascontiguousarray(mu_r, np.float64)
+        self._c(self.lib.wadg_set_materials(self.ctx, _ptr(er), _ptr(mr)))
+
+    def set_pml(self, profile, scheme="waa"):
+        if profile is None:
+            self._c(self.lib.wadg_set_pml_profile(self.ctx, None, SCHEME[scheme]))
+            return
+        if not isinstance(profile, wadg_pml_profile):
+            profile = make_profile(profile.u0, profile.L, profile.sigma_max,
+                                   profile.p_sigma, profile.kappa_max, profile.eps0)
+        self._c(self.lib.wadg_set_pml_profile(self.ctx, C.byref(profile), SCHEME[scheme]))
+
+    def set_sources(self, dipoles):
+        arr = (wadg_dipole * max(1, len(dipoles)))()
+        for i, d in enumerate(dipoles):
+            for k in range(3):
+                arr[i].x[k] = d.x[k]
+                arr[i].dir[k] = d.dir[k]
+            arr[i].t0, arr[i].width, arr[i].amplitude = d.t0, d.width, d.amplitude
+            arr[i].batch = d.batch
+        self._c(self.lib.wadg_set_sources(self.ctx, len(dipoles), arr))
+
+    def set_probes(self, xyz):
+        p = np.ascontiguousarray(np.asarray(xyz, np.float64).reshape(-1, 3))
+        self.n_probe = p.shape[0]
+        self._c(self.lib.wadg_set_probes(self.ctx, p.shape[0], _ptr(p)))
+
+    def info(self):
+        K, K1 = C.c_int64(), C.c_int64()
+        Np, Nq = C.c_int32(), C.c_int32()
+        self._c(self.lib.wadg_mesh_info(self.ctx, C.byref(K), C.byref(K1), C.byref(Np),
+                                        C.byref(Nq)))
+        return dict(K=K.value, K_pml=K1.value, Np=Np.value, Nq=Nq.value)
+
+    def set_state(self, q=None, t=0.0):
+        a = None if q is None else np.ascontiguousarray(q, np.float64)
+        self._c(self.lib.wadg_set_state(self.ctx, _ptr(a), t))
+
+    def get_state(self):
+        inf = self.info()
+        q = np.empty((self.n_batch, inf["K"], 12, inf["Np"]))
+        t = C.c_double()
+        self._c(self.lib.wadg_get_state(self.ctx, _ptr(q), C.byref(t)))
+        return q, t.value
+
+    def rk_stage(self, stage, t, dt):
+        self._c(self.lib.wadg_rk_stage(self.ctx, stage, t, dt))
+
+    def run_steps(self, nsteps, dt, record=True):
+        out = None
+        if record and getattr(self, "n_probe", 0):
+            out = np.empty((nsteps, self.n_probe, 6, self.n_batch))
+        self._c(self.lib.wadg_run_steps(self.ctx, nsteps, dt, _ptr(out)))
+        return out
+
+    def profile_stage(self, reps, dt):
+        ms = np.zeros(2)
+        self._c(self.lib.wadg_profile_stage(self.ctx, reps, dt, _ptr(ms)))
+        return ms
+
+    def stable_dt(self, cfl=1.0):
+        d = C.c_double()
+        self._c(self.lib.wadg_stable_dt(self.ctx, cfl, C.byref(d)))
+        return d.value
+
+    def objective(self):
+        J = np.empty(self.n_batch)
+        self._c(self.lib.wadg_objective(self.ctx, _ptr(J)))
+        return J
+
+    def memory_report(self):
+        v = [C.c_size_t() for _ in range(4)]
+        self._c(self.lib.wadg_memory_report(self.ctx, *[C.byref(x) for x in v]))
+        return dict(state=v[0].value, pml_coeff=v[1].value, operators=v[2].value,
+                    geometry=v[3].value)
+
+    def synchronize(self):
+        self._c(self.lib.wadg_synchronize(self.ctx))
