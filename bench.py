@@ -183,6 +183,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cube40_n4")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--hex", type=int, default=None,
+                    help="override the cube size of the workload (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--ref-hex", type=int, default=4,
@@ -196,6 +198,8 @@ def main():
 
     from synthetic import workload
     w = workload(args.workload)
+    if args.hex:
+        w = workload(args.workload, n_hex=args.hex)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

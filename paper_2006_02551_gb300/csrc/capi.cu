@@ -194,17 +194,19 @@ template <typename Real>
 wadg_status upload_ops(wadg_ctx* ctx) {
   const RefOps& R = ctx->ref;
   const int Np = R.Np, Nfp = R.Nfp, Nq = R.Nq, NF = 4 * Nfp;
+  // padded, transposed layouts: DrT, DsT, DtT [Np][NpP], LIFTT [NF][NpP],
+  // VqT [Np][NqP], PqT [Nq][NpP] (zeros in the padding)
+  const int NpP = (Np + 3) & ~3, NqP = (Nq + 3) & ~3;
   std::vector<double> h;
-  h.reserve(3 * Np * Np + NF * Np + 2 * Np * Nq);
   for (const std::vector<double>* D : {&R.Dr, &R.Ds, &R.Dt})
     for (int j = 0; j < Np; ++j)
-      for (int i = 0; i < Np; ++i) h.push_back((*D)[i * Np + j]);
+      for (int i = 0; i < NpP; ++i) h.push_back(i < Np ? (*D)[i * Np + j] : 0.0);
   for (int fm = 0; fm < NF; ++fm)
-    for (int i = 0; i < Np; ++i) h.push_back(R.LIFT[(size_t)i * NF + fm]);
+    for (int i = 0; i < NpP; ++i) h.push_back(i < Np ? R.LIFT[(size_t)i * NF + fm] : 0.0);
   for (int j = 0; j < Np; ++j)
-    for (int q = 0; q < Nq; ++q) h.push_back(R.Vq[(size_t)q * Np + j]);
+    for (int q = 0; q < NqP; ++q) h.push_back(q < Nq ? R.Vq[(size_t)q * Np + j] : 0.0);
   for (int q = 0; q < Nq; ++q)
-    for (int i = 0; i < Np; ++i) h.push_back(R.Pq[(size_t)i * Nq + q]);
+    for (int i = 0; i < NpP; ++i) h.push_back(i < Np ? R.Pq[(size_t)i * Nq + q] : 0.0);
   std::vector<Real> hr = cvt<Real>(h);
   CK(dalloc(ctx->ops, hr.size() * sizeof(Real)));
   CK(cudaMemcpy(ctx->ops.p, hr.data(), hr.size() * sizeof(Real), cudaMemcpyHostToDevice));
@@ -335,7 +337,7 @@ wadg_status rebuild_typed(wadg_ctx* ctx) {
     CK(dalloc(dprof, sizeof prof));
     CK(cudaMemcpy(drq.p, rq.data(), rq.size() * 8, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(dprof.p, prof, sizeof prof, cudaMemcpyHostToDevice));
-    const size_t sb = (size_t)ctx->K1 * 3 * Nq * sizeof(Real);
+    const size_t sb = (size_t)ctx->K1 * 3 * ((Nq + 3) & ~3) * sizeof(Real);
     CK(dalloc(ctx->sig, sb));
     if (ctx->kappa) CK(dalloc(ctx->kap, sb));
     CK((launch_pml_samples<Real>(Nq, (int)ctx->K1, (int)ctx->K0, (const double*)ctx->verts.p,

@@ -16,7 +16,9 @@
 // (element, node) or (element, quadrature node) order.
 #include "kernels.cuh"
 
+#include <algorithm>
 #include <cstdio>
+#include <type_traits>
 
 namespace wadg {
 
@@ -26,21 +28,39 @@ struct Dims {
   static constexpr int Nfp = (N + 1) * (N + 2) / 2;
   static constexpr int Nq = (N + 1) * (N + 1) * (N + 1);
   static constexpr int NF = 4 * Nfp;
+  static constexpr int NpP = (Np + 3) & ~3;   // padded to whole quads
+  static constexpr int NqP = (Nq + 3) & ~3;
+  static constexpr int NIQ = NpP / 4;         // node quads
+  static constexpr int NQQ = NqP / 4;         // quadrature-point quads
 };
 
-constexpr int kThreads = 256;
-
+// Launch configuration: persistent blocks, the reference operators staged in
+// shared memory once per block, tiles of T elements processed in a loop.
 template <typename Real, int N, bool PML>
 struct Tile {
   using D = Dims<N>;
-  static constexpr int per_elem_std = 6 * D::Np + 6 * D::NF + 16 + 9;
-  static constexpr int big_pml = (6 * D::NF > 12 * D::Nq) ? 6 * D::NF : 12 * D::Nq;
-  static constexpr int per_elem_pml = 18 * D::Np + big_pml + 16 + 9;
-  static constexpr int per_elem = PML ? per_elem_pml : per_elem_std;
-  static constexpr int budget = 96 * 1024;
-  static constexpr int t0 = budget / (per_elem * (int)sizeof(Real));
-  static constexpr int T = t0 < 1 ? 1 : (t0 > 32 ? 32 : t0);
-  static constexpr size_t smem = (size_t)T * per_elem * sizeof(Real) + 64 * sizeof(int);
+  static constexpr int THREADS = (sizeof(Real) == 4 && PML) ? 512 : 256;
+  static constexpr int CF = PML ? 12 : 6;                  // field components held
+  static constexpr int f_sz = D::Np * CF;                  // F[e][j][CF]
+  static constexpr int u_sz = PML ? ((D::NF * 6 > D::NqP * 12) ? D::NF * 6 : D::NqP * 12)
+                                  : D::NF * 6;             // flux[e][f][6] / tz[e][q][12]
+  static constexpr int r_sz = PML ? D::NpP * 6 : 0;        // rs[e][i][6]
+  static constexpr int per_elem = f_sz + u_sz + r_sz + 16 + 12;
+  // operators: DrT DsT DtT [Np][NpP], LIFTT [NF][NpP] (+ VqT [Np][NqP], PqT [Nq][NpP]);
+  // staged in shared memory when they fit, read through L1 otherwise
+  static constexpr int ops_all = 3 * D::Np * D::NpP + D::NF * D::NpP +
+                                 (PML ? D::Np * D::NqP + D::Nq * D::NpP : 0);
+  static constexpr bool OPS_SMEM = ops_all * (int)sizeof(Real) <= 160 * 1024;
+  static constexpr int ops_sz = OPS_SMEM ? ops_all : 0;
+  static constexpr int budget = (PML || sizeof(Real) == 8) ? 200 * 1024 : 100 * 1024;
+  static constexpr int avail = budget - ops_sz * (int)sizeof(Real) - 256;
+  static constexpr int t0 = avail / (per_elem * (int)sizeof(Real));
+  // enough tiles of work per phase for the block's threads, not more
+  static constexpr int t_tasks = PML ? THREADS / D::NQQ : THREADS / (2 * D::NIQ);
+  static constexpr int t1 = t0 < t_tasks ? t0 : t_tasks;
+  static constexpr int T = t1 < 1 ? 1 : (t1 > 32 ? 32 : t1);
+  static constexpr size_t smem =
+      (size_t)(ops_sz + T * per_elem) * sizeof(Real) + 64 * sizeof(int);
 };
 
 __device__ __forceinline__ double dipole_current(const SrcDev& s, double t) {
@@ -49,92 +69,151 @@ __device__ __forceinline__ double dipole_current(const SrcDev& s, double t) {
   return s.amp * (-(t - s.t0) / (2.0 * tau * tau)) * g;
 }
 
+// global read-only loads of four consecutive values (16-byte aligned)
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
+  float4 t = __ldg(reinterpret_cast<const float4*>(p));
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
+  double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  double2 b = __ldg(reinterpret_cast<const double2*>(p + 2));
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+// shared-memory vector loads
+__device__ __forceinline__ void lds4(const float* p, float* v) {
+  float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void lds4(const double* p, double* v) {
+  double2 a = *reinterpret_cast<const double2*>(p);
+  double2 b = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void sts4(float* p, const float* v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void sts4(double* p, const double* v) {
+  *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+}
+__device__ __forceinline__ void lds2(const float* p, float* v) {
+  float2 t = *reinterpret_cast<const float2*>(p);
+  v[0] = t.x; v[1] = t.y;
+}
+__device__ __forceinline__ void lds2(const double* p, double* v) {
+  double2 t = *reinterpret_cast<const double2*>(p);
+  v[0] = t.x; v[1] = t.y;
+}
+
+// Stage kernel.  Threads work on register tiles: 4 nodes x 3 components x 3
+// reference derivatives (curl), 4 quadrature points x 12 components (V_q),
+// 4 nodes x 4 components (P_q).  All operator reads come from shared memory.
 template <typename Real, int N, bool PML, bool KAPPA>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(Tile<Real, N, PML>::THREADS)
 stage_kernel(const StageParams<Real> P) {
   using D = Dims<N>;
   constexpr int Np = D::Np, Nfp = D::Nfp, Nq = D::Nq, NF = D::NF;
+  constexpr int NpP = D::NpP, NqP = D::NqP, NIQ = D::NIQ, NQQ = D::NQQ;
   using TL = Tile<Real, N, PML>;
-  constexpr int T = TL::T;
+  constexpr int T = TL::T, CF = TL::CF, NT = TL::THREADS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* sm = reinterpret_cast<Real*>(smem_raw);
-  Real* qs = sm;                          // [T][6][Np]
-  Real* ps = qs + T * 6 * Np;             // [T][6][Np]   (PML)
-  Real* rs = ps + (PML ? T * 6 * Np : 0); // [T][6][Np]   (PML)
-  Real* big = rs + (PML ? T * 6 * Np : 0);// flux [T][6][NF] / tz [T][12][Nq]
-  Real* fl = big;
-  Real* nrm = big + T * (PML ? TL::big_pml : 6 * NF);  // [T][4][4]
-  Real* met = nrm + T * 16;                             // [T][9]
-  int* srcl = reinterpret_cast<int*>(met + T * 9);      // [64]
+  const Real* DrT = TL::OPS_SMEM ? sm : P.ops;   // operators
+  const Real* DsT = DrT + Np * NpP;
+  const Real* DtT = DsT + Np * NpP;
+  const Real* LIFTT = DtT + Np * NpP;
+  const Real* VqT = LIFTT + NF * NpP;   // PML only
+  const Real* PqT = VqT + Np * NqP;     // PML only
+  Real* F = sm + TL::ops_sz;         // [T][Np][CF]
+  Real* U = F + T * TL::f_sz;        // flux [T][NF][6] | tz [T][NqP][12]
+  Real* RS = U + T * TL::u_sz;       // [T][NpP][6]
+  Real* nrm = RS + T * TL::r_sz;     // [T][4][4]
+  Real* met = nrm + T * 16;          // [T][12] (9 used)
+  int* srcl = reinterpret_cast<int*>(met + T * 12);
   __shared__ int nsl;
 
-  const Real* DrT = P.ops;
-  const Real* DsT = DrT + Np * Np;
-  const Real* DtT = DsT + Np * Np;
-  const Real* LIFTT = DtT + Np * Np;
-  const Real* VqT = LIFTT + NF * Np;
-  const Real* PqT = VqT + Np * Nq;
   const unsigned char* Fmask = P.tabs;
   const unsigned char* fperm = P.tabs + NF;
-
   const int tid = threadIdx.x;
-  const int b = blockIdx.y;
-  const int t0 = blockIdx.x * T;
-  if (t0 >= P.n_elem) return;
-  const int ne = min(T, P.n_elem - t0);
-  const int eg0 = P.e_begin + t0;           // internal id of the first element
-  const Real* qin = P.qin + (int64_t)b * P.strideQ;
-  Real* qout = P.qout + (int64_t)b * P.strideQ;
-  Real* resq = P.resq + (int64_t)b * P.strideQ;
+
+  // operators -> shared memory, once per block
+  for (int idx = tid; idx < TL::ops_sz / 2; idx += NT) {
+    const Real* src = P.ops + 2 * idx;
+    sm[2 * idx] = src[0];
+    sm[2 * idx + 1] = src[1];
+  }
+  if ((TL::ops_sz & 1) && tid == 0) sm[TL::ops_sz - 1] = P.ops[TL::ops_sz - 1];
+
   const double tbase = P.t_dev ? *P.t_dev : P.t;
   const double tst = tbase + P.rk_c * P.dt;
   const Real rka = (Real)P.rk_a, rkb = (Real)P.rk_b, rdt = (Real)P.dt;
+  const int tiles_per_batch = (P.n_elem + T - 1) / T;
+  const int ntiles = tiles_per_batch * P.nb;
 
-  // ---- phase 0: fields, geometry, sources of this tile
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  const int b = tile / tiles_per_batch;
+  const int t0 = (tile - b * tiles_per_batch) * T;
+  const int ne = min(T, P.n_elem - t0);
+  const int eg0 = P.e_begin + t0;
+  const int ep0 = eg0 - P.K0;
+  const Real* qin = P.qin + (int64_t)b * P.strideQ;
+  Real* qout = P.qout + (int64_t)b * P.strideQ;
+  Real* resq = P.resq + (int64_t)b * P.strideQ;
+  Real* pio = P.p + (int64_t)b * P.strideP;
+  Real* resp = P.resp + (int64_t)b * P.strideP;
+  __syncthreads();   // previous tile done with the shared buffers
+
+  // ---- phase 0: fields (component-fastest), geometry, sources of the tile
   if (tid == 0) nsl = 0;
-  for (int idx = tid; idx < ne * 6 * Np; idx += kThreads)
-    qs[idx] = qin[(int64_t)eg0 * 6 * Np + idx];
-  if (PML) {
-    const Real* pin = P.p + (int64_t)b * P.strideP + (int64_t)(eg0 - P.K0) * 6 * Np;
-    for (int idx = tid; idx < ne * 6 * Np; idx += kThreads) ps[idx] = pin[idx];
+  for (int idx = tid; idx < ne * 6 * Np; idx += NT) {
+    const int e = idx / (6 * Np), r = idx - e * 6 * Np, c = r / Np, j = r - c * Np;
+    F[(e * Np + j) * CF + c] = qin[(int64_t)eg0 * 6 * Np + idx];
   }
-  for (int idx = tid; idx < ne * 4; idx += kThreads) {
-    int e = idx >> 2, f = idx & 3;
+  if (PML) {
+    const Real* pin = pio + (int64_t)ep0 * 6 * Np;
+    for (int idx = tid; idx < ne * 6 * Np; idx += NT) {
+      const int e = idx / (6 * Np), r = idx - e * 6 * Np, c = r / Np, j = r - c * Np;
+      F[(e * Np + j) * CF + 6 + c] = pin[idx];
+    }
+  }
+  for (int idx = tid; idx < ne * 4; idx += NT) {
+    const int e = idx >> 2, f = idx & 3;
     const double* g = P.geo + (int64_t)(eg0 + e) * 9;
     double gx, gy, gz;
     if (f == 0) { gx = -g[6]; gy = -g[7]; gz = -g[8]; }
     else if (f == 1) { gx = -g[3]; gy = -g[4]; gz = -g[5]; }
     else if (f == 2) { gx = g[0] + g[3] + g[6]; gy = g[1] + g[4] + g[7]; gz = g[2] + g[5] + g[8]; }
     else { gx = -g[0]; gy = -g[1]; gz = -g[2]; }
-    double mag = sqrt(gx * gx + gy * gy + gz * gz);
+    const double mag = sqrt(gx * gx + gy * gy + gz * gz);
     Real* nn = nrm + (e * 4 + f) * 4;
     nn[0] = (Real)(gx / mag); nn[1] = (Real)(gy / mag); nn[2] = (Real)(gz / mag);
     nn[3] = (Real)mag;   // Fscale = sJ / J = |grad of the face coordinate|
   }
-  for (int idx = tid; idx < ne * 9; idx += kThreads)
-    met[idx] = (Real)P.geo[(int64_t)eg0 * 9 + idx];
+  for (int idx = tid; idx < ne * 9; idx += NT) {
+    const int e = idx / 9, k = idx - e * 9;
+    met[e * 12 + k] = (Real)P.geo[(int64_t)eg0 * 9 + idx];
+  }
   __syncthreads();
-  for (int s = tid; s < P.nsrc; s += kThreads) {
+  for (int s = tid; s < P.nsrc; s += NT) {
     const SrcDev& sd = P.src[s];
     if (sd.batch == b && sd.elem >= eg0 && sd.elem < eg0 + ne) {
-      int slot = atomicAdd(&nsl, 1);
+      const int slot = atomicAdd(&nsl, 1);
       if (slot < 64) srcl[slot] = s;
     }
   }
 
-  // ---- phase 1: upwind flux at the 4 Nfp trace nodes (scaled by Fscale)
-  for (int idx = tid; idx < ne * NF; idx += kThreads) {
+  // ---- phase 1: upwind flux at the 4 Nfp trace nodes, scaled by Fscale
+  Real* FL = U;   // [T][NF][6]: 0..2 drive E, 3..5 drive H
+  for (int idx = tid; idx < ne * NF; idx += NT) {
     const int e = idx / NF, fm = idx - e * NF;
     const int f = fm / Nfp, m = fm - f * Nfp;
     const int eg = eg0 + e;
     const int ni = Fmask[fm];
     const Real* nn = nrm + (e * 4 + f) * 4;
     const Real nx = nn[0], ny = nn[1], nz = nn[2], fsc = nn[3];
-    Real Em[3], Hm[3], Ep[3], Hp[3];
-    for (int c = 0; c < 3; ++c) {
-      Em[c] = qs[(e * 6 + c) * Np + ni];
-      Hm[c] = qs[(e * 6 + 3 + c) * Np + ni];
-    }
+    const Real* fe = F + (e * Np + ni) * CF;
+    Real Em[3] = {fe[0], fe[1], fe[2]}, Hm[3] = {fe[3], fe[4], fe[5]};
+    Real Ep[3], Hp[3];
     const Real ZM = P.mat[eg * 3 + 2];
     Real ZP = ZM;
     const int nb = P.nbr[eg * 4 + f];
@@ -142,231 +221,333 @@ stage_kernel(const StageParams<Real> P) {
       const int code = P.code[eg * 4 + f];
       const int np2 = fperm[(f * 24 + code) * Nfp + m];
       const Real* qn = qin + (int64_t)nb * 6 * Np + np2;
-      for (int c = 0; c < 3; ++c) {
-        Ep[c] = qn[c * Np];
-        Hp[c] = qn[(3 + c) * Np];
-      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) { Ep[c] = qn[c * Np]; Hp[c] = qn[(3 + c) * Np]; }
       ZP = P.mat[nb * 3 + 2];
     } else {   // perfect electric conductor: mirror state
+#pragma unroll
       for (int c = 0; c < 3; ++c) { Ep[c] = -Em[c]; Hp[c] = Hm[c]; }
     }
     const Real dEx = Ep[0] - Em[0], dEy = Ep[1] - Em[1], dEz = Ep[2] - Em[2];
     const Real dHx = Hp[0] - Hm[0], dHy = Hp[1] - Hm[1], dHz = Hp[2] - Hm[2];
     const Real ndE = nx * dEx + ny * dEy + nz * dEz;
     const Real ndH = nx * dHx + ny * dHy + nz * dHz;
-    // n x dH, n x (n x dE) = n (n.dE) - dE
     const Real cHx = ny * dHz - nz * dHy, cHy = nz * dHx - nx * dHz, cHz = nx * dHy - ny * dHx;
     const Real cEx = ny * dEz - nz * dEy, cEy = nz * dEx - nx * dEz, cEz = nx * dEy - ny * dEx;
     const Real al = (Real)P.alpha;
     const Real YM = Real(1) / ZM, YP = Real(1) / ZP;
     const Real sH = fsc / (ZM + ZP), sE = fsc / (YM + YP);
-    Real* fe = fl + e * 6 * NF + fm;
+    Real* fo = FL + (e * NF + fm) * 6;
     // drives E: (Z+ n x dH - alpha n x (n x dE)) / (Z- + Z+)
-    fe[0 * NF] = sH * (ZP * cHx - al * (nx * ndE - dEx));
-    fe[1 * NF] = sH * (ZP * cHy - al * (ny * ndE - dEy));
-    fe[2 * NF] = sH * (ZP * cHz - al * (nz * ndE - dEz));
+    fo[0] = sH * (ZP * cHx - al * (nx * ndE - dEx));
+    fo[1] = sH * (ZP * cHy - al * (ny * ndE - dEy));
+    fo[2] = sH * (ZP * cHz - al * (nz * ndE - dEz));
     // drives H: (Y+ n x dE + alpha n x (n x dH)) / (Y- + Y+)
-    fe[3 * NF] = sE * (YP * cEx + al * (nx * ndH - dHx));
-    fe[4 * NF] = sE * (YP * cEy + al * (ny * ndH - dHy));
-    fe[5 * NF] = sE * (YP * cEz + al * (nz * ndH - dHz));
+    fo[3] = sE * (YP * cEx + al * (nx * ndH - dHx));
+    fo[4] = sE * (YP * cEy + al * (ny * ndH - dHy));
+    fo[5] = sE * (YP * cEz + al * (nz * ndH - dHz));
   }
   __syncthreads();
   const int nsrc_l = min(nsl, 64);
 
-  // ---- phase 2: volume curl + LIFT  ->  Cbar(H) (E rows), Cbar(E) (H rows)
-  for (int idx = tid; idx < ne * Np; idx += kThreads) {
-    const int e = idx / Np, i = idx - e * Np;
+  // ---- phase 2 (+ phase 3 in PML tiles, same loop: they are independent)
+  //   curl task (e, fld, iq): fld 0: Cbar(E) -> rhs_H = -Cbar(E)/mu,
+  //                           fld 1: Cbar(H) -> rhs_E =  Cbar(H)/eps
+  //   V_q task (e, qq): 12 fields at 4 quadrature points, then eq. 9 pointwise
+  // In PML tiles the V_q results go to TZ, which aliases FL; so the V_q tasks
+  // must not start before every curl task has read FL: they run after a
+  // barrier in the second loop below.
+  const int n2 = ne * 2 * NIQ;
+  for (int task = tid; task < n2; task += NT) {
+    const int e = task / (2 * NIQ), r = task - e * 2 * NIQ, fld = r / NIQ, iq = r - fld * NIQ;
     const int eg = eg0 + e;
-    Real dr[6], ds[6], dt[6];
+    Real d[3][3][4];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) { dr[c] = 0; ds[c] = 0; dt[c] = 0; }
-    const Real* qe = qs + e * 6 * Np;
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int n = 0; n < 4; ++n) d[c][k][n] = 0;
+    const Real* fe = F + e * Np * CF + 3 * fld;
+#pragma unroll 5
     for (int j = 0; j < Np; ++j) {
-      const Real a = DrT[j * Np + i], bb = DsT[j * Np + i], cc = DtT[j * Np + i];
+      Real a[4], bb[4], cc[4];
+      lds4(DrT + j * NpP + 4 * iq, a);
+      lds4(DsT + j * NpP + 4 * iq, bb);
+      lds4(DtT + j * NpP + 4 * iq, cc);
 #pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        const Real v = qe[c * Np + j];
-        dr[c] += a * v; ds[c] += bb * v; dt[c] += cc * v;
+      for (int c = 0; c < 3; ++c) {
+        const Real v = fe[j * CF + c];
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+          d[c][0][n] += a[n] * v;
+          d[c][1][n] += bb[n] * v;
+          d[c][2][n] += cc[n] * v;
+        }
       }
     }
-    const Real* g = met + e * 9;
-    Real dx[6], dy[6], dz[6];
+    Real l[3][4];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
-      dx[c] = g[0] * dr[c] + g[3] * ds[c] + g[6] * dt[c];
-      dy[c] = g[1] * dr[c] + g[4] * ds[c] + g[7] * dt[c];
-      dz[c] = g[2] * dr[c] + g[5] * ds[c] + g[8] * dt[c];
-    }
-    Real lf[6];
+    for (int c = 0; c < 3; ++c)
 #pragma unroll
-    for (int c = 0; c < 6; ++c) lf[c] = 0;
-    const Real* fe = fl + e * 6 * NF;
+      for (int n = 0; n < 4; ++n) l[c][n] = 0;
+    const Real* fl = FL + e * NF * 6 + (fld == 0 ? 3 : 0);
+#pragma unroll 4
     for (int fm = 0; fm < NF; ++fm) {
-      const Real L = LIFTT[fm * Np + i];
+      Real L[4];
+      lds4(LIFTT + fm * NpP + 4 * iq, L);
+      const Real f0 = fl[fm * 6], f1 = fl[fm * 6 + 1], f2 = fl[fm * 6 + 2];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) lf[c] += L * fe[c * NF + fm];
+      for (int n = 0; n < 4; ++n) {
+        l[0][n] += L[n] * f0; l[1][n] += L[n] * f1; l[2][n] += L[n] * f2;
+      }
     }
-    // Cbar(H) = curl H + LIFT flux  (E rows); Cbar(E) = curl E + LIFT flux (H rows)
-    Real CH[3], CE[3];
-    CH[0] = dy[5] - dz[4] + lf[0];
-    CH[1] = dz[3] - dx[5] + lf[1];
-    CH[2] = dx[4] - dy[3] + lf[2];
-    CE[0] = dy[2] - dz[1] + lf[3];
-    CE[1] = dz[0] - dx[2] + lf[4];
-    CE[2] = dx[1] - dy[0] + lf[5];
-    for (int s = 0; s < nsrc_l; ++s) {
-      const SrcDev& sd = P.src[srcl[s]];
-      if (sd.elem != eg) continue;
-      const Real jt = (Real)dipole_current(sd, tst);
-      const Real w = P.src_w[srcl[s] * Np + i];
-      CH[0] -= jt * (Real)sd.dir[0] * w;
-      CH[1] -= jt * (Real)sd.dir[1] * w;
-      CH[2] -= jt * (Real)sd.dir[2] * w;
-    }
+    const Real* g = met + e * 12;
+    const Real rx = g[0], ry = g[1], rz = g[2], sx = g[3], sy = g[4], sz = g[5];
+    const Real tx = g[6], ty = g[7], tz_ = g[8];
     const Real ie = P.mat[eg * 3 + 0], im = P.mat[eg * 3 + 1];
-    Real rhs[6];
-    rhs[0] = ie * CH[0]; rhs[1] = ie * CH[1]; rhs[2] = ie * CH[2];
-    rhs[3] = -im * CE[0]; rhs[4] = -im * CE[1]; rhs[5] = -im * CE[2];
+    Real out[3][4];
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+#define DX(c) (rx * d[c][0][n] + sx * d[c][1][n] + tx * d[c][2][n])
+#define DY(c) (ry * d[c][0][n] + sy * d[c][1][n] + ty * d[c][2][n])
+#define DZ(c) (rz * d[c][0][n] + sz * d[c][1][n] + tz_ * d[c][2][n])
+      const Real c0 = DY(2) - DZ(1) + l[0][n];
+      const Real c1 = DZ(0) - DX(2) + l[1][n];
+      const Real c2 = DX(1) - DY(0) + l[2][n];
+#undef DX
+#undef DY
+#undef DZ
+      if (fld == 0) { out[0][n] = -im * c0; out[1][n] = -im * c1; out[2][n] = -im * c2; }
+      else { out[0][n] = c0; out[1][n] = c1; out[2][n] = c2; }
+    }
+    if (fld == 1) {
+      for (int s = 0; s < nsrc_l; ++s) {
+        const SrcDev& sd = P.src[srcl[s]];
+        if (sd.elem != eg) continue;
+        const Real jt = (Real)dipole_current(sd, tst);
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+          const int i = 4 * iq + n;
+          const Real w = i < Np ? P.src_w[srcl[s] * Np + i] : Real(0);
+#pragma unroll
+          for (int c = 0; c < 3; ++c) out[c][n] -= jt * (Real)sd.dir[c] * w;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int n = 0; n < 4; ++n) out[c][n] *= ie;
+    }
+    const int oc = fld == 0 ? 3 : 0;   // rhs_H lands on components 3..5
     if (!PML) {
 #pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        const int64_t gi = ((int64_t)eg * 6 + c) * Np + i;
-        Real r = rka * resq[gi] + rdt * rhs[c];
-        resq[gi] = r;
-        qout[gi] = qe[c * Np + i] + rkb * r;
-      }
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+          const int i = 4 * iq + n;
+          if (i < Np) {
+            const int64_t gi = ((int64_t)eg * 6 + oc + c) * Np + i;
+            const Real rr = rka * resq[gi] + rdt * out[c][n];
+            resq[gi] = rr;
+            qout[gi] = F[(e * Np + i) * CF + oc + c] + rkb * rr;
+          }
+        }
     } else {
 #pragma unroll
-      for (int c = 0; c < 6; ++c) rs[(e * 6 + c) * Np + i] = rhs[c];
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int n = 0; n < 4; ++n) RS[(e * NpP + 4 * iq + n) * 6 + oc + c] = out[c][n];
     }
   }
-  if (!PML) return;
-  __syncthreads();
+  if (PML) {
+  __syncthreads();   // FL is reused as TZ below
 
-  // ---- phase 3: quadrature-node values and the pointwise CPML terms
-  const int ep0 = eg0 - P.K0;
-  Real* tz = big;  // [T][12][Nq]
+  // ---- phase 3: V_q of the 12 fields at 4 quadrature points; eq. 9 pointwise
+  Real* TZ = U;    // [T][NqP][12]: b VE + c VPE | b VH + c VPH | k^-1 VE - d VPE | k^-1 VH - d VPH
   const Real ie0 = Real(1) / (Real)P.eps0;
-  for (int idx = tid; idx < ne * Nq; idx += kThreads) {
-    const int e = idx / Nq, qp = idx - e * Nq;
-    Real v[12];
+  for (int task = tid; task < ne * NQQ; task += NT) {
+    const int e = task / NQQ, qq = task - e * NQQ;
+    Real v[12][4];
 #pragma unroll
-    for (int c = 0; c < 12; ++c) v[c] = 0;
-    const Real* qe = qs + e * 6 * Np;
-    const Real* pe = ps + e * 6 * Np;
+    for (int c = 0; c < 12; ++c)
+#pragma unroll
+      for (int n = 0; n < 4; ++n) v[c][n] = 0;
+    const Real* fe = F + e * Np * 12;
+#pragma unroll 5
     for (int j = 0; j < Np; ++j) {
-      const Real w = VqT[j * Nq + qp];
+      Real w[4], f[12];
+      lds4(VqT + j * NqP + 4 * qq, w);
+      lds4(fe + j * 12, f);
+      lds4(fe + j * 12 + 4, f + 4);
+      lds4(fe + j * 12 + 8, f + 8);
 #pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        v[c] += w * qe[c * Np + j];
-        v[6 + c] += w * pe[c * Np + j];
-      }
+      for (int c = 0; c < 12; ++c)
+#pragma unroll
+        for (int n = 0; n < 4; ++n) v[c][n] += w[n] * f[c];
     }
-    const Real* sg = P.sig + (int64_t)(ep0 + e) * 3 * Nq + qp;
-    Real sig[3] = {sg[0], sg[Nq], sg[2 * Nq]};
-    Real kap[3] = {Real(1), Real(1), Real(1)};
+    const int64_t sb = (int64_t)(ep0 + e) * 3 * NqP + 4 * qq;
+    Real sg[3][4], kp[3][4];
+    ld4(P.sig + sb, sg[0]);
+    ld4(P.sig + sb + NqP, sg[1]);
+    ld4(P.sig + sb + 2 * NqP, sg[2]);
     if (KAPPA) {
-      const Real* kp = P.kap + (int64_t)(ep0 + e) * 3 * Nq + qp;
-      kap[0] = kp[0]; kap[1] = kp[Nq]; kap[2] = kp[2 * Nq];
-    }
-    Real* tze = tz + e * 12 * Nq + qp;
-#pragma unroll
-    for (int u = 0; u < 3; ++u) {
-      const int vv = (u + 1) % 3, ww = (u + 2) % 3;
-      // eq. 9
-      const Real a = kap[vv] * kap[ww] / kap[u];
-      const Real bc = (sig[vv] * kap[ww] + sig[ww] * kap[vv] - a * sig[u]) / kap[u] * ie0;
-      const Real cc = sig[vv] * sig[ww] * ie0 * ie0 - bc * sig[u] * ie0;
-      const Real dd = sig[u] / kap[u] * ie0;
-      const Real ki = Real(1) / kap[u];
-      tze[u * Nq] = bc * v[u] + cc * v[6 + u];                   // E:  b V E + c V P^E
-      tze[(3 + u) * Nq] = bc * v[3 + u] + cc * v[9 + u];         // H:  b V H + c V P^H
-      tze[(6 + u) * Nq] = ki * v[u] - dd * v[6 + u];             // P^E: k^-1 V E - d V P^E
-      tze[(9 + u) * Nq] = ki * v[3 + u] - dd * v[9 + u];         // P^H
-    }
-  }
-  __syncthreads();
-
-  // ---- phase 4: projections P_q; finish eqs. 26-29 (kappa = 1) or P^E, P^H
-  Real* pout = P.p + (int64_t)b * P.strideP;
-  Real* resp = P.resp + (int64_t)b * P.strideP;
-  for (int idx = tid; idx < ne * Np; idx += kThreads) {
-    const int e = idx / Np, i = idx - e * Np;
-    const int eg = eg0 + e;
-    Real s[12];
-#pragma unroll
-    for (int c = 0; c < 12; ++c) s[c] = 0;
-    const Real* tze = tz + e * 12 * Nq;
-    for (int qp = 0; qp < Nq; ++qp) {
-      const Real w = PqT[qp * Np + i];
-#pragma unroll
-      for (int c = 0; c < 12; ++c) s[c] += w * tze[c * Nq + qp];
+      ld4(P.kap + sb, kp[0]);
+      ld4(P.kap + sb + NqP, kp[1]);
+      ld4(P.kap + sb + 2 * NqP, kp[2]);
     }
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
-      const Real wv = rs[(e * 6 + c) * Np + i] - s[c];
-      if (!KAPPA) {
-        const int64_t gi = ((int64_t)eg * 6 + c) * Np + i;
-        Real r = rka * resq[gi] + rdt * wv;
-        resq[gi] = r;
-        qout[gi] = qs[(e * 6 + c) * Np + i] + rkb * r;
-      } else {
-        rs[(e * 6 + c) * Np + i] = wv;
+    for (int n = 0; n < 4; ++n) {
+      Real* tzo = TZ + (e * NqP + 4 * qq + n) * 12;
+      Real o[12];
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int vv = (u + 1) % 3, ww = (u + 2) % 3;
+        const Real ku = KAPPA ? kp[u][n] : Real(1), kv = KAPPA ? kp[vv][n] : Real(1);
+        const Real kw = KAPPA ? kp[ww][n] : Real(1);
+        const Real su = sg[u][n], sv = sg[vv][n], sw = sg[ww][n];
+        // eq. 9
+        const Real a = kv * kw / ku;
+        const Real bc = (sv * kw + sw * kv - a * su) / ku * ie0;
+        const Real cc = sv * sw * ie0 * ie0 - bc * su * ie0;
+        const Real dd = su / ku * ie0;
+        const Real ki = Real(1) / ku;
+        o[u] = bc * v[u][n] + cc * v[6 + u][n];
+        o[3 + u] = bc * v[3 + u][n] + cc * v[9 + u][n];
+        o[6 + u] = ki * v[u][n] - dd * v[6 + u][n];
+        o[9 + u] = ki * v[3 + u][n] - dd * v[9 + u][n];
       }
-      const int64_t pi = ((int64_t)(eg - P.K0) * 6 + c) * Np + i;
-      Real r = rka * resp[pi] + rdt * s[6 + c];
-      resp[pi] = r;
-      pout[pi] = ps[(e * 6 + c) * Np + i] + rkb * r;
+#pragma unroll
+      for (int c = 0; c < 12; c += 4) sts4(tzo + c, o + c);
     }
   }
-  if (!KAPPA) return;
   __syncthreads();
 
-  // ---- phase 5: a^{-1} V_q applied to (Cbar/eps - s), kappa != 1
-  for (int idx = tid; idx < ne * Nq; idx += kThreads) {
-    const int e = idx / Nq, qp = idx - e * Nq;
-    Real v[6];
+  // ---- phase 4: P_q back to the nodes, 4 nodes x 4 of the 12 components:
+  //   components 0..5 give s (E,H), 6..11 the right-hand side of P^E, P^H
+  for (int task = tid; task < ne * 3 * NIQ; task += NT) {
+    const int e = task / (3 * NIQ), r = task - e * 3 * NIQ, cg = r / NIQ, iq = r - cg * NIQ;
+    const int eg = eg0 + e;
+    Real s[4][4];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) v[c] = 0;
-    const Real* re = rs + e * 6 * Np;
-    for (int j = 0; j < Np; ++j) {
-      const Real w = VqT[j * Nq + qp];
+    for (int c = 0; c < 4; ++c)
 #pragma unroll
-      for (int c = 0; c < 6; ++c) v[c] += w * re[c * Np + j];
+      for (int n = 0; n < 4; ++n) s[c][n] = 0;
+    const Real* tze = TZ + e * NqP * 12 + 4 * cg;
+#pragma unroll 5
+    for (int q = 0; q < Nq; ++q) {
+      Real w[4], t4[4];
+      lds4(PqT + q * NpP + 4 * iq, w);
+      lds4(tze + q * 12, t4);
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int n = 0; n < 4; ++n) s[c][n] += w[n] * t4[c];
     }
-    const Real* kp = P.kap + (int64_t)(ep0 + e) * 3 * Nq + qp;
-    Real kap[3] = {kp[0], kp[Nq], kp[2 * Nq]};
-    Real* tze = tz + e * 12 * Nq + qp;
 #pragma unroll
-    for (int u = 0; u < 3; ++u) {
-      const Real ainv = kap[u] / (kap[(u + 1) % 3] * kap[(u + 2) % 3]);
-      tze[u * Nq] = ainv * v[u];
-      tze[(3 + u) * Nq] = ainv * v[3 + u];
+    for (int n = 0; n < 4; ++n) {
+      const int i = 4 * iq + n;
+      if (i >= Np) continue;
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        const int c = 4 * cg + cc;
+        if (c < 6) {
+          const Real wv = RS[(e * NpP + i) * 6 + c] - s[cc][n];
+          if (!KAPPA) {
+            const int64_t gi = ((int64_t)eg * 6 + c) * Np + i;
+            const Real rr = rka * resq[gi] + rdt * wv;
+            resq[gi] = rr;
+            qout[gi] = F[(e * Np + i) * 12 + c] + rkb * rr;
+          } else {
+            RS[(e * NpP + i) * 6 + c] = wv;
+          }
+        } else {
+          const int64_t pi = ((int64_t)(eg - P.K0) * 6 + c - 6) * Np + i;
+          const Real rr = rka * resp[pi] + rdt * s[cc][n];
+          resp[pi] = rr;
+          pio[pi] = F[(e * Np + i) * 12 + c] + rkb * rr;
+        }
+      }
+    }
+  }
+  if (KAPPA) {
+  __syncthreads();
+
+  // ---- phase 5: a^{-1} V_q (Cbar/eps - s) at the quadrature points
+  for (int task = tid; task < ne * NQQ; task += NT) {
+    const int e = task / NQQ, qq = task - e * NQQ;
+    Real v[6][4];
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+#pragma unroll
+      for (int n = 0; n < 4; ++n) v[c][n] = 0;
+    const Real* re = RS + e * NpP * 6;
+    for (int j = 0; j < Np; ++j) {
+      Real w[4], f[6];
+      lds4(VqT + j * NqP + 4 * qq, w);
+      lds2(re + j * 6, f);
+      lds2(re + j * 6 + 2, f + 2);
+      lds2(re + j * 6 + 4, f + 4);
+#pragma unroll
+      for (int c = 0; c < 6; ++c)
+#pragma unroll
+        for (int n = 0; n < 4; ++n) v[c][n] += w[n] * f[c];
+    }
+    const int64_t sb = (int64_t)(ep0 + e) * 3 * NqP + 4 * qq;
+    Real kp[3][4];
+    ld4(P.kap + sb, kp[0]);
+    ld4(P.kap + sb + NqP, kp[1]);
+    ld4(P.kap + sb + 2 * NqP, kp[2]);
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+      Real* tzo = TZ + (e * NqP + 4 * qq + n) * 12;
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const Real ainv = kp[u][n] / (kp[(u + 1) % 3][n] * kp[(u + 2) % 3][n]);
+        tzo[u] = ainv * v[u][n];
+        tzo[3 + u] = ainv * v[3 + u][n];
+      }
     }
   }
   __syncthreads();
 
   // ---- phase 6: P_q back to the nodes, E/H update
-  for (int idx = tid; idx < ne * Np; idx += kThreads) {
-    const int e = idx / Np, i = idx - e * Np;
+  for (int task = tid; task < ne * NIQ; task += NT) {
+    const int e = task / NIQ, iq = task - e * NIQ;
     const int eg = eg0 + e;
-    Real s[6];
+    Real s[6][4];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) s[c] = 0;
-    const Real* tze = tz + e * 12 * Nq;
-    for (int qp = 0; qp < Nq; ++qp) {
-      const Real w = PqT[qp * Np + i];
+    for (int c = 0; c < 6; ++c)
 #pragma unroll
-      for (int c = 0; c < 6; ++c) s[c] += w * tze[c * Nq + qp];
+      for (int n = 0; n < 4; ++n) s[c][n] = 0;
+    const Real* tze = TZ + e * NqP * 12;
+    for (int q = 0; q < Nq; ++q) {
+      Real w[4], t6[6];
+      lds4(PqT + q * NpP + 4 * iq, w);
+      lds2(tze + q * 12, t6);
+      lds2(tze + q * 12 + 2, t6 + 2);
+      lds2(tze + q * 12 + 4, t6 + 4);
+#pragma unroll
+      for (int c = 0; c < 6; ++c)
+#pragma unroll
+        for (int n = 0; n < 4; ++n) s[c][n] += w[n] * t6[c];
     }
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
-      const int64_t gi = ((int64_t)eg * 6 + c) * Np + i;
-      Real r = rka * resq[gi] + rdt * s[c];
-      resq[gi] = r;
-      qout[gi] = qs[(e * 6 + c) * Np + i] + rkb * r;
+    for (int n = 0; n < 4; ++n) {
+      const int i = 4 * iq + n;
+      if (i >= Np) continue;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        const int64_t gi = ((int64_t)eg * 6 + c) * Np + i;
+        const Real rr = rka * resq[gi] + rdt * s[c][n];
+        resq[gi] = rr;
+        qout[gi] = F[(e * Np + i) * 12 + c] + rkb * rr;
+      }
     }
   }
+  }  // KAPPA
+  }  // PML
+  }  // tile loop
 }
 
 template <typename Real, int N, bool PML, bool KAPPA>
@@ -376,12 +557,33 @@ static cudaError_t configure_one() {
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL::smem);
 }
 
+// resident blocks per SM of one stage-kernel instance (cached per instance)
+template <typename Real, int N, bool PML, bool KAPPA>
+static int resident_blocks() {
+  static int cached = 0;
+  if (cached == 0) {
+    using TL = Tile<Real, N, PML>;
+    int nb = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stage_kernel<Real, N, PML, KAPPA>,
+                                                      TL::THREADS, TL::smem) != cudaSuccess ||
+        nb < 1)
+      nb = 1;
+    cached = nb * (sms > 0 ? sms : 1);
+  }
+  return cached;
+}
+
 template <typename Real, int N, bool PML, bool KAPPA>
 static cudaError_t launch_one(const StageParams<Real>& P, int nb, cudaStream_t s) {
   using TL = Tile<Real, N, PML>;
   if (P.n_elem <= 0) return cudaSuccess;
-  dim3 grid((P.n_elem + TL::T - 1) / TL::T, nb);
-  stage_kernel<Real, N, PML, KAPPA><<<grid, kThreads, TL::smem, s>>>(P);
+  StageParams<Real> Q = P;
+  Q.nb = nb;
+  const long long tiles = (long long)((P.n_elem + TL::T - 1) / TL::T) * nb;
+  const int grid = (int)std::min<long long>(tiles, resident_blocks<Real, N, PML, KAPPA>());
+  stage_kernel<Real, N, PML, KAPPA><<<grid, TL::THREADS, TL::smem, s>>>(Q);
   return cudaGetLastError();
 }
 
@@ -478,12 +680,19 @@ cudaError_t launch_advance(double* t_dev, int64_t* step_dev, double dt, cudaStre
 // sigma_u, kappa_u at the quadrature nodes of every PML element, in double.
 // prof: u0[3], L[3], sigma_max[3], p_sigma[3], kappa_max[3], eps0
 template <typename Real>
-__global__ void pml_samples_kernel(int Nq, int K1, int K0, const double* verts,
+__global__ void pml_samples_kernel(int Nq, int NqP, int K1, int K0, const double* verts,
                                    const double* rq, const double* prof, Real* sig,
                                    Real* kap) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)K1 * Nq) return;
-  const int e = (int)(idx / Nq), q = (int)(idx - (int64_t)e * Nq);
+  if (idx >= (int64_t)K1 * NqP) return;
+  const int e = (int)(idx / NqP), q = (int)(idx - (int64_t)e * NqP);
+  if (q >= Nq) {   // padding of the quadrature axis
+    for (int u = 0; u < 3; ++u) {
+      sig[((int64_t)e * 3 + u) * NqP + q] = Real(0);
+      if (kap) kap[((int64_t)e * 3 + u) * NqP + q] = Real(1);
+    }
+    return;
+  }
   const double* v = verts + (int64_t)(K0 + e) * 12;
   const double r = rq[q * 3], s = rq[q * 3 + 1], t = rq[q * 3 + 2];
   const double l0 = -0.5 * (1 + r + s + t), l1 = 0.5 * (1 + r), l2 = 0.5 * (1 + s),
@@ -493,19 +702,20 @@ __global__ void pml_samples_kernel(int Nq, int K1, int K0, const double* verts,
     const double d = (fabs(x) - prof[u]) / prof[3 + u];
     double g = 0.0;
     if (d > 0) g = pow(d, prof[9 + u]);
-    sig[((int64_t)e * 3 + u) * Nq + q] = (Real)(prof[6 + u] * g);
-    if (kap) kap[((int64_t)e * 3 + u) * Nq + q] = (Real)(1.0 + (prof[12 + u] - 1.0) * g);
+    sig[((int64_t)e * 3 + u) * NqP + q] = (Real)(prof[6 + u] * g);
+    if (kap) kap[((int64_t)e * 3 + u) * NqP + q] = (Real)(1.0 + (prof[12 + u] - 1.0) * g);
   }
 }
 
 template <typename Real>
 cudaError_t launch_pml_samples(int Nq, int K1, int K0, const double* verts, const double* rq,
                                const double* prof, Real* sig, Real* kap, cudaStream_t s) {
-  const int64_t n = (int64_t)K1 * Nq;
+  const int NqP = (Nq + 3) & ~3;
+  const int64_t n = (int64_t)K1 * NqP;
   if (n == 0) return cudaSuccess;
   const int th = 256;
-  pml_samples_kernel<Real><<<(unsigned)((n + th - 1) / th), th, 0, s>>>(Nq, K1, K0, verts, rq,
-                                                                       prof, sig, kap);
+  pml_samples_kernel<Real><<<(unsigned)((n + th - 1) / th), th, 0, s>>>(Nq, NqP, K1, K0, verts,
+                                                                       rq, prof, sig, kap);
   return cudaGetLastError();
 }
 template cudaError_t launch_pml_samples<double>(int, int, int, const double*, const double*,

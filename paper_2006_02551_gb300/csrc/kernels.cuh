@@ -44,6 +44,7 @@ struct StageParams {
   int K0;                   // first PML element (internal id)
   int e_begin;              // first element of this launch's class
   int n_elem;               // elements of this launch's class
+  int nb;                   // excitations (set by the launcher)
   int nsrc;
   const SrcDev* src;
   const Real* src_w;        // [nsrc][Np]: M_k^{-1} l(r_s)
