@@ -182,14 +182,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cube40_n4")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="tf32", choices=["fp32", "fp64", "tf32"])
     ap.add_argument("--hex", type=int, default=None,
                     help="override the cube size of the workload (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--ref-hex", type=int, default=4,
                     help="cube size of the oracle sample for --impl reference")
-    ap.add_argument("--cpu-hex", type=int, default=10,
+    ap.add_argument("--cpu-hex", type=int, default=12,
                     help="cube size of the oracle sample for the cpu_baseline entry")
     args = ap.parse_args()
     args.metric = "DOF-updates/s (WADG-PML DGTD, N=4), mixed-precision vs FP64 at stated L2 error"
@@ -267,22 +267,33 @@ def main():
                    cost["flops_pml"] * K1 * w.n_batch)}
     dom = max(per, key=lambda k: per[k][0])
     d_ms, d_bytes, d_flops = per[dom]
-    if args.precision == "fp64":
-        peak = FP64_PEAK_TFLOPS
-        peak_note = "nominal GB300 FP64 (1.25 TFLOP/s)"
-    else:
-        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-        peak_note = "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
     achieved = d_flops / (d_ms * 1e-3) / 1e12
-    hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
-        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": f"stage_kernel<{dom}>",
-                "peak_source": peak_note,
-                "hbm": {"achieved_gbs": d_bytes / (d_ms * 1e-3) / 1e9, "peak_gbs": hbm,
-                        "frac": d_bytes / (d_ms * 1e-3) / 1e9 / hbm},
-                "kernel_ms": {"std": kms[0], "pml": kms[1]},
-                "bytes_per_launch": d_bytes, "flops_per_launch": d_flops}
+    achieved_gbs = d_bytes / (d_ms * 1e-3) / 1e9
+    if args.precision == "tf32":
+        # tensor-core contractions: the stage is bound by HBM traffic
+        roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved_gbs / hbm, "traffic": None,
+                    "kernel": f"tc_stage_kernel<{dom}>",
+                    "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                    "alu": {"achieved_tflops": achieved}}
+    else:
+        if args.precision == "fp64":
+            peak = FP64_PEAK_TFLOPS
+            peak_note = "nominal GB300 FP64 (1.25 TFLOP/s)"
+        else:
+            peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+            peak_note = "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None, "kernel": f"stage_kernel<{dom}>",
+                    "peak_source": peak_note,
+                    "hbm": {"achieved_gbs": achieved_gbs, "peak_gbs": hbm,
+                            "frac": achieved_gbs / hbm}}
+    roofline.update({"kernel_ms": {"std": kms[0], "pml": kms[1]},
+                     "bytes_per_launch": d_bytes, "flops_per_launch": d_flops})
 
     # end to end through the public API with host buffers
     rec_bytes = len(w.probes) * 6 * w.n_batch * 8
@@ -299,28 +310,45 @@ def main():
 
     mem = s.memory_report()
     out_extra = {}
-    # accuracy of this precision against the FP64 path, and the FP64 rate
-    if args.precision != "fp64" and not args.no_fp64 and rank == 0:
+    # accuracy against the FP64 path over the same steps, and the other rates
+    if not args.no_fp64 and rank == 0:
         nst = 20
         s.set_state(None, 0.0)
         s.run_steps(nst, dt, record=False)
-        q32, _ = s.get_state()
+        q_main, _ = s.get_state()
         s.close()
-        s64 = setup_solver(w, "fp64", sh, local)
-        s64.run_steps(3, dt, record=False)
-        s64.set_state(None, 0.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        s64.run_steps(nst, dt, record=False)
-        e1.record(stream)
-        e1.synchronize()
-        q64, _ = s64.get_state()
-        ms64 = e0.elapsed_time(e1) / nst
-        s64.close()
+        others = {}
+        for prec in ("fp64", "fp32"):
+            if prec == args.precision:
+                continue
+            so = setup_solver(w, prec, sh, local)
+            nrate = 20 if prec == "fp64" else 200
+            so.run_steps(3, dt, record=False)
+            so.set_state(None, 0.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            so.run_steps(nrate, dt, record=False)
+            e1.record(stream)
+            e1.synchronize()
+            mso = e0.elapsed_time(e1) / nrate
+            so.set_state(None, 0.0)
+            so.run_steps(nst, dt, record=False)
+            qo, _ = so.get_state()
+            so.close()
+            others[prec] = ({"value": dofs / (mso * 1e-3), "ms_per_step": mso}, qo)
         sel = (slice(None), slice(None), slice(0, 6))
-        l2 = float(np.linalg.norm(q32[sel] - q64[sel]) / np.linalg.norm(q64[sel]))
-        out_extra["accuracy"] = {"l2_rel_vs_fp64": l2, "fields": "E,H", "steps": nst}
-        out_extra["fp64"] = {"value": dofs / (ms64 * 1e-3), "ms_per_step": ms64}
+        if "fp64" in others:
+            q64 = others["fp64"][1]
+            acc = {"fields": "E,H", "steps": nst, "reference": "FP64 path on the GPU",
+                   f"l2_rel_{args.precision}_vs_fp64":
+                       float(np.linalg.norm(q_main[sel] - q64[sel]) / np.linalg.norm(q64[sel]))}
+            if "fp32" in others:
+                q32 = others["fp32"][1]
+                acc["l2_rel_fp32_vs_fp64"] = float(np.linalg.norm(q32[sel] - q64[sel]) /
+                                                   np.linalg.norm(q64[sel]))
+            out_extra["accuracy"] = acc
+        for prec, (rate, _) in others.items():
+            out_extra[prec] = rate
     else:
         s.close()
 
@@ -338,7 +366,8 @@ def main():
         line = {"metric": args.metric, "value": value, "unit": "DOF-updates/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32" if rs == 4 else "f64",
+                "vs_baseline": None,
+                "dtype": {"fp32": "f32", "fp64": "f64", "tf32": "tf32 x tf32 -> f32"}[args.precision],
                 "data": "synthetic",
                 "config": {"workload": describe(w), "K": K, "K_pml": K1, "N": N, "Np": Np,
                            "Nq": Nq, "dofs_per_step": dofs, "precision": args.precision,

@@ -81,7 +81,8 @@ struct wadg_ctx {
 
   // device
   DevPtr q[2], rq, p, rp, geo, mat, nbr, code, sig, kap, ops, tabs, verts;
-  DevPtr src, srcw, pr_elem, pr_ell, pr_out, obj, tdev, stepdev, flag;
+  DevPtr src, srcw, pr_elem, pr_ell, pr_out, obj, tdev, stepdev, flag, tcops, errflag;
+  bool tc = false;   // tensor-core stage kernels (TF32)
   int cur = 0;
   int nsrc = 0, nprobe = 0;
   std::vector<wadg_dipole> src_user;
@@ -215,6 +216,26 @@ wadg_status upload_ops(wadg_ctx* ctx) {
   for (int i = 0; i < 4 * 24 * Nfp; ++i) t[NF + i] = (unsigned char)std::max(R.fperm[i], 0);
   CK(dalloc(ctx->tabs, t.size()));
   CK(cudaMemcpy(ctx->tabs.p, t.data(), t.size(), cudaMemcpyHostToDevice));
+  if (ctx->tc) {
+    // row-major Dr | Ds | Dt [Np][Np], LIFT [Np][NF], Vq [Nq][Np], Pq [Np][Nq],
+    // rounded to TF32 (nearest, ties away from zero)
+    std::vector<float> tf;
+    auto push = [&](double v) {
+      float f = (float)v;
+      uint32_t u;
+      std::memcpy(&u, &f, 4);
+      u = (u + 0x1000u) & 0xFFFFE000u;
+      std::memcpy(&f, &u, 4);
+      tf.push_back(f);
+    };
+    for (const std::vector<double>* D : {&R.Dr, &R.Ds, &R.Dt})
+      for (double v : *D) push(v);
+    for (double v : R.LIFT) push(v);
+    for (double v : R.Vq) push(v);
+    for (double v : R.Pq) push(v);
+    CK(dalloc(ctx->tcops, tf.size() * 4));
+    CK(cudaMemcpy(ctx->tcops.p, tf.data(), tf.size() * 4, cudaMemcpyHostToDevice));
+  }
   return WADG_OK;
 }
 
@@ -458,11 +479,23 @@ StageParams<Real> stage_params(wadg_ctx* ctx, int stage, double dt, double t, bo
   P.t_dev = use_tdev ? (const double*)ctx->tdev.p : nullptr;
   P.eps0 = ctx->has_prof ? ctx->prof.eps0 : 1.0;
   P.alpha = 1.0;
+  P.tcops = ctx->tcops.p;
+  P.err = (int*)ctx->errflag.p;
   return P;
 }
 
 template <typename Real>
 wadg_status issue_stage(wadg_ctx* ctx, int stage, double dt, double t, bool use_tdev) {
+  if (ctx->tc) {
+    StageParams<float> A = stage_params<float>(ctx, stage, dt, t, use_tdev, false);
+    CK(launch_stage_tc(ctx->N, false, A, ctx->nb, ctx->stream));
+    if (ctx->K1 > 0) {
+      StageParams<float> B = stage_params<float>(ctx, stage, dt, t, use_tdev, true);
+      CK(launch_stage_tc(ctx->N, true, B, ctx->nb, ctx->stream));
+    }
+    ctx->cur ^= 1;
+    return WADG_OK;
+  }
   StageParams<Real> A = stage_params<Real>(ctx, stage, dt, t, use_tdev, false);
   CK(launch_stage<Real>(ctx->N, false, false, A, ctx->nb, ctx->stream));
   if (ctx->K1 > 0) {
@@ -515,6 +548,18 @@ wadg_status capture_graphs(wadg_ctx* ctx, double dt) {
   ctx->cur = start;
   ctx->graph_dt = dt;
   ctx->graph_valid = true;
+  return WADG_OK;
+}
+
+// bounded device waits that gave up leave a flag behind
+wadg_status check_err_flag(wadg_ctx* ctx) {
+  int e = 0;
+  CK(cudaMemcpyAsync(&e, ctx->errflag.p, 4, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (e) {
+    CK(cudaMemset(ctx->errflag.p, 0, 4));
+    return fail(ctx, WADG_ETIMEOUT, "a tensor-core stage kernel gave up waiting for its products");
+  }
   return WADG_OK;
 }
 
@@ -591,11 +636,13 @@ wadg_status wadg_create(int N, wadg_precision prec, int32_t n_batch, int device,
   if (!out) return fail(nullptr, WADG_EINVAL, "out is NULL");
   *out = nullptr;
   if (N < 1 || N > 5) return fail(nullptr, WADG_EINVAL, "N must be in 1..5 (got %d)", N);
-  if (prec != WADG_FP64 && prec != WADG_FP32) {
-    if (prec == WADG_TF32 || prec == WADG_BF16)
+  if (prec != WADG_FP64 && prec != WADG_FP32 && prec != WADG_TF32) {
+    if (prec == WADG_BF16)
       return fail(nullptr, WADG_EUNSUPPORTED, "precision %d not available in this build", prec);
     return fail(nullptr, WADG_EINVAL, "unknown precision %d", prec);
   }
+  if (prec == WADG_TF32 && !tc_supported(N, false))
+    return fail(nullptr, WADG_EUNSUPPORTED, "TF32 tensor-core stage is built for N <= 4");
   if (n_batch < 1) return fail(nullptr, WADG_EINVAL, "n_batch must be >= 1");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
@@ -608,6 +655,7 @@ wadg_status wadg_create(int N, wadg_precision prec, int32_t n_batch, int device,
   ctx->nb = n_batch;
   ctx->device = device;
   ctx->rs = prec == WADG_FP64 ? 8 : 4;
+  ctx->tc = prec == WADG_TF32;
   const char* e = nullptr;
   if (!build_ref_ops(N, ctx->ref, &e)) {
     delete ctx;
@@ -626,6 +674,7 @@ wadg_status wadg_create(int N, wadg_precision prec, int32_t n_batch, int device,
   if (s == WADG_OK) {
     cudaError_t ce = ctx->rs == 8 ? configure_stage_kernels<double>(N)
                                   : configure_stage_kernels<float>(N);
+    if (ce == cudaSuccess && ctx->tc) ce = configure_tc_kernels(N);
     if (ce != cudaSuccess) s = fail(ctx, WADG_ECUDA, "kernel set-up: %s", cudaGetErrorString(ce));
   }
   if (s == WADG_OK) {
@@ -633,6 +682,8 @@ wadg_status wadg_create(int N, wadg_precision prec, int32_t n_batch, int device,
     if (ce == cudaSuccess) ce = dalloc(ctx->tdev, 8);
     if (ce == cudaSuccess) ce = dalloc(ctx->stepdev, 8);
     if (ce == cudaSuccess) ce = dalloc(ctx->flag, 4);
+    if (ce == cudaSuccess) ce = dalloc(ctx->errflag, 4);
+    if (ce == cudaSuccess) ce = cudaMemset(ctx->errflag.p, 0, 4);
     if (ce == cudaSuccess) ce = dalloc(ctx->obj, 8 * (size_t)n_batch);
     if (ce == cudaSuccess) ce = cudaMemset(ctx->obj.p, 0, 8 * (size_t)n_batch);
     if (ce != cudaSuccess) s = fail(nullptr, WADG_ECUDA, "%s", cudaGetErrorString(ce));
@@ -655,7 +706,8 @@ wadg_status wadg_destroy(wadg_ctx* ctx) {
   for (DevPtr* d : {&ctx->q[0], &ctx->q[1], &ctx->rq, &ctx->p, &ctx->rp, &ctx->geo, &ctx->mat,
                     &ctx->nbr, &ctx->code, &ctx->sig, &ctx->kap, &ctx->ops, &ctx->tabs,
                     &ctx->verts, &ctx->src, &ctx->srcw, &ctx->pr_elem, &ctx->pr_ell,
-                    &ctx->pr_out, &ctx->obj, &ctx->tdev, &ctx->stepdev, &ctx->flag})
+                    &ctx->pr_out, &ctx->obj, &ctx->tdev, &ctx->stepdev, &ctx->flag,
+                    &ctx->tcops, &ctx->errflag})
     dfree(*d);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
@@ -806,11 +858,14 @@ wadg_status wadg_set_pml_profile(wadg_ctx* ctx, const wadg_pml_profile* prof,
         return fail(ctx, WADG_EINVAL, "bad PML profile on axis %d", u);
     }
     if (!(prof->eps0 > 0)) return fail(ctx, WADG_EINVAL, "eps0 must be positive");
+    bool kap = false;
+    for (int u = 0; u < 3; ++u)
+      if (prof->kappa_max[u] != 1.0) kap = true;
+    if (kap && ctx->tc)
+      return fail(ctx, WADG_EUNSUPPORTED, "kappa_max != 1 is not built for the TF32 stage");
     ctx->has_prof = true;
     ctx->prof = *prof;
-    ctx->kappa = false;
-    for (int u = 0; u < 3; ++u)
-      if (prof->kappa_max[u] != 1.0) ctx->kappa = true;
+    ctx->kappa = kap;
   } else {
     ctx->has_prof = false;
     ctx->kappa = false;
@@ -869,8 +924,10 @@ wadg_status wadg_rk_stage(wadg_ctx* ctx, int stage, double t, double dt) {
   if (s != WADG_OK) return s;
   if (stage < 0 || stage > 4) return fail(ctx, WADG_EINVAL, "stage must be 0..4");
   cudaSetDevice(ctx->device);
-  return ctx->rs == 8 ? issue_stage<double>(ctx, stage, dt, t, false)
-                      : issue_stage<float>(ctx, stage, dt, t, false);
+  s = ctx->rs == 8 ? issue_stage<double>(ctx, stage, dt, t, false)
+                   : issue_stage<float>(ctx, stage, dt, t, false);
+  if (s != WADG_OK || !ctx->tc) return s;
+  return check_err_flag(ctx);
 }
 
 wadg_status wadg_run_steps(wadg_ctx* ctx, int64_t nsteps, double dt, double* probe_out) {
@@ -917,7 +974,7 @@ wadg_status wadg_run_steps(wadg_ctx* ctx, int64_t nsteps, double dt, double* pro
   CK(cudaMemcpyAsync(&flag, ctx->flag.p, 4, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   if (flag) return fail(ctx, WADG_ENONFINITE, "state became non-finite");
-  return WADG_OK;
+  return check_err_flag(ctx);
 }
 
 wadg_status wadg_profile_stage(wadg_ctx* ctx, int reps, double dt, double* ms_out) {
@@ -933,7 +990,10 @@ wadg_status wadg_profile_stage(wadg_ctx* ctx, int reps, double dt, double* ms_ou
     for (int cls = 0; cls < 2; ++cls) {
       if (cls == 1 && ctx->K1 == 0) continue;
       CK(cudaEventRecord(ev[2 * cls], ctx->stream));
-      if (ctx->rs == 8) {
+      if (ctx->tc) {
+        StageParams<float> P = stage_params<float>(ctx, stage, dt, ctx->t, false, cls == 1);
+        CK(launch_stage_tc(ctx->N, cls == 1, P, ctx->nb, ctx->stream));
+      } else if (ctx->rs == 8) {
         StageParams<double> P = stage_params<double>(ctx, stage, dt, ctx->t, false, cls == 1);
         CK(launch_stage<double>(ctx->N, cls == 1, ctx->kappa, P, ctx->nb, ctx->stream));
       } else {

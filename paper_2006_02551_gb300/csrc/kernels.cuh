@@ -53,6 +53,8 @@ struct StageParams {
   const double* t_dev;      // device base time (graph replays)
   double eps0;
   double alpha;             // flux upwinding (1 upwind, 0 central)
+  const void* tcops;        // tensor-core operator tables (TF32 path)
+  int* err;                 // device error flag (bounded waits that gave up)
 };
 
 struct ProbeParams {
@@ -73,6 +75,10 @@ template <typename Real>
 cudaError_t launch_stage(int N, bool pml, bool kappa, const StageParams<Real>& P, int nb,
                          cudaStream_t s);
 cudaError_t launch_probes(bool fp64, const ProbeParams& P, cudaStream_t s);
+// tensor-core (tcgen05, TF32) stage kernels
+bool tc_supported(int N, bool kappa);
+cudaError_t configure_tc_kernels(int N);
+cudaError_t launch_stage_tc(int N, bool pml, const StageParams<float>& P, int nb, cudaStream_t s);
 cudaError_t launch_advance(double* t_dev, int64_t* step_dev, double dt, cudaStream_t s);
 template <typename Real>
 cudaError_t launch_pml_samples(int Nq, int K1, int K0, const double* verts,

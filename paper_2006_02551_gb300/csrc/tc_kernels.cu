@@ -1,0 +1,761 @@
+// Tensor-core stage kernels for sm_103a (tcgen05, TF32 operands, FP32
+// accumulation in tensor memory, FP32 field state).
+//
+// Every reference-element contraction of the stage is one matrix product
+//     D[row][(e,c)] = sum_k A[row][k] * B[(e,c)][k]
+// with the operator as A (rows = output node or quadrature point, which
+// become TMEM lanes) and the tile's field data as B (one row per
+// (element, component) pair, K-major), so each thread of the epilogue owns one
+// node / quadrature point of every element of the tile:
+//   volume  : A = Dr, Ds, Dt  (Np x Np)   B = E,H           -> d/dr, d/ds, d/dt
+//   LIFT    : A = LIFT (Np x 4Nfp)        B = scaled flux   -> surface term
+//   PML     : A = V_q (Nq x Np)           B = E,H,P^E,P^H   -> values at x_q
+//             A = P_q (Np x Nq)           B = (t, z) at x_q -> s, rhs of P
+// (eqs. 16, 17, 20, 21, 26-29).  The upwind flux, the metric chain rule,
+// eq. 9 at the quadrature points and the Runge-Kutta update run on the CUDA
+// cores between the products.  Operand tiles use the K-major canonical
+// layout without swizzle: 8-row x 16-byte core matrices, K-adjacent core
+// matrices 128 B apart (LBO), 8-row groups SBO apart.  M = 128 always;
+// operators with fewer rows are stored with their real rows only and the
+// rows the instruction reads beyond them fall on later shared-memory buffers
+// (their lanes are never read back).
+//
+// Waits on the MMA-completion mbarrier are bounded; on timeout the kernel
+// records an error and stops after releasing its tensor memory.
+#include "kernels.cuh"
+
+#include <algorithm>
+#include <cstdint>
+
+namespace wadg {
+namespace tc {
+
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte
+// offsets, fixed 0b001 at bits 46-48, no swizzle
+__device__ __forceinline__ uint64_t make_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((addr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16;
+  d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  return d;
+}
+
+// instruction descriptor, kind::tf32: D f32, A and B tf32, both K-major
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+      : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait for the given phase parity
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
+  for (int i = 0; i < (1 << 22); ++i)
+    if (mbar_try_wait(a, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// this thread's lane of 2 / 4 consecutive TMEM columns (load and wait fused so
+// the registers are valid when the statement ends)
+__device__ __forceinline__ void tld2(uint32_t taddr, float* v) {
+  uint32_t r0, r1;
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r0), "=r"(r1)
+      : "r"(taddr)
+      : "memory");
+  v[0] = __uint_as_float(r0);
+  v[1] = __uint_as_float(r1);
+}
+__device__ __forceinline__ void tld4(uint32_t taddr, float* v) {
+  uint32_t r0, r1, r2, r3;
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+      : "r"(taddr)
+      : "memory");
+  v[0] = __uint_as_float(r0);
+  v[1] = __uint_as_float(r1);
+  v[2] = __uint_as_float(r2);
+  v[3] = __uint_as_float(r3);
+}
+__device__ __forceinline__ void tld6(uint32_t taddr, float* v) {
+  tld4(taddr, v);
+  tld2(taddr + 4, v + 4);
+}
+
+// 6 consecutive columns at each of two / four column addresses, one wait
+__device__ __forceinline__ void tld_6x2(uint32_t a0, uint32_t a1, float* v) {
+  uint32_t r[12];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%12];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%4, %5}, [%13];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%6, %7, %8, %9}, [%14];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%10, %11}, [%15];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11])
+      : "r"(a0), "r"(a0 + 4), "r"(a1), "r"(a1 + 4)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 12; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tld_6x4(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                        float* v) {
+  tld_6x2(a0, a1, v);
+  tld_6x2(a2, a3, v + 12);
+}
+
+// 4-byte asynchronous global -> shared copies
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(saddr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// byte offset of (row r, k) in a K-major canonical tile: 8-row x 16-byte core
+// matrices, K-adjacent core matrices lbo bytes apart, 8-row groups sbo apart.
+// The field operands use lbo = 144 (one 16-byte gap per core matrix) so that
+// consecutive K written by consecutive lanes fall on distinct banks.
+__host__ __device__ constexpr uint32_t cofs(int r, int k, uint32_t sbo, uint32_t lbo) {
+  return static_cast<uint32_t>(r >> 3) * sbo + static_cast<uint32_t>(k >> 2) * lbo +
+         static_cast<uint32_t>(r & 7) * 16u + static_cast<uint32_t>(k & 3) * 4u;
+}
+
+constexpr int rup8(int x) { return (x + 7) & ~7; }
+constexpr int rup16(int x) { return (x + 15) & ~15; }
+
+// Shared-memory plan of one tile (all offsets in bytes).
+template <int N, bool PML>
+struct Plan {
+  static constexpr int Np = (N + 1) * (N + 2) * (N + 3) / 6;
+  static constexpr int Nfp = (N + 1) * (N + 2) / 2;
+  static constexpr int NF = 4 * Nfp;
+  static constexpr int Nq = (N + 1) * (N + 1) * (N + 1);
+  static constexpr int NpK = rup8(Np), NFK = rup8(NF), NqK = rup8(Nq);
+  static constexpr int T = 8;                        // elements per tile
+  static constexpr int NV = rup16(6 * T);            // columns of E,H products
+  static constexpr int NQ = rup16(12 * T);           // columns of 12-component products
+  static constexpr int G_p = NpK / 8;                // 8-row groups of an Np-row operator
+  static constexpr uint32_t LA = 128, LB = 144;      // K strides of operator / field tiles
+  static constexpr uint32_t SBO_V = (NpK / 4) * LA;  // operators, K = Np
+  static constexpr uint32_t SBO_L = (NFK / 4) * LA;  // K = 4 Nfp
+  static constexpr uint32_t SBO_Q = (NqK / 4) * LA;  // K = Nq
+  static constexpr uint32_t SBB_V = (NpK / 4) * LB;  // field tiles
+  static constexpr uint32_t SBB_L = (NFK / 4) * LB;
+  static constexpr uint32_t SBB_Q = (NqK / 4) * LB;
+  // A operands
+  static constexpr uint32_t oPq = 0;
+  static constexpr uint32_t oL = PML ? oPq + G_p * SBO_Q : 0;
+  static constexpr uint32_t oDr = oL + G_p * SBO_L;
+  static constexpr uint32_t oDs = oDr + G_p * SBO_V;
+  static constexpr uint32_t oDt = oDs + G_p * SBO_V;
+  static constexpr uint32_t oVq = oDt + G_p * SBO_V;
+  // B operands
+  static constexpr uint32_t oBF = PML ? oVq + 16 * SBO_V : oVq;
+  static constexpr int ROWS_F = PML ? NQ : NV;        // E,H (+ P) rows
+  static constexpr uint32_t oBFL = oBF + (ROWS_F / 8) * SBB_V;
+  static constexpr uint32_t oBTZ = oBFL + (NV / 8) * SBB_L;
+  static constexpr uint32_t oRS = PML ? oBTZ + (NQ / 8) * SBB_Q : oBTZ;
+  static constexpr int NpP = (Np + 3) & ~3;
+  static constexpr uint32_t oGeo = oRS + (PML ? T * 6 * NpP * 4 : 0);
+  static constexpr int TS = T * 6 * Np;               // floats of one staged field block
+  static constexpr uint32_t TSB = (TS * 4 + 15) & ~15;
+  static constexpr uint32_t SET = (PML ? 4 : 2) * TSB;  // q, res (+ P, res of P)
+  static constexpr uint32_t oST = oGeo + 2 * T * 28 * 4;  // two staging sets
+  static constexpr uint32_t oMisc = oST + 2 * SET;
+  static constexpr uint32_t bytes_used = oMisc + 64 * 4 + 64;
+  // residency follows the tensor-memory budget of 512 columns per SM: one PML
+  // block (512 columns) or two non-PML blocks (256 each) per SM, enforced by
+  // the shared-memory request so that no block waits in tcgen05.alloc
+  static constexpr uint32_t min_bytes = PML ? 116 * 1024 : 100 * 1024;
+  static constexpr uint32_t bytes = bytes_used < min_bytes ? min_bytes : bytes_used;
+  static constexpr uint32_t TMEM_COLS = PML ? 512 : 256;
+  // TMEM column bases
+  static constexpr uint32_t cDr = 0, cDs = NV, cDt = 2 * NV, cL = 3 * NV;
+  static constexpr uint32_t cVq = 4 * NV, cPq = 4 * NV + NQ;
+  static_assert(!PML || 4 * NV + 2 * NQ <= 512, "TMEM columns");
+  static_assert(PML || 4 * NV <= 256, "TMEM columns");
+  static_assert(Nq <= 128 || !PML, "V_q rows must fit one M=128 tile");
+  static_assert(Np <= 64, "node rows");
+  // every A operand read (128 rows from its start) stays inside the block
+  static_assert(oPq + 16 * SBO_Q <= bytes || !PML, "P_q span");
+  static_assert(oL + 16 * SBO_L <= bytes, "LIFT span");
+  static_assert(oDt + 16 * SBO_V <= bytes, "Dt span");
+  static_assert(bytes <= 227 * 1024, "shared memory");
+};
+
+constexpr int kTcThreads = 256;
+
+template <int N, bool PML>
+__global__ void __launch_bounds__(kTcThreads, 1) tc_stage_kernel(const StageParams<float> P) {
+  using PL = Plan<N, PML>;
+  constexpr int Np = PL::Np, Nfp = PL::Nfp, NF = PL::NF, Nq = PL::Nq, T = PL::T;
+  constexpr int NpK = PL::NpK, NFK = PL::NFK, NqK = PL::NqK, NpP = PL::NpP;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int quad = warp & 3, half = warp >> 2;   // TMEM lane quadrant, element half
+  const uint32_t sbase = saddr(smem);
+  float* RS = reinterpret_cast<float*>(smem + PL::oRS);     // [T][6][NpP]
+  float* geo = reinterpret_cast<float*>(smem + PL::oGeo);   // [2][T][28]: n,Fscale x4 | metric
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + PL::oMisc);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + PL::oMisc + 8);
+  int* flags = reinterpret_cast<int*>(smem + PL::oMisc + 16);   // [0] source count
+  int* srcl = reinterpret_cast<int*>(smem + PL::oMisc + 64);
+  const float* tops = reinterpret_cast<const float*>(P.tcops);
+  const unsigned char* Fmask = P.tabs;
+  const unsigned char* fperm = P.tabs + NF;
+
+  // ---- prologue: zero the operand buffers, stage the operators
+  for (uint32_t i = tid; i < PL::oGeo / 16; i += kTcThreads)
+    reinterpret_cast<float4*>(smem)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  __syncthreads();
+  {
+    // tcops layout: Dr | Ds | Dt [Np][Np], LIFT [Np][NF], Vq [Nq][Np], Pq [Np][Nq]
+    const float* gDr = tops;
+    const float* gL = gDr + 3 * Np * Np;
+    const float* gVq = gL + Np * NF;
+    const float* gPq = gVq + Nq * Np;
+    for (int idx = tid; idx < 3 * Np * Np; idx += kTcThreads) {
+      const int d = idx / (Np * Np), r = idx - d * Np * Np, i = r / Np, j = r - i * Np;
+      const uint32_t base = d == 0 ? PL::oDr : (d == 1 ? PL::oDs : PL::oDt);
+      *reinterpret_cast<float*>(smem + base + cofs(i, j, PL::SBO_V, PL::LA)) = gDr[idx];
+    }
+    for (int idx = tid; idx < Np * NF; idx += kTcThreads) {
+      const int i = idx / NF, f = idx - i * NF;
+      *reinterpret_cast<float*>(smem + PL::oL + cofs(i, f, PL::SBO_L, PL::LA)) = gL[idx];
+    }
+    if (PML) {
+      for (int idx = tid; idx < Nq * Np; idx += kTcThreads) {
+        const int q = idx / Np, j = idx - q * Np;
+        *reinterpret_cast<float*>(smem + PL::oVq + cofs(q, j, PL::SBO_V, PL::LA)) = gVq[idx];
+      }
+      for (int idx = tid; idx < Np * Nq; idx += kTcThreads) {
+        const int i = idx / Nq, q = idx - i * Nq;
+        *reinterpret_cast<float*>(smem + PL::oPq + cofs(i, q, PL::SBO_Q, PL::LA)) = gPq[idx];
+      }
+    }
+  }
+  if (tid == 0) {
+    mbar_init(saddr(mbar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(saddr(tmem_slot), PL::TMEM_COLS);
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t lane_base = static_cast<uint32_t>(quad * 32) << 16;
+  uint32_t phase = 0;
+  bool failed = false;
+
+  const double tbase = P.t_dev ? *P.t_dev : P.t;
+  const double tst = tbase + P.rk_c * P.dt;
+  const float rka = (float)P.rk_a, rkb = (float)P.rk_b, rdt = (float)P.dt;
+  const int tiles_per_batch = (P.n_elem + T - 1) / T;
+  const int ntiles = tiles_per_batch * P.nb;
+
+  constexpr int FT = (T * NF + kTcThreads - 1) / kTcThreads;   // flux tasks per thread
+
+  // copies of one tile's contiguous field blocks into staging set `set`
+  auto stage_tile = [&](int tile, int set) {
+    const int b = tile / tiles_per_batch;
+    const int t0 = (tile - b * tiles_per_batch) * T;
+    const int ne = min(T, P.n_elem - t0);
+    const int eg0 = P.e_begin + t0;
+    const int nval = ne * 6 * Np;
+    unsigned char* st = smem + PL::oST + set * PL::SET;
+    float* sq = reinterpret_cast<float*>(st);
+    float* sr = reinterpret_cast<float*>(st + PL::TSB);
+    const float* gq = P.qin + (int64_t)b * P.strideQ + (int64_t)eg0 * 6 * Np;
+    const float* gr = P.resq + (int64_t)b * P.strideQ + (int64_t)eg0 * 6 * Np;
+    for (int idx = tid; idx < nval; idx += kTcThreads) {
+      cp_async4(sq + idx, gq + idx);
+      cp_async4(sr + idx, gr + idx);
+    }
+    if (PML) {
+      float* sp = reinterpret_cast<float*>(st + 2 * PL::TSB);
+      float* srp = reinterpret_cast<float*>(st + 3 * PL::TSB);
+      const float* gp = P.p + (int64_t)b * P.strideP + (int64_t)(eg0 - P.K0) * 6 * Np;
+      const float* grp = P.resp + (int64_t)b * P.strideP + (int64_t)(eg0 - P.K0) * 6 * Np;
+      for (int idx = tid; idx < nval; idx += kTcThreads) {
+        cp_async4(sp + idx, gp + idx);
+        cp_async4(srp + idx, grp + idx);
+      }
+    }
+  };
+  if ((int)blockIdx.x < ntiles) stage_tile(blockIdx.x, 0);
+  asm volatile("cp.async.commit_group;" ::: "memory");
+
+  // per-tile scattered loads (neighbour traces, sigma samples, geometry),
+  // issued one tile ahead so their latency overlaps the previous tile's work
+  constexpr int NqP = (Nq + 3) & ~3;
+  constexpr int EH = (T + 1) / 2;
+  auto load_nbr = [&](int tile, float (&Ep)[FT][3], float (&Hp)[FT][3], float (&ZPv)[FT]) {
+    const int b = tile / tiles_per_batch;
+    const int t0 = (tile - b * tiles_per_batch) * T;
+    const int ne = min(T, P.n_elem - t0);
+    const int eg0 = P.e_begin + t0;
+    const float* qin = P.qin + (int64_t)b * P.strideQ;
+#pragma unroll
+    for (int u = 0; u < FT; ++u) {
+      const int task = tid + u * kTcThreads;
+      ZPv[u] = 0.f;
+      if (task < ne * NF) {
+        const int e = task / NF, fm = task - e * NF;
+        const int f = fm / Nfp, m = fm - f * Nfp;
+        const int eg = eg0 + e;
+        const int nb = P.nbr[eg * 4 + f];
+        if (nb >= 0) {
+          const int code = P.code[eg * 4 + f];
+          const int np2 = fperm[(f * 24 + code) * Nfp + m];
+          const float* qn = qin + (int64_t)nb * 6 * Np + np2;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) { Ep[u][c] = qn[c * Np]; Hp[u][c] = qn[(3 + c) * Np]; }
+          ZPv[u] = P.mat[nb * 3 + 2];
+        } else {
+          ZPv[u] = -1.f;   // marks the PEC mirror
+#pragma unroll
+          for (int c = 0; c < 3; ++c) { Ep[u][c] = 0.f; Hp[u][c] = 0.f; }
+        }
+      }
+    }
+  };
+  auto load_sig = [&](int tile, float (&sgv)[PML ? EH : 1][3]) {
+    if (!PML) return;
+    const int b = tile / tiles_per_batch;
+    const int t0 = (tile - b * tiles_per_batch) * T;
+    const int ne = min(T, P.n_elem - t0);
+    const int ep0 = P.e_begin + t0 - P.K0;
+    const int q = quad * 32 + lane;
+#pragma unroll
+    for (int k = 0; k < (PML ? EH : 1); ++k) {
+      const int e = half + 2 * k;
+      sgv[k][0] = sgv[k][1] = sgv[k][2] = 0.f;
+      if (e < ne && q < Nq) {
+        const int64_t sb = (int64_t)(ep0 + e) * 3 * NqP + q;
+        sgv[k][0] = P.sig[sb];
+        sgv[k][1] = P.sig[sb + NqP];
+        sgv[k][2] = P.sig[sb + 2 * NqP];
+      }
+    }
+  };
+  auto load_geo = [&](int tile, float* gb) {
+    const int b = tile / tiles_per_batch;
+    const int t0 = (tile - b * tiles_per_batch) * T;
+    const int ne = min(T, P.n_elem - t0);
+    const int eg0 = P.e_begin + t0;
+    for (int idx = tid; idx < ne * 4; idx += kTcThreads) {
+      const int e = idx >> 2, f = idx & 3;
+      const double* g = P.geo + (int64_t)(eg0 + e) * 9;
+      double gx, gy, gz;
+      if (f == 0) { gx = -g[6]; gy = -g[7]; gz = -g[8]; }
+      else if (f == 1) { gx = -g[3]; gy = -g[4]; gz = -g[5]; }
+      else if (f == 2) { gx = g[0] + g[3] + g[6]; gy = g[1] + g[4] + g[7]; gz = g[2] + g[5] + g[8]; }
+      else { gx = -g[0]; gy = -g[1]; gz = -g[2]; }
+      const double mag = sqrt(gx * gx + gy * gy + gz * gz);
+      float* nn = gb + e * 28 + f * 4;
+      nn[0] = (float)(gx / mag); nn[1] = (float)(gy / mag); nn[2] = (float)(gz / mag);
+      nn[3] = (float)mag;
+    }
+    for (int idx = tid; idx < ne * 9; idx += kTcThreads) {
+      const int e = idx / 9, k = idx - e * 9;
+      gb[e * 28 + 16 + k] = (float)P.geo[(int64_t)eg0 * 9 + idx];
+    }
+  };
+  float Ep[FT][3], Hp[FT][3], ZPv[FT];
+  float sgv[PML ? EH : 1][3];
+  if ((int)blockIdx.x < ntiles) {
+    load_nbr(blockIdx.x, Ep, Hp, ZPv);
+    load_sig(blockIdx.x, sgv);
+    load_geo(blockIdx.x, geo);
+  }
+
+  int it = 0;
+  for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x, ++it) {
+    const int set = it & 1;
+    const int next = tile + gridDim.x;
+    unsigned char* stg = smem + PL::oST + set * PL::SET;
+    float* SQ = reinterpret_cast<float*>(stg);
+    float* SR = reinterpret_cast<float*>(stg + PL::TSB);
+    float* SP = reinterpret_cast<float*>(stg + 2 * PL::TSB);
+    float* SRP = reinterpret_cast<float*>(stg + 3 * PL::TSB);
+    float* geo = reinterpret_cast<float*>(smem + PL::oGeo) + set * T * 28;
+    float* geo_next = reinterpret_cast<float*>(smem + PL::oGeo) + (set ^ 1) * T * 28;
+    // the next tile's blocks stream in while this one is processed
+    if (next < ntiles) stage_tile(next, set ^ 1);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    const int b = tile / tiles_per_batch;
+    const int t0 = (tile - b * tiles_per_batch) * T;
+    const int ne = min(T, P.n_elem - t0);
+    const int eg0 = P.e_begin + t0;
+    const int ep0 = eg0 - P.K0;
+    const int nval = ne * 6 * Np;
+    float* qout = P.qout + (int64_t)b * P.strideQ;
+    float* resq = P.resq + (int64_t)b * P.strideQ;
+    float* pio = P.p + (int64_t)b * P.strideP;
+    float* resp = P.resp + (int64_t)b * P.strideP;
+
+    if (tid == 0) flags[0] = 0;
+    asm volatile("cp.async.wait_group 1;" ::: "memory");   // this tile's copies landed
+    __syncthreads();
+    for (int s = tid; s < P.nsrc; s += kTcThreads) {
+      const SrcDev& sd = P.src[s];
+      if (sd.batch == b && sd.elem >= eg0 && sd.elem < eg0 + ne) {
+        const int slot = atomicAdd(&flags[0], 1);
+        if (slot < 64) srcl[slot] = s;
+      }
+    }
+    // ---- B operand of the field products (TF32-rounded), from the staged blocks
+    for (int idx = tid; idx < nval; idx += kTcThreads) {
+      const int e = idx / (6 * Np), r = idx - e * 6 * Np, c = r / Np, j = r - c * Np;
+      *reinterpret_cast<float*>(smem + PL::oBF + cofs(e * 6 + c, j, PL::SBB_V, PL::LB)) = to_tf32(SQ[idx]);
+      if (PML)
+        *reinterpret_cast<float*>(smem + PL::oBF + cofs(6 * T + e * 6 + c, j, PL::SBB_V, PL::LB)) =
+            to_tf32(SP[idx]);
+    }
+    // ---- upwind flux, scaled by Fscale, into the B operand of LIFT
+#pragma unroll
+    for (int u = 0; u < FT; ++u) {
+      const int task = tid + u * kTcThreads;
+      if (task >= ne * NF) continue;
+      const int e = task / NF, fm = task - e * NF;
+      const int f = fm / Nfp;
+      const int eg = eg0 + e;
+      const int ni = Fmask[fm];
+      const float* nn = geo + e * 28 + f * 4;
+      const float nx = nn[0], ny = nn[1], nz = nn[2], fsc = nn[3];
+      const float* sq = SQ + e * 6 * Np + ni;
+      float Em[3], Hm[3], Eo[3], Ho[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) { Em[c] = sq[c * Np]; Hm[c] = sq[(3 + c) * Np]; }
+      const float ZM = P.mat[eg * 3 + 2];
+      float ZP = ZPv[u];
+      if (ZP < 0.f) {   // perfect electric conductor: mirror state
+        ZP = ZM;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) { Eo[c] = -Em[c]; Ho[c] = Hm[c]; }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) { Eo[c] = Ep[u][c]; Ho[c] = Hp[u][c]; }
+      }
+      const float dEx = Eo[0] - Em[0], dEy = Eo[1] - Em[1], dEz = Eo[2] - Em[2];
+      const float dHx = Ho[0] - Hm[0], dHy = Ho[1] - Hm[1], dHz = Ho[2] - Hm[2];
+      const float ndE = nx * dEx + ny * dEy + nz * dEz;
+      const float ndH = nx * dHx + ny * dHy + nz * dHz;
+      const float cHx = ny * dHz - nz * dHy, cHy = nz * dHx - nx * dHz, cHz = nx * dHy - ny * dHx;
+      const float cEx = ny * dEz - nz * dEy, cEy = nz * dEx - nx * dEz, cEz = nx * dEy - ny * dEx;
+      const float al = (float)P.alpha;
+      const float YM = 1.f / ZM, YP = 1.f / ZP;
+      const float sH = fsc / (ZM + ZP), sE = fsc / (YM + YP);
+      float fo[6];
+      fo[0] = sH * (ZP * cHx - al * (nx * ndE - dEx));
+      fo[1] = sH * (ZP * cHy - al * (ny * ndE - dEy));
+      fo[2] = sH * (ZP * cHz - al * (nz * ndE - dEz));
+      fo[3] = sE * (YP * cEx + al * (nx * ndH - dHx));
+      fo[4] = sE * (YP * cEy + al * (ny * ndH - dHy));
+      fo[5] = sE * (YP * cEz + al * (nz * ndH - dHz));
+#pragma unroll
+      for (int c = 0; c < 6; ++c)
+        *reinterpret_cast<float*>(smem + PL::oBFL + cofs(e * 6 + c, fm, PL::SBB_L, PL::LB)) =
+            to_tf32(fo[c]);
+    }
+    if (next < ntiles) {
+      load_nbr(next, Ep, Hp, ZPv);
+      load_geo(next, geo_next);
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+
+    // ---- products: volume (3), LIFT, V_q
+    if (tid == 0) {
+      constexpr uint32_t idV = idesc_tf32(128, PL::NV);
+      for (int d = 0; d < 3; ++d) {
+        const uint32_t oa = d == 0 ? PL::oDr : (d == 1 ? PL::oDs : PL::oDt);
+        const uint32_t col = d == 0 ? PL::cDr : (d == 1 ? PL::cDs : PL::cDt);
+        for (int k = 0; k < NpK / 8; ++k)
+          mma_tf32(tmem + col, make_desc(sbase + oa + 256 * k, 128, PL::SBO_V),
+                   make_desc(sbase + PL::oBF + 2 * PL::LB * k, PL::LB, PL::SBB_V), idV, k > 0);
+      }
+      for (int k = 0; k < NFK / 8; ++k)
+        mma_tf32(tmem + PL::cL, make_desc(sbase + PL::oL + 256 * k, 128, PL::SBO_L),
+                 make_desc(sbase + PL::oBFL + 2 * PL::LB * k, PL::LB, PL::SBB_L), idV, k > 0);
+      if (PML) {
+        constexpr uint32_t idQ = idesc_tf32(128, PL::NQ);
+        for (int k = 0; k < NpK / 8; ++k)
+          mma_tf32(tmem + PL::cVq, make_desc(sbase + PL::oVq + 256 * k, 128, PL::SBO_V),
+                   make_desc(sbase + PL::oBF + 2 * PL::LB * k, PL::LB, PL::SBB_V), idQ, k > 0);
+      }
+      mma_commit(saddr(mbar));
+    }
+    bool ok = mbar_wait(saddr(mbar), phase);
+    phase ^= 1;
+    if (!__syncthreads_and(ok)) { failed = true; break; }
+    fence_after();
+    const int nsrc_l = min(flags[0], 64);
+
+    // ---- epilogue A1 (PML): eq. 9 at the quadrature points -> B of P_q
+    if (PML) {
+      const int q = quad * 32 + lane;     // quadrature point of this lane
+      const float ie0 = 1.f / (float)P.eps0;
+#pragma unroll
+      for (int k = 0; k < EH; ++k) {       // warp-uniform loop over this half's elements
+        const int e = half + 2 * k;
+        if (e >= T) break;
+        float v[12];
+        tld_6x2(tmem + lane_base + PL::cVq + e * 6, tmem + lane_base + PL::cVq + 6 * T + e * 6, v);
+        if (e >= ne || q >= NqK) continue;
+        const float* sg = sgv[k];
+        float o[12];
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          const float su = sg[u], sv = sg[(u + 1) % 3], sw = sg[(u + 2) % 3];
+          // eq. 9 with kappa = 1: a = 1, b = (sv + sw - su)/eps0, c = sv sw/eps0^2 - b su/eps0
+          const float bc = (sv + sw - su) * ie0;
+          const float cc = sv * sw * ie0 * ie0 - bc * su * ie0;
+          const float dd = su * ie0;
+          o[u] = bc * v[u] + cc * v[6 + u];
+          o[3 + u] = bc * v[3 + u] + cc * v[9 + u];
+          o[6 + u] = v[u] - dd * v[6 + u];
+          o[9 + u] = v[3 + u] - dd * v[9 + u];
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          *reinterpret_cast<float*>(smem + PL::oBTZ + cofs(e * 6 + c, q, PL::SBB_Q, PL::LB)) =
+              to_tf32(o[c]);
+          *reinterpret_cast<float*>(smem + PL::oBTZ + cofs(6 * T + e * 6 + c, q, PL::SBB_Q, PL::LB)) =
+              to_tf32(o[6 + c]);
+        }
+      }
+    }
+
+    if (next < ntiles) load_sig(next, sgv);
+
+    // ---- epilogue A2: curl + LIFT at node i = lane of quadrants 0..(Np-1)/32
+    if (quad * 32 < Np) {
+      const int i = quad * 32 + lane;
+      for (int e = half; e < T; e += 2) {
+        float d[24];   // dr | ds | dt | lift, 6 components each
+        tld_6x4(tmem + lane_base + PL::cDr + e * 6, tmem + lane_base + PL::cDs + e * 6,
+                tmem + lane_base + PL::cDt + e * 6, tmem + lane_base + PL::cL + e * 6, d);
+        if (e >= ne || i >= Np) continue;
+        const int eg = eg0 + e;
+        const float* g = geo + e * 28 + 16;
+        float dx[6], dy[6], dz[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          dx[c] = g[0] * d[c] + g[3] * d[6 + c] + g[6] * d[12 + c];
+          dy[c] = g[1] * d[c] + g[4] * d[6 + c] + g[7] * d[12 + c];
+          dz[c] = g[2] * d[c] + g[5] * d[6 + c] + g[8] * d[12 + c];
+        }
+        const float* lf = d + 18;
+        // Cbar(H) (E rows) and Cbar(E) (H rows)
+        float CH[3], CE[3];
+        CH[0] = dy[5] - dz[4] + lf[0];
+        CH[1] = dz[3] - dx[5] + lf[1];
+        CH[2] = dx[4] - dy[3] + lf[2];
+        CE[0] = dy[2] - dz[1] + lf[3];
+        CE[1] = dz[0] - dx[2] + lf[4];
+        CE[2] = dx[1] - dy[0] + lf[5];
+        for (int s = 0; s < nsrc_l; ++s) {
+          const SrcDev& sd = P.src[srcl[s]];
+          if (sd.elem != eg) continue;
+          const double tau = sd.width;
+          const double gg = exp(-(tst - sd.t0) * (tst - sd.t0) / (4.0 * tau * tau));
+          const float jt = (float)(sd.amp * (-(tst - sd.t0) / (2.0 * tau * tau)) * gg);
+          const float w = P.src_w[srcl[s] * Np + i];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) CH[c] -= jt * (float)sd.dir[c] * w;
+        }
+        const float ie = P.mat[eg * 3 + 0], im = P.mat[eg * 3 + 1];
+        float rhs[6] = {ie * CH[0], ie * CH[1], ie * CH[2], -im * CE[0], -im * CE[1], -im * CE[2]};
+        if (!PML) {
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            const int li = (e * 6 + c) * Np + i;
+            const int64_t gi = (int64_t)eg0 * 6 * Np + li;
+            const float rr = rka * SR[li] + rdt * rhs[c];
+            resq[gi] = rr;
+            qout[gi] = SQ[li] + rkb * rr;
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < 6; ++c) RS[(e * 6 + c) * NpP + i] = rhs[c];
+        }
+      }
+    }
+
+    if (PML) {
+      // ---- P_q product
+      fence_async_smem();
+      fence_before();
+      __syncthreads();
+      fence_after();
+      if (tid == 0) {
+        constexpr uint32_t idQ = idesc_tf32(128, PL::NQ);
+        for (int k = 0; k < NqK / 8; ++k)
+          mma_tf32(tmem + PL::cPq, make_desc(sbase + PL::oPq + 256 * k, 128, PL::SBO_Q),
+                   make_desc(sbase + PL::oBTZ + 2 * PL::LB * k, PL::LB, PL::SBB_Q), idQ, k > 0);
+        mma_commit(saddr(mbar));
+      }
+      ok = mbar_wait(saddr(mbar), phase);
+      phase ^= 1;
+      if (!__syncthreads_and(ok)) { failed = true; break; }
+      fence_after();
+      // ---- epilogue B: s, rhs of P; Runge-Kutta update of E, H, P^E, P^H
+      if (quad * 32 < Np) {
+        const int i = quad * 32 + lane;
+        for (int e = half; e < T; e += 2) {
+          float v[12];   // s | rhs of P
+          tld_6x2(tmem + lane_base + PL::cPq + e * 6, tmem + lane_base + PL::cPq + 6 * T + e * 6, v);
+          if (e >= ne || i >= Np) continue;
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            const int li = (e * 6 + c) * Np + i;
+            const int64_t gi = (int64_t)eg0 * 6 * Np + li;
+            const float rr = rka * SR[li] + rdt * (RS[(e * 6 + c) * NpP + i] - v[c]);
+            resq[gi] = rr;
+            qout[gi] = SQ[li] + rkb * rr;
+            const int64_t pi = (int64_t)ep0 * 6 * Np + li;
+            const float rp = rka * SRP[li] + rdt * v[6 + c];
+            resp[pi] = rp;
+            pio[pi] = SP[li] + rkb * rp;
+          }
+        }
+      }
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+  }
+
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  if (failed) {
+    if (tid == 0) atomicExch(P.err, 1);
+    // let any product still in flight finish before the memory is released
+    mbar_wait(saddr(mbar), phase);
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0) tmem_dealloc(tmem, PL::TMEM_COLS);
+}
+
+template <int N, bool PML>
+cudaError_t configure_n() {
+  return cudaFuncSetAttribute(tc_stage_kernel<N, PML>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)Plan<N, PML>::bytes);
+}
+
+template <int N, bool PML>
+cudaError_t launch_n(const StageParams<float>& P, int nb, cudaStream_t s) {
+  using PL = Plan<N, PML>;
+  if (P.n_elem <= 0) return cudaSuccess;
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  StageParams<float> Q = P;
+  Q.nb = nb;
+  const long long tiles = (long long)((P.n_elem + PL::T - 1) / PL::T) * nb;
+  const int per_sm = 512 / (int)PL::TMEM_COLS;
+  const int grid = (int)std::min<long long>(tiles, (long long)per_sm * sms);
+  tc_stage_kernel<N, PML><<<grid, kTcThreads, PL::bytes, s>>>(Q);
+  return cudaGetLastError();
+}
+
+}  // namespace tc
+
+bool tc_supported(int N, bool kappa) { return N >= 1 && N <= 4 && !kappa; }
+
+cudaError_t configure_tc_kernels(int N) {
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (N) {
+    case 1: e = tc::configure_n<1, false>(); if (e == cudaSuccess) e = tc::configure_n<1, true>(); break;
+    case 2: e = tc::configure_n<2, false>(); if (e == cudaSuccess) e = tc::configure_n<2, true>(); break;
+    case 3: e = tc::configure_n<3, false>(); if (e == cudaSuccess) e = tc::configure_n<3, true>(); break;
+    case 4: e = tc::configure_n<4, false>(); if (e == cudaSuccess) e = tc::configure_n<4, true>(); break;
+    default: break;
+  }
+  return e;
+}
+
+cudaError_t launch_stage_tc(int N, bool pml, const StageParams<float>& P, int nb, cudaStream_t s) {
+  switch (N) {
+    case 1: return pml ? tc::launch_n<1, true>(P, nb, s) : tc::launch_n<1, false>(P, nb, s);
+    case 2: return pml ? tc::launch_n<2, true>(P, nb, s) : tc::launch_n<2, false>(P, nb, s);
+    case 3: return pml ? tc::launch_n<3, true>(P, nb, s) : tc::launch_n<3, false>(P, nb, s);
+    case 4: return pml ? tc::launch_n<4, true>(P, nb, s) : tc::launch_n<4, false>(P, nb, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace wadg
