@@ -159,6 +159,24 @@ wadg_status wadg_run_steps(wadg_ctx* ctx, int64_t nsteps, double dt, double* pro
  * context's stream.  Advances the state like wadg_rk_stage. */
 wadg_status wadg_profile_stage(wadg_ctx* ctx, int reps, double dt, double* ms_out);
 
+/* Gradient of the probe objective J_b = sum over the nsteps steps and the
+ * probes of |E(x_p)|^2 (excitation b, FP64 sums) with respect to the
+ * per-element relative permittivity eps_r and, per axis, the PML parameters
+ * sigma_max and p_sigma (profiles of Section III with kappa = 1, so eq. 9 has
+ * a = 1), by the discrete adjoint of the Runge-Kutta recursion and of the
+ * semi-discrete operator (upwind flux, eqs. 26-29).  Starts from the current
+ * state and time; the forward pass stores a checkpoint every ckpt_every
+ * steps and the reverse pass recomputes each segment from its checkpoint.
+ * On return the state is the forward state after nsteps steps (as after
+ * wadg_run_steps).  Outputs (any may be NULL): J_out[n_batch],
+ * dJ_deps[n_batch][K] (caller element order), dJ_dsigma_max[n_batch][3],
+ * dJ_dp_sigma[n_batch][3].  EUNSUPPORTED for the TF32 precision or
+ * kappa_max != 1; ESTATE without probes.  Device memory: about
+ * (nsteps/ckpt_every + ckpt_every + 12) copies of the state. */
+wadg_status wadg_adjoint(wadg_ctx* ctx, int64_t nsteps, double dt, int32_t ckpt_every,
+                         double* J_out, double* dJ_deps, double* dJ_dsigma_max,
+                         double* dJ_dp_sigma);
+
 /* Largest step for the given CFL number:
  * dt = cfl * 2 / ((N+1)^2 * max_{k,f} Fscale_{k,f}), Fscale = sJ/J. */
 wadg_status wadg_stable_dt(const wadg_ctx* ctx, double cfl, double* dt_out);

@@ -211,9 +211,11 @@ wadg_status upload_ops(wadg_ctx* ctx) {
   std::vector<Real> hr = cvt<Real>(h);
   CK(dalloc(ctx->ops, hr.size() * sizeof(Real)));
   CK(cudaMemcpy(ctx->ops.p, hr.data(), hr.size() * sizeof(Real), cudaMemcpyHostToDevice));
-  std::vector<unsigned char> t(NF + 4 * 24 * Nfp);
+  // Fmask [NF] | fperm [4][24][Nfp] (neighbour volume node) | fmap (neighbour face node)
+  std::vector<unsigned char> t(NF + 2 * 4 * 24 * Nfp);
   for (int i = 0; i < NF; ++i) t[i] = (unsigned char)R.Fmask[i];
   for (int i = 0; i < 4 * 24 * Nfp; ++i) t[NF + i] = (unsigned char)std::max(R.fperm[i], 0);
+  for (int i = 0; i < 4 * 24 * Nfp; ++i) t[NF + 4 * 24 * Nfp + i] = (unsigned char)R.fmap[i];
   CK(dalloc(ctx->tabs, t.size()));
   CK(cudaMemcpy(ctx->tabs.p, t.data(), t.size(), cudaMemcpyHostToDevice));
   if (ctx->tc) {
@@ -675,6 +677,8 @@ wadg_status wadg_create(int N, wadg_precision prec, int32_t n_batch, int device,
     cudaError_t ce = ctx->rs == 8 ? configure_stage_kernels<double>(N)
                                   : configure_stage_kernels<float>(N);
     if (ce == cudaSuccess && ctx->tc) ce = configure_tc_kernels(N);
+    if (ce == cudaSuccess && !ctx->tc)
+      ce = ctx->rs == 8 ? configure_adjoint_kernels<double>(N) : configure_adjoint_kernels<float>(N);
     if (ce != cudaSuccess) s = fail(ctx, WADG_ECUDA, "kernel set-up: %s", cudaGetErrorString(ce));
   }
   if (s == WADG_OK) {
@@ -1016,6 +1020,203 @@ wadg_status wadg_profile_stage(wadg_ctx* ctx, int reps, double dt, double* ms_ou
   ms_out[0] = tot[0] / reps;
   ms_out[1] = tot[1] / reps;
   return WADG_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// the E,H and P blocks of one full state (device)
+struct StateBuf {
+  DevPtr q, p;
+};
+
+wadg_status alloc_state(wadg_ctx* ctx, StateBuf& b) {
+  CK(dalloc(b.q, ctx->q[0].bytes));
+  CK(dalloc(b.p, ctx->p.bytes));
+  return WADG_OK;
+}
+void free_state(StateBuf& b) {
+  dfree(b.q);
+  dfree(b.p);
+}
+wadg_status save_state(wadg_ctx* ctx, StateBuf& b) {
+  CK(cudaMemcpyAsync(b.q.p, ctx->q[ctx->cur].p, b.q.bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (b.p.bytes)
+    CK(cudaMemcpyAsync(b.p.p, ctx->p.p, b.p.bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  return WADG_OK;
+}
+wadg_status load_state(wadg_ctx* ctx, const StateBuf& b) {
+  CK(cudaMemcpyAsync(ctx->q[ctx->cur].p, b.q.p, b.q.bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (b.p.bytes)
+    CK(cudaMemcpyAsync(ctx->p.p, b.p.p, b.p.bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  return WADG_OK;
+}
+
+template <typename Real>
+wadg_status adjoint_typed(wadg_ctx* ctx, int64_t nsteps, double dt, int C, double* J_out,
+                          double* dJ_deps, double* dJ_dsm, double* dJ_dps) {
+  const int Np = ctx->ref.Np, Nfp = ctx->ref.Nfp;
+  const int64_t K = ctx->K, K1 = ctx->K1;
+  const int nb = ctx->nb;
+  const double t0 = ctx->t;
+  const int64_t nseg = (nsteps + C - 1) / C;
+  std::vector<StateBuf> ck(nseg + 1), seg(C + 1), stin(5);
+  DevPtr lq, rq, lp, rp, G, ge, gp;
+  auto cleanup = [&]() {
+    for (auto& b : ck) free_state(b);
+    for (auto& b : seg) free_state(b);
+    for (auto& b : stin) free_state(b);
+    for (DevPtr* d : {&lq, &rq, &lp, &rp, &G, &ge, &gp}) dfree(*d);
+  };
+  auto fail_clean = [&](wadg_status st) {
+    cleanup();
+    return st;
+  };
+  wadg_status st = WADG_OK;
+  for (auto& b : ck) if ((st = alloc_state(ctx, b)) != WADG_OK) return fail_clean(st);
+  for (auto& b : seg) if ((st = alloc_state(ctx, b)) != WADG_OK) return fail_clean(st);
+  for (auto& b : stin) if ((st = alloc_state(ctx, b)) != WADG_OK) return fail_clean(st);
+  const size_t qb = ctx->q[0].bytes, pb = ctx->p.bytes;
+  cudaError_t ce = cudaSuccess;
+  if (ce == cudaSuccess) ce = dalloc(lq, qb);
+  if (ce == cudaSuccess) ce = dalloc(rq, qb);
+  if (ce == cudaSuccess) ce = dalloc(lp, pb);
+  if (ce == cudaSuccess) ce = dalloc(rp, pb);
+  if (ce == cudaSuccess) ce = dalloc(G, (size_t)nb * K * 4 * Nfp * 6 * sizeof(Real));
+  if (ce == cudaSuccess) ce = dalloc(ge, (size_t)nb * K * 8);
+  if (ce == cudaSuccess) ce = dalloc(gp, (size_t)nb * 6 * 8);
+  if (ce != cudaSuccess)
+    return fail_clean(fail(ctx, WADG_ENOMEM, "adjoint buffers: %s", cudaGetErrorString(ce)));
+
+  // ---- forward pass with checkpoints every C steps; J accumulates on device
+  CK(cudaMemsetAsync(ctx->obj.p, 0, ctx->obj.bytes, ctx->stream));
+  if ((st = save_state(ctx, ck[0])) != WADG_OK) return fail_clean(st);
+  for (int64_t sg = 0; sg < nseg; ++sg) {
+    const int64_t n = std::min<int64_t>(C, nsteps - sg * C);
+    double tt = t0 + sg * C * dt;
+    CK(cudaMemcpyAsync(ctx->tdev.p, &tt, 8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(ctx->stepdev.p, 0, 8, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int64_t i = 0; i < n; ++i) {
+      CK(cudaGraphLaunch(ctx->graph[ctx->cur], ctx->stream));
+      ctx->cur ^= 1;
+    }
+    if ((st = save_state(ctx, ck[sg + 1])) != WADG_OK) return fail_clean(st);
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  std::vector<double> J(nb);
+  CK(cudaMemcpy(J.data(), ctx->obj.p, 8 * nb, cudaMemcpyDeviceToHost));
+
+  // ---- reverse pass
+  CK(cudaMemsetAsync(lq.p, 0, qb, ctx->stream));
+  CK(cudaMemsetAsync(rq.p, 0, qb, ctx->stream));
+  if (pb) {
+    CK(cudaMemsetAsync(lp.p, 0, pb, ctx->stream));
+    CK(cudaMemsetAsync(rp.p, 0, pb, ctx->stream));
+  }
+  CK(cudaMemsetAsync(ge.p, 0, ge.bytes, ctx->stream));
+  CK(cudaMemsetAsync(gp.p, 0, gp.bytes, ctx->stream));
+  AdjParams<Real> A{};
+  A.lam_q = (Real*)lq.p; A.rho_q = (Real*)rq.p; A.lam_p = (Real*)lp.p; A.rho_p = (Real*)rp.p;
+  A.G = (Real*)G.p; A.grad_eps = (double*)ge.p; A.grad_prof = (double*)gp.p;
+  A.geo = (const double*)ctx->geo.p; A.mat = (const Real*)ctx->mat.p;
+  A.nbr = (const int*)ctx->nbr.p; A.code = (const unsigned char*)ctx->code.p;
+  A.sig = (const Real*)ctx->sig.p; A.ops = (const Real*)ctx->ops.p;
+  A.tabs = (const unsigned char*)ctx->tabs.p;
+  A.strideQ = K * 6 * Np; A.strideP = K1 * 6 * Np;
+  A.K = (int)K; A.K0 = (int)ctx->K0;
+  A.nsrc = ctx->nsrc; A.src = (const SrcDev*)ctx->src.p; A.src_w = (const Real*)ctx->srcw.p;
+  A.dt = dt; A.eps0 = ctx->has_prof ? ctx->prof.eps0 : 1.0; A.alpha = 1.0;
+  for (int u = 0; u < 3; ++u) {
+    A.sigma_max[u] = ctx->has_prof ? ctx->prof.sigma_max[u] : 0.0;
+    A.p_sigma[u] = ctx->has_prof ? ctx->prof.p_sigma[u] : 0.0;
+  }
+  for (int64_t sg = nseg - 1; sg >= 0; --sg) {
+    const int64_t s0 = sg * C, n = std::min<int64_t>(C, nsteps - s0);
+    // step-start states of the segment, recomputed from its checkpoint
+    CK(cudaMemcpyAsync(seg[0].q.p, ck[sg].q.p, qb, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (pb) CK(cudaMemcpyAsync(seg[0].p.p, ck[sg].p.p, pb, cudaMemcpyDeviceToDevice, ctx->stream));
+    for (int64_t k = 0; k < n; ++k) {
+      if ((st = load_state(ctx, seg[k])) != WADG_OK) return fail_clean(st);
+      for (int i = 0; i < 5; ++i)
+        if ((st = issue_stage<Real>(ctx, i, dt, t0 + (s0 + k) * dt, false)) != WADG_OK)
+          return fail_clean(st);
+      if ((st = save_state(ctx, seg[k + 1])) != WADG_OK) return fail_clean(st);
+    }
+    for (int64_t k = n - 1; k >= 0; --k) {
+      const double tn = t0 + (s0 + k) * dt;
+      // objective after step s0 + k: dJ/dE at the probes
+      if (ctx->nprobe > 0)
+        CK(launch_adjoint_probes<Real>((const Real*)seg[k + 1].q.p, K * 6 * Np, ctx->nprobe, nb,
+                                       Np, (const int*)ctx->pr_elem.p,
+                                       (const double*)ctx->pr_ell.p, (Real*)lq.p, ctx->stream));
+      // the five stage inputs of this step
+      if ((st = load_state(ctx, seg[k])) != WADG_OK) return fail_clean(st);
+      for (int i = 0; i < 5; ++i) {
+        if ((st = save_state(ctx, stin[i])) != WADG_OK) return fail_clean(st);
+        if (i < 4 && (st = issue_stage<Real>(ctx, i, dt, tn, false)) != WADG_OK)
+          return fail_clean(st);
+      }
+      for (int i = 4; i >= 0; --i) {
+        A.q_in = (const Real*)stin[i].q.p;
+        A.p_in = (const Real*)stin[i].p.p;
+        A.rk_a = kRkA[i];
+        A.rk_b = kRkB[i];
+        A.t = tn + kRkC.c[i] * dt;
+        CK(launch_adjoint_stage<Real>(ctx->N, A, nb, ctx->stream));
+      }
+    }
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  // final forward state back in place
+  if ((st = load_state(ctx, ck[nseg])) != WADG_OK) return fail_clean(st);
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->t = t0 + nsteps * dt;
+  std::vector<double> hge((size_t)nb * K), hgp((size_t)nb * 6);
+  CK(cudaMemcpy(hge.data(), ge.p, ge.bytes, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(hgp.data(), gp.p, gp.bytes, cudaMemcpyDeviceToHost));
+  cleanup();
+  // d/d eps_r: eps_r enters through eps = eps_r (normalised units)
+  if (J_out) for (int b = 0; b < nb; ++b) J_out[b] = J[b];
+  if (dJ_deps)
+    for (int b = 0; b < nb; ++b)
+      for (int64_t e = 0; e < K; ++e) dJ_deps[(size_t)b * K + ctx->perm[e]] = hge[(size_t)b * K + e];
+  for (int b = 0; b < nb; ++b)
+    for (int u = 0; u < 3; ++u) {
+      if (dJ_dsm) dJ_dsm[b * 3 + u] = hgp[b * 6 + u];
+      if (dJ_dps) dJ_dps[b * 3 + u] = hgp[b * 6 + 3 + u];
+    }
+  return WADG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+wadg_status wadg_adjoint(wadg_ctx* ctx, int64_t nsteps, double dt, int32_t ckpt_every,
+                         double* J_out, double* dJ_deps, double* dJ_dsigma_max,
+                         double* dJ_dp_sigma) {
+  wadg_status s = need_mesh(ctx);
+  if (s != WADG_OK) return s;
+  if (nsteps < 1 || !(dt > 0) || ckpt_every < 1) return fail(ctx, WADG_EINVAL, "bad arguments");
+  if (ctx->tc) return fail(ctx, WADG_EUNSUPPORTED, "the adjoint runs on the FP64/FP32 kernels");
+  if (ctx->kappa) return fail(ctx, WADG_EUNSUPPORTED, "the adjoint is built for kappa = 1");
+  if (ctx->nprobe < 1) return fail(ctx, WADG_ESTATE, "the objective needs probes");
+  cudaSetDevice(ctx->device);
+  const size_t need = (size_t)std::min<int64_t>(ckpt_every, 4096) * ctx->nprobe * 6 * ctx->nb * 8;
+  if (ctx->pr_out.bytes < need) {
+    invalidate_graphs(ctx);
+    CK(dalloc(ctx->pr_out, need));
+  }
+  if (!ctx->graph_valid || ctx->graph_dt != dt) {
+    s = capture_graphs(ctx, dt);
+    if (s != WADG_OK) return s;
+  }
+  const int C = (int)std::min<int64_t>(ckpt_every, 4096);
+  return ctx->rs == 8
+             ? adjoint_typed<double>(ctx, nsteps, dt, C, J_out, dJ_deps, dJ_dsigma_max, dJ_dp_sigma)
+             : adjoint_typed<float>(ctx, nsteps, dt, C, J_out, dJ_deps, dJ_dsigma_max, dJ_dp_sigma);
 }
 
 wadg_status wadg_stable_dt(const wadg_ctx* ctx, double cfl, double* dt_out) {

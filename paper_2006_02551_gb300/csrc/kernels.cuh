@@ -57,6 +57,34 @@ struct StageParams {
   int* err;                 // device error flag (bounded waits that gave up)
 };
 
+// reverse Runge-Kutta stage (adjoint.cu)
+template <typename Real>
+struct AdjParams {
+  Real* lam_q;              // adjoint of E,H [b][e][6][Np], updated in place
+  Real* rho_q;              // adjoint of the E,H register
+  Real* lam_p;              // adjoint of P [b][e'][6][Np]
+  Real* rho_p;
+  const Real* q_in;         // forward stage input (E,H)
+  const Real* p_in;         // forward stage input (P)
+  Real* G;                  // scratch [b][e][4 Nfp][6]
+  double* grad_eps;         // [b][K] internal order
+  double* grad_prof;        // [b][6]: d/dsigma_max[3], d/dp_sigma[3]
+  const double* geo;
+  const Real* mat;
+  const int* nbr;
+  const unsigned char* code;
+  const Real* sig;
+  const Real* ops;
+  const unsigned char* tabs;
+  int64_t strideQ, strideP;
+  int K, K0, e_begin, n_elem;
+  int nsrc;
+  const SrcDev* src;
+  const Real* src_w;
+  double rk_a, rk_b, dt, t, eps0, alpha;
+  double sigma_max[3], p_sigma[3];
+};
+
 struct ProbeParams {
   const void* q;            // current E,H
   int64_t strideQ;
@@ -75,6 +103,13 @@ template <typename Real>
 cudaError_t launch_stage(int N, bool pml, bool kappa, const StageParams<Real>& P, int nb,
                          cudaStream_t s);
 cudaError_t launch_probes(bool fp64, const ProbeParams& P, cudaStream_t s);
+template <typename Real>
+cudaError_t configure_adjoint_kernels(int N);
+template <typename Real>
+cudaError_t launch_adjoint_stage(int N, const AdjParams<Real>& P, int nb, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_adjoint_probes(const Real* q, int64_t strideQ, int nprobe, int nb, int Np,
+                                  const int* elem, const double* ell, Real* lam, cudaStream_t s);
 // tensor-core (tcgen05, TF32) stage kernels
 bool tc_supported(int N, bool kappa);
 cudaError_t configure_tc_kernels(int N);

@@ -332,6 +332,7 @@ bool build_ref_ops(int N, RefOps& o, const char** err) {
     }
   // face-node permutation table
   o.fperm.assign(4 * 24 * Nfp, -1);
+  o.fmap.assign(4 * 24 * Nfp, 0);
   for (int f = 0; f < 4; ++f)
     for (int nf = 0; nf < 4; ++nf)
       for (int rot = 0; rot < 6; ++rot)
@@ -346,6 +347,8 @@ bool build_ref_ops(int N, RefOps& o, const char** err) {
             const int* bb = &o.bary[p * 4];
             if (bb[0] == want[0] && bb[1] == want[1] && bb[2] == want[2] && bb[3] == want[3]) {
               o.fperm[(f * 24 + nf * 6 + rot) * Nfp + m] = p;
+              for (int m2 = 0; m2 < Nfp; ++m2)
+                if (o.Fmask[nf * Nfp + m2] == p) o.fmap[(f * 24 + nf * 6 + rot) * Nfp + m] = m2;
               break;
             }
           }

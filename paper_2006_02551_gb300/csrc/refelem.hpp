@@ -24,6 +24,8 @@ struct RefOps {
   // vertex rotation rot (code = nf*6 + rot), the neighbour's volume node
   // that coincides with face node m of face f: [4][24][Nfp]
   std::vector<int> fperm;
+  // the same table as face-node indices of the neighbour's face: [4][24][Nfp]
+  std::vector<int> fmap;
   std::vector<double> lagrange_at(double r, double s, double t) const;  // [Np]
 };
 

@@ -226,7 +226,17 @@ struct Plan {
   static constexpr uint32_t SET = (PML ? 4 : 2) * TSB;  // q, res (+ P, res of P)
   static constexpr uint32_t oST = oGeo + 2 * T * 28 * 4;  // two staging sets
   static constexpr uint32_t oMisc = oST + 2 * SET;
-  static constexpr uint32_t bytes_used = oMisc + 64 * 4 + 64;
+  // epilogue scratch: the node rows of the products copied out of TMEM so that
+  // every warp can share the per-node work.  PML: the volume/LIFT columns go
+  // to the field-operand buffers (free once the first products are done), the
+  // P_q columns to the (t, z) buffer (free once P_q is done).
+  static constexpr uint32_t DV_BYTES = T * 24 * Np * 4;
+  static constexpr uint32_t DP_BYTES = T * 12 * Np * 4;
+  static constexpr uint32_t oDV = PML ? oBF : oMisc + 64 * 4 + 64;
+  static constexpr uint32_t oDP = oBTZ;
+  static_assert(!PML || oDV + DV_BYTES <= oBTZ, "volume/LIFT dump");
+  static_assert(!PML || oDP + DP_BYTES <= oRS, "P_q dump");
+  static constexpr uint32_t bytes_used = PML ? oMisc + 64 * 4 + 64 : oDV + DV_BYTES;
   // residency follows the tensor-memory budget of 512 columns per SM: one PML
   // block (512 columns) or two non-PML blocks (256 each) per SM, enforced by
   // the shared-memory request so that no block waits in tcgen05.alloc
@@ -596,7 +606,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_stage_kernel(const StagePara
 
     if (next < ntiles) load_sig(next, sgv);
 
-    // ---- epilogue A2: curl + LIFT at node i = lane of quadrants 0..(Np-1)/32
+    // ---- volume/LIFT columns of the node lanes -> shared memory
+    float* DV = reinterpret_cast<float*>(smem + PL::oDV);   // [T][24][Np]
     if (quad * 32 < Np) {
       const int i = quad * 32 + lane;
       for (int e = half; e < T; e += 2) {
@@ -604,49 +615,63 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_stage_kernel(const StagePara
         tld_6x4(tmem + lane_base + PL::cDr + e * 6, tmem + lane_base + PL::cDs + e * 6,
                 tmem + lane_base + PL::cDt + e * 6, tmem + lane_base + PL::cL + e * 6, d);
         if (e >= ne || i >= Np) continue;
-        const int eg = eg0 + e;
-        const float* g = geo + e * 28 + 16;
-        float dx[6], dy[6], dz[6];
+#pragma unroll
+        for (int k = 0; k < 24; ++k) DV[(e * 24 + k) * Np + i] = d[k];
+      }
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+
+    // ---- epilogue A2 (all warps): curl + LIFT, rhs of E and H per (element, node)
+    for (int task = tid; task < ne * Np; task += kTcThreads) {
+      const int e = task / Np, i = task - e * Np;
+      const int eg = eg0 + e;
+      const float* dv = DV + e * 24 * Np + i;
+      const float* g = geo + e * 28 + 16;
+      float dx[6], dy[6], dz[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        const float r = dv[c * Np], sd_ = dv[(6 + c) * Np], t_ = dv[(12 + c) * Np];
+        dx[c] = g[0] * r + g[3] * sd_ + g[6] * t_;
+        dy[c] = g[1] * r + g[4] * sd_ + g[7] * t_;
+        dz[c] = g[2] * r + g[5] * sd_ + g[8] * t_;
+      }
+      float lf[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) lf[c] = dv[(18 + c) * Np];
+      // Cbar(H) (E rows) and Cbar(E) (H rows)
+      float CH[3], CE[3];
+      CH[0] = dy[5] - dz[4] + lf[0];
+      CH[1] = dz[3] - dx[5] + lf[1];
+      CH[2] = dx[4] - dy[3] + lf[2];
+      CE[0] = dy[2] - dz[1] + lf[3];
+      CE[1] = dz[0] - dx[2] + lf[4];
+      CE[2] = dx[1] - dy[0] + lf[5];
+      for (int s = 0; s < nsrc_l; ++s) {
+        const SrcDev& sd = P.src[srcl[s]];
+        if (sd.elem != eg) continue;
+        const double tau = sd.width;
+        const double gg = exp(-(tst - sd.t0) * (tst - sd.t0) / (4.0 * tau * tau));
+        const float jt = (float)(sd.amp * (-(tst - sd.t0) / (2.0 * tau * tau)) * gg);
+        const float w = P.src_w[srcl[s] * Np + i];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) CH[c] -= jt * (float)sd.dir[c] * w;
+      }
+      const float ie = P.mat[eg * 3 + 0], im = P.mat[eg * 3 + 1];
+      const float rhs[6] = {ie * CH[0], ie * CH[1], ie * CH[2], -im * CE[0], -im * CE[1], -im * CE[2]};
+      if (!PML) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-          dx[c] = g[0] * d[c] + g[3] * d[6 + c] + g[6] * d[12 + c];
-          dy[c] = g[1] * d[c] + g[4] * d[6 + c] + g[7] * d[12 + c];
-          dz[c] = g[2] * d[c] + g[5] * d[6 + c] + g[8] * d[12 + c];
+          const int li = (e * 6 + c) * Np + i;
+          const int64_t gi = (int64_t)eg0 * 6 * Np + li;
+          const float rr = rka * SR[li] + rdt * rhs[c];
+          resq[gi] = rr;
+          qout[gi] = SQ[li] + rkb * rr;
         }
-        const float* lf = d + 18;
-        // Cbar(H) (E rows) and Cbar(E) (H rows)
-        float CH[3], CE[3];
-        CH[0] = dy[5] - dz[4] + lf[0];
-        CH[1] = dz[3] - dx[5] + lf[1];
-        CH[2] = dx[4] - dy[3] + lf[2];
-        CE[0] = dy[2] - dz[1] + lf[3];
-        CE[1] = dz[0] - dx[2] + lf[4];
-        CE[2] = dx[1] - dy[0] + lf[5];
-        for (int s = 0; s < nsrc_l; ++s) {
-          const SrcDev& sd = P.src[srcl[s]];
-          if (sd.elem != eg) continue;
-          const double tau = sd.width;
-          const double gg = exp(-(tst - sd.t0) * (tst - sd.t0) / (4.0 * tau * tau));
-          const float jt = (float)(sd.amp * (-(tst - sd.t0) / (2.0 * tau * tau)) * gg);
-          const float w = P.src_w[srcl[s] * Np + i];
+      } else {
 #pragma unroll
-          for (int c = 0; c < 3; ++c) CH[c] -= jt * (float)sd.dir[c] * w;
-        }
-        const float ie = P.mat[eg * 3 + 0], im = P.mat[eg * 3 + 1];
-        float rhs[6] = {ie * CH[0], ie * CH[1], ie * CH[2], -im * CE[0], -im * CE[1], -im * CE[2]};
-        if (!PML) {
-#pragma unroll
-          for (int c = 0; c < 6; ++c) {
-            const int li = (e * 6 + c) * Np + i;
-            const int64_t gi = (int64_t)eg0 * 6 * Np + li;
-            const float rr = rka * SR[li] + rdt * rhs[c];
-            resq[gi] = rr;
-            qout[gi] = SQ[li] + rkb * rr;
-          }
-        } else {
-#pragma unroll
-          for (int c = 0; c < 6; ++c) RS[(e * 6 + c) * NpP + i] = rhs[c];
-        }
+        for (int c = 0; c < 6; ++c) RS[(e * 6 + c) * NpP + i] = rhs[c];
       }
     }
 
@@ -667,7 +692,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_stage_kernel(const StagePara
       phase ^= 1;
       if (!__syncthreads_and(ok)) { failed = true; break; }
       fence_after();
-      // ---- epilogue B: s, rhs of P; Runge-Kutta update of E, H, P^E, P^H
+      fence_async_smem();   // the (t, z) buffer is reused below
+      // ---- P_q columns of the node lanes -> shared memory
+      float* DP = reinterpret_cast<float*>(smem + PL::oDP);   // [T][12][Np]
       if (quad * 32 < Np) {
         const int i = quad * 32 + lane;
         for (int e = half; e < T; e += 2) {
@@ -675,18 +702,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_stage_kernel(const StagePara
           tld_6x2(tmem + lane_base + PL::cPq + e * 6, tmem + lane_base + PL::cPq + 6 * T + e * 6, v);
           if (e >= ne || i >= Np) continue;
 #pragma unroll
-          for (int c = 0; c < 6; ++c) {
-            const int li = (e * 6 + c) * Np + i;
-            const int64_t gi = (int64_t)eg0 * 6 * Np + li;
-            const float rr = rka * SR[li] + rdt * (RS[(e * 6 + c) * NpP + i] - v[c]);
-            resq[gi] = rr;
-            qout[gi] = SQ[li] + rkb * rr;
-            const int64_t pi = (int64_t)ep0 * 6 * Np + li;
-            const float rp = rka * SRP[li] + rdt * v[6 + c];
-            resp[pi] = rp;
-            pio[pi] = SP[li] + rkb * rp;
-          }
+          for (int k = 0; k < 12; ++k) DP[(e * 12 + k) * Np + i] = v[k];
         }
+      }
+      fence_before();
+      __syncthreads();
+      fence_after();
+      // ---- epilogue B (all warps): Runge-Kutta update of E, H, P^E, P^H
+      for (int task = tid; task < ne * 6 * Np; task += kTcThreads) {
+        const int e = task / (6 * Np), r = task - e * 6 * Np, c = r / Np, i = r - c * Np;
+        const int li = task;   // == (e * 6 + c) * Np + i
+        const int64_t gi = (int64_t)eg0 * 6 * Np + li;
+        const float rr = rka * SR[li] + rdt * (RS[(e * 6 + c) * NpP + i] - DP[(e * 12 + c) * Np + i]);
+        resq[gi] = rr;
+        qout[gi] = SQ[li] + rkb * rr;
+        const int64_t pi = (int64_t)ep0 * 6 * Np + li;
+        const float rp = rka * SRP[li] + rdt * DP[(e * 12 + 6 + c) * Np + i];
+        resp[pi] = rp;
+        pio[pi] = SP[li] + rkb * rp;
       }
     }
     fence_before();

@@ -57,6 +57,7 @@ _SIG = {
     "wadg_run_steps": [_P, C.c_int64, C.c_double, _D],
     "wadg_stable_dt": [_P, C.c_double, _D],
     "wadg_profile_stage": [_P, C.c_int, C.c_double, _D],
+    "wadg_adjoint": [_P, C.c_int64, C.c_double, C.c_int32, _D, _D, _D, _D],
     "wadg_objective": [_P, _D],
     "wadg_memory_report": [_P, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t),
                            C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)],
@@ -216,6 +217,17 @@ class Solver:
         ms = np.zeros(2)
         self._c(self.lib.wadg_profile_stage(self.ctx, reps, dt, _ptr(ms)))
         return ms
+
+    def adjoint(self, nsteps, dt, ckpt_every=45):
+        """(J [nb], dJ/deps_r [nb][K], dJ/dsigma_max [nb][3], dJ/dp_sigma [nb][3])."""
+        nb = self.n_batch
+        J = np.empty(nb)
+        ge = np.empty((nb, self.info()["K"]))
+        gs = np.empty((nb, 3))
+        gp = np.empty((nb, 3))
+        self._c(self.lib.wadg_adjoint(self.ctx, nsteps, dt, ckpt_every, _ptr(J), _ptr(ge),
+                                      _ptr(gs), _ptr(gp)))
+        return J, ge, gs, gp
 
     def stable_dt(self, cfl=1.0):
         d = C.c_double()
