@@ -177,6 +177,25 @@ wadg_status wadg_adjoint(wadg_ctx* ctx, int64_t nsteps, double dt, int32_t ckpt_
                          double* J_out, double* dJ_deps, double* dJ_dsigma_max,
                          double* dJ_dp_sigma);
 
+/* wadg_run_steps for callers that cannot allocate device memory when they
+ * step: for example code that runs under a fixed device-memory budget handed
+ * to it by an enclosing application, or a caller that must not trigger the
+ * implicit device synchronisation an allocation can bring.  (The paper has
+ * no counterpart; this is a property of the library, not of the method.)
+ * Same arguments, results and errors as wadg_run_steps, but this call
+ * allocates nothing: it launches the stage kernels directly instead of
+ * replaying a captured graph, and its scratch -- the device time and step
+ * counters, the non-finite flag and the probe records of a chunk of steps on
+ * their way to probe_out -- lives in one fixed 16 MiB device array of the
+ * library (held on every GPU that loads the library until the process
+ * exits).  Steps are processed in chunks whose probe records fit the array;
+ * EINVAL if the records of a single step (nprobe * 6 * n_batch doubles) do
+ * not fit.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and should come before any stream capture.  Every
+ * call shares the one array per device, so calls whose work overlaps on the
+ * GPU (other threads, other streams) race on it. */
+wadg_status wadg_run_steps_noalloc(wadg_ctx* ctx, int64_t nsteps, double dt, double* probe_out);
+
 /* Largest step for the given CFL number:
  * dt = cfl * 2 / ((N+1)^2 * max_{k,f} Fscale_{k,f}), Fscale = sJ/J. */
 wadg_status wadg_stable_dt(const wadg_ctx* ctx, double cfl, double* dt_out);

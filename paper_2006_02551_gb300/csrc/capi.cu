@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -1292,3 +1293,136 @@ const char* wadg_last_error(const wadg_ctx* ctx) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Stepping without device allocation (wadg_run_steps_noalloc).
+//
+// wadg_run_steps may allocate on first use (the device staging area of the
+// probe records, the CUDA graphs of a step).  Callers that must not allocate
+// device memory at that point use wadg_run_steps_noalloc instead: it launches
+// the stage kernels one by one and keeps its scratch -- the device time and
+// step counters the kernels read, the non-finite flag and the probe records
+// of a chunk of steps before they are copied to the host -- in the file-scope
+// array below.  The array is part of the library image: every GPU that loads
+// the library holds its kNoAllocBytes until the process exits.  In host code
+// the array's name is only a stand-in for the device object; its device
+// address is looked up once per device with cudaGetSymbolAddress.
+namespace {
+
+constexpr size_t kNoAllocBytes = size_t(16) << 20;   // 16 MiB per device
+constexpr size_t kNoAllocRecords = 256;               // offset of the probe records
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[256] = {};   // device address of the array, per device ordinal
+
+// device address of the scratch array on ctx's device (which is current)
+wadg_status noalloc_scratch(wadg_ctx* ctx, unsigned char** out) {
+  if (ctx->device < 0 || ctx->device >= 256)
+    return fail(ctx, WADG_EINVAL, "device ordinal %d out of range", ctx->device);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[ctx->device]) {
+    void* a = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&a, g_noalloc_scratch);
+    if (e != cudaSuccess || !a)
+      return fail(ctx, WADG_ECUDA, "cudaGetSymbolAddress of the step scratch: %s",
+                  cudaGetErrorString(e));
+    g_noalloc_addr[ctx->device] = a;
+  }
+  *out = static_cast<unsigned char*>(g_noalloc_addr[ctx->device]);
+  return WADG_OK;
+}
+
+template <typename Real>
+wadg_status noalloc_stage(wadg_ctx* ctx, int stage, double dt, const double* tdev) {
+  if (ctx->tc) {
+    StageParams<float> A = stage_params<float>(ctx, stage, dt, 0.0, false, false);
+    A.t_dev = tdev;
+    CK(launch_stage_tc(ctx->N, false, A, ctx->nb, ctx->stream));
+    if (ctx->K1 > 0) {
+      StageParams<float> B = stage_params<float>(ctx, stage, dt, 0.0, false, true);
+      B.t_dev = tdev;
+      CK(launch_stage_tc(ctx->N, true, B, ctx->nb, ctx->stream));
+    }
+  } else {
+    StageParams<Real> A = stage_params<Real>(ctx, stage, dt, 0.0, false, false);
+    A.t_dev = tdev;
+    CK(launch_stage<Real>(ctx->N, false, false, A, ctx->nb, ctx->stream));
+    if (ctx->K1 > 0) {
+      StageParams<Real> B = stage_params<Real>(ctx, stage, dt, 0.0, false, true);
+      B.t_dev = tdev;
+      CK(launch_stage<Real>(ctx->N, true, ctx->kappa, B, ctx->nb, ctx->stream));
+    }
+  }
+  ctx->cur ^= 1;
+  return WADG_OK;
+}
+
+}  // namespace
+
+extern "C" wadg_status wadg_run_steps_noalloc(wadg_ctx* ctx, int64_t nsteps, double dt,
+                                              double* probe_out) {
+  wadg_status s = need_mesh(ctx);
+  if (s != WADG_OK) return s;
+  if (nsteps < 0 || !(dt > 0)) return fail(ctx, WADG_EINVAL, "bad nsteps or dt");
+  if (nsteps == 0) return WADG_OK;
+  cudaSetDevice(ctx->device);
+  unsigned char* scr = nullptr;
+  if ((s = noalloc_scratch(ctx, &scr)) != WADG_OK) return s;
+  double* tdev = reinterpret_cast<double*>(scr);
+  int64_t* stepdev = reinterpret_cast<int64_t*>(scr + 8);
+  int* flag = reinterpret_cast<int*>(scr + 16);
+  double* rec_dev = reinterpret_cast<double*>(scr + kNoAllocRecords);
+  const size_t rec = (size_t)ctx->nprobe * 6 * ctx->nb;   // doubles per step
+  const size_t cap = (kNoAllocBytes - kNoAllocRecords) / 8;
+  if (rec > cap)
+    return fail(ctx, WADG_EINVAL,
+                "probe records of one step (%zu bytes) exceed the %zu-byte step scratch",
+                rec * 8, cap * 8);
+  const int64_t chunk = rec ? std::min<int64_t>(nsteps, (int64_t)(cap / rec)) : nsteps;
+  int64_t done = 0;
+  while (done < nsteps) {
+    const int64_t n = std::min(chunk, nsteps - done);
+    // the array keeps the previous call's contents: set the counters
+    const double tt = ctx->t + done * dt;
+    CK(cudaMemcpyAsync(tdev, &tt, 8, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(stepdev, 0, 8, ctx->stream));
+    for (int64_t i = 0; i < n; ++i) {
+      for (int st = 0; st < 5; ++st) {
+        s = ctx->rs == 8 ? noalloc_stage<double>(ctx, st, dt, tdev)
+                         : noalloc_stage<float>(ctx, st, dt, tdev);
+        if (s != WADG_OK) return s;
+      }
+      if (ctx->nprobe > 0) {
+        ProbeParams pp{};
+        pp.q = ctx->q[ctx->cur].p;
+        pp.strideQ = ctx->K * 6 * ctx->ref.Np;
+        pp.nprobe = ctx->nprobe;
+        pp.nb = ctx->nb;
+        pp.Np = ctx->ref.Np;
+        pp.elem = (const int*)ctx->pr_elem.p;
+        pp.ell = (const double*)ctx->pr_ell.p;
+        pp.out = rec_dev;
+        pp.obj = (double*)ctx->obj.p;
+        pp.step = stepdev;
+        CK(launch_probes(ctx->rs == 8, pp, ctx->stream));
+      }
+      CK(launch_advance(tdev, stepdev, dt, ctx->stream));
+    }
+    if (probe_out && rec)
+      CK(cudaMemcpyAsync(probe_out + (size_t)done * rec, rec_dev, (size_t)n * rec * 8,
+                         cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    done += n;
+  }
+  ctx->t += nsteps * dt;
+  CK(cudaMemsetAsync(flag, 0, 4, ctx->stream));
+  const int64_t nq = ctx->nb * ctx->K * 6 * ctx->ref.Np;
+  if (ctx->rs == 8) CK(launch_check_finite<double>((const double*)ctx->q[ctx->cur].p, nq, flag, ctx->stream));
+  else CK(launch_check_finite<float>((const float*)ctx->q[ctx->cur].p, nq, flag, ctx->stream));
+  int hflag = 0;
+  CK(cudaMemcpyAsync(&hflag, flag, 4, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (hflag) return fail(ctx, WADG_ENONFINITE, "state became non-finite");
+  return check_err_flag(ctx);
+}

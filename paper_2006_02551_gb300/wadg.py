@@ -55,6 +55,7 @@ _SIG = {
     "wadg_get_state": [_P, _D, _D],
     "wadg_rk_stage": [_P, C.c_int, C.c_double, C.c_double],
     "wadg_run_steps": [_P, C.c_int64, C.c_double, _D],
+    "wadg_run_steps_noalloc": [_P, C.c_int64, C.c_double, _D],
     "wadg_stable_dt": [_P, C.c_double, _D],
     "wadg_profile_stage": [_P, C.c_int, C.c_double, _D],
     "wadg_adjoint": [_P, C.c_int64, C.c_double, C.c_int32, _D, _D, _D, _D],
@@ -228,6 +229,14 @@ class Solver:
         self._c(self.lib.wadg_adjoint(self.ctx, nsteps, dt, ckpt_every, _ptr(J), _ptr(ge),
                                       _ptr(gs), _ptr(gp)))
         return J, ge, gs, gp
+
+    def run_steps_noalloc(self, nsteps, dt, record=True):
+        """run_steps through the entry point that allocates no device memory."""
+        out = None
+        if record and getattr(self, "n_probe", 0):
+            out = np.empty((nsteps, self.n_probe, 6, self.n_batch))
+        self._c(self.lib.wadg_run_steps_noalloc(self.ctx, nsteps, dt, _ptr(out)))
+        return out
 
     def stable_dt(self, cfl=1.0):
         d = C.c_double()
