@@ -81,7 +81,7 @@ struct wadg_ctx {
   int64_t K0 = 0, K1 = 0;
 
   // device
-  DevPtr q[2], rq, p, rp, geo, mat, nbr, code, sig, kap, ops, tabs, verts;
+  DevPtr q[2], rq, p, rp, geo, fnrm, mat, nbr, code, sig, kap, ops, tabs, verts;
   DevPtr src, srcw, pr_elem, pr_ell, pr_out, obj, tdev, stepdev, flag, tcops, errflag;
   bool tc = false;   // tensor-core stage kernels (TF32)
   int cur = 0;
@@ -291,12 +291,29 @@ wadg_status rebuild_typed(wadg_ctx* ctx) {
   ctx->K0 = K - ctx->K1;
   // ---- per-element arrays in internal order
   std::vector<double> geo(K * 9), verts(K * 12);
+  std::vector<Real> fn(K * 16);
   std::vector<Real> mat(K * 3);
   std::vector<int> nbr(K * 4);
   std::vector<unsigned char> code(K * 4);
   for (int64_t e = 0; e < K; ++e) {
     const int64_t k = ctx->perm[e];
     for (int i = 0; i < 9; ++i) geo[e * 9 + i] = ctx->metric_u[k * 9 + i];
+    {
+      // unit outward normals and Fscale = sJ/J = |grad of the face coordinate|
+      const double* g = &ctx->metric_u[k * 9];
+      for (int f = 0; f < 4; ++f) {
+        double gx, gy, gz;
+        if (f == 0) { gx = -g[6]; gy = -g[7]; gz = -g[8]; }
+        else if (f == 1) { gx = -g[3]; gy = -g[4]; gz = -g[5]; }
+        else if (f == 2) { gx = g[0] + g[3] + g[6]; gy = g[1] + g[4] + g[7]; gz = g[2] + g[5] + g[8]; }
+        else { gx = -g[0]; gy = -g[1]; gz = -g[2]; }
+        const double mag = std::sqrt(gx * gx + gy * gy + gz * gz);
+        fn[e * 16 + f * 4 + 0] = (Real)(gx / mag);
+        fn[e * 16 + f * 4 + 1] = (Real)(gy / mag);
+        fn[e * 16 + f * 4 + 2] = (Real)(gz / mag);
+        fn[e * 16 + f * 4 + 3] = (Real)mag;
+      }
+    }
     for (int a = 0; a < 4; ++a)
       for (int d = 0; d < 3; ++d) verts[e * 12 + a * 3 + d] = ctx->vxyz[3 * ctx->etov[4 * k + a] + d];
     double er = ctx->eps_r.empty() ? 1.0 : ctx->eps_r[k];
@@ -312,6 +329,8 @@ wadg_status rebuild_typed(wadg_ctx* ctx) {
   }
   CK(dalloc(ctx->geo, geo.size() * 8));
   CK(cudaMemcpy(ctx->geo.p, geo.data(), geo.size() * 8, cudaMemcpyHostToDevice));
+  CK(dalloc(ctx->fnrm, fn.size() * sizeof(Real)));
+  CK(cudaMemcpy(ctx->fnrm.p, fn.data(), fn.size() * sizeof(Real), cudaMemcpyHostToDevice));
   CK(dalloc(ctx->verts, verts.size() * 8));
   CK(cudaMemcpy(ctx->verts.p, verts.data(), verts.size() * 8, cudaMemcpyHostToDevice));
   CK(dalloc(ctx->mat, mat.size() * sizeof(Real)));
@@ -459,6 +478,7 @@ StageParams<Real> stage_params(wadg_ctx* ctx, int stage, double dt, double t, bo
   P.p = (Real*)ctx->p.p;
   P.resp = (Real*)ctx->rp.p;
   P.geo = (const double*)ctx->geo.p;
+  P.fnrm = (const Real*)ctx->fnrm.p;
   P.mat = (const Real*)ctx->mat.p;
   P.nbr = (const int*)ctx->nbr.p;
   P.code = (const unsigned char*)ctx->code.p;
@@ -708,7 +728,7 @@ wadg_status wadg_destroy(wadg_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   invalidate_graphs(ctx);
-  for (DevPtr* d : {&ctx->q[0], &ctx->q[1], &ctx->rq, &ctx->p, &ctx->rp, &ctx->geo, &ctx->mat,
+  for (DevPtr* d : {&ctx->q[0], &ctx->q[1], &ctx->rq, &ctx->p, &ctx->rp, &ctx->geo, &ctx->fnrm, &ctx->mat,
                     &ctx->nbr, &ctx->code, &ctx->sig, &ctx->kap, &ctx->ops, &ctx->tabs,
                     &ctx->verts, &ctx->src, &ctx->srcw, &ctx->pr_elem, &ctx->pr_ell,
                     &ctx->pr_out, &ctx->obj, &ctx->tdev, &ctx->stepdev, &ctx->flag,
@@ -1242,7 +1262,7 @@ wadg_status wadg_memory_report(const wadg_ctx* ctx, size_t* bytes_state, size_t*
   if (bytes_pml_coeff) *bytes_pml_coeff = ctx->sig.bytes + ctx->kap.bytes;
   if (bytes_operators) *bytes_operators = ctx->ops.bytes + ctx->tabs.bytes;
   if (bytes_geometry)
-    *bytes_geometry = ctx->geo.bytes + ctx->mat.bytes + ctx->nbr.bytes + ctx->code.bytes;
+    *bytes_geometry = ctx->geo.bytes + ctx->fnrm.bytes + ctx->mat.bytes + ctx->nbr.bytes + ctx->code.bytes;
   return WADG_OK;
 }
 

@@ -176,19 +176,8 @@ stage_kernel(const StageParams<Real> P) {
       F[(e * Np + j) * CF + 6 + c] = pin[idx];
     }
   }
-  for (int idx = tid; idx < ne * 4; idx += NT) {
-    const int e = idx >> 2, f = idx & 3;
-    const double* g = P.geo + (int64_t)(eg0 + e) * 9;
-    double gx, gy, gz;
-    if (f == 0) { gx = -g[6]; gy = -g[7]; gz = -g[8]; }
-    else if (f == 1) { gx = -g[3]; gy = -g[4]; gz = -g[5]; }
-    else if (f == 2) { gx = g[0] + g[3] + g[6]; gy = g[1] + g[4] + g[7]; gz = g[2] + g[5] + g[8]; }
-    else { gx = -g[0]; gy = -g[1]; gz = -g[2]; }
-    const double mag = sqrt(gx * gx + gy * gy + gz * gz);
-    Real* nn = nrm + (e * 4 + f) * 4;
-    nn[0] = (Real)(gx / mag); nn[1] = (Real)(gy / mag); nn[2] = (Real)(gz / mag);
-    nn[3] = (Real)mag;   // Fscale = sJ / J = |grad of the face coordinate|
-  }
+  for (int idx = tid; idx < ne * 16; idx += NT)
+    nrm[idx] = P.fnrm[(int64_t)eg0 * 16 + idx];   // n_x, n_y, n_z, Fscale per face
   for (int idx = tid; idx < ne * 9; idx += NT) {
     const int e = idx / 9, k = idx - e * 9;
     met[e * 12 + k] = (Real)P.geo[(int64_t)eg0 * 9 + idx];

@@ -259,8 +259,10 @@ struct Plan {
 
 constexpr int kTcThreads = 256;
 
+// PML blocks own all 512 TMEM columns of an SM (one block per SM); non-PML
+// blocks take 256, two per SM, so they must fit two blocks' registers.
 template <int N, bool PML>
-__global__ void __launch_bounds__(kTcThreads, 1) tc_stage_kernel(const StageParams<float> P) {
+__global__ void __launch_bounds__(kTcThreads, PML ? 1 : 2) tc_stage_kernel(const StageParams<float> P) {
   using PL = Plan<N, PML>;
   constexpr int Np = PL::Np, Nfp = PL::Nfp, NF = PL::NF, Nq = PL::Nq, T = PL::T;
   constexpr int NpK = PL::NpK, NFK = PL::NFK, NqK = PL::NqK, NpP = PL::NpP;
@@ -364,33 +366,45 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_stage_kernel(const StagePara
   // issued one tile ahead so their latency overlaps the previous tile's work
   constexpr int NqP = (Nq + 3) & ~3;
   constexpr int EH = (T + 1) / 2;
-  auto load_nbr = [&](int tile, float (&Ep)[FT][3], float (&Hp)[FT][3], float (&ZPv)[FT]) {
+  // level 1 (no use of the loaded values): neighbour ids and face codes
+  auto load_nbr_idx = [&](int tile, int (&nbv)[FT], int (&codev)[FT]) {
     const int b = tile / tiles_per_batch;
     const int t0 = (tile - b * tiles_per_batch) * T;
     const int ne = min(T, P.n_elem - t0);
     const int eg0 = P.e_begin + t0;
+#pragma unroll
+    for (int u = 0; u < FT; ++u) {
+      const int task = tid + u * kTcThreads;
+      nbv[u] = -1;
+      codev[u] = 0;
+      if (task < ne * NF) {
+        const int e = task / NF, f = (task - e * NF) / Nfp;
+        nbv[u] = P.nbr[(eg0 + e) * 4 + f];
+        codev[u] = P.code[(eg0 + e) * 4 + f];
+      }
+    }
+  };
+  // level 2: the neighbour traces themselves (issued once the ids are in)
+  auto load_nbr_val = [&](int tile, const int (&nbv)[FT], const int (&codev)[FT],
+                          float (&Ep)[FT][3], float (&Hp)[FT][3], float (&ZPv)[FT]) {
+    const int b = tile / tiles_per_batch;
+    const int t0 = (tile - b * tiles_per_batch) * T;
+    const int ne = min(T, P.n_elem - t0);
     const float* qin = P.qin + (int64_t)b * P.strideQ;
 #pragma unroll
     for (int u = 0; u < FT; ++u) {
       const int task = tid + u * kTcThreads;
-      ZPv[u] = 0.f;
-      if (task < ne * NF) {
-        const int e = task / NF, fm = task - e * NF;
+      ZPv[u] = -1.f;   // marks the PEC mirror
+#pragma unroll
+      for (int c = 0; c < 3; ++c) { Ep[u][c] = 0.f; Hp[u][c] = 0.f; }
+      if (task < ne * NF && nbv[u] >= 0) {
+        const int fm = task % NF;
         const int f = fm / Nfp, m = fm - f * Nfp;
-        const int eg = eg0 + e;
-        const int nb = P.nbr[eg * 4 + f];
-        if (nb >= 0) {
-          const int code = P.code[eg * 4 + f];
-          const int np2 = fperm[(f * 24 + code) * Nfp + m];
-          const float* qn = qin + (int64_t)nb * 6 * Np + np2;
+        const int np2 = fperm[(f * 24 + codev[u]) * Nfp + m];
+        const float* qn = qin + (int64_t)nbv[u] * 6 * Np + np2;
 #pragma unroll
-          for (int c = 0; c < 3; ++c) { Ep[u][c] = qn[c * Np]; Hp[u][c] = qn[(3 + c) * Np]; }
-          ZPv[u] = P.mat[nb * 3 + 2];
-        } else {
-          ZPv[u] = -1.f;   // marks the PEC mirror
-#pragma unroll
-          for (int c = 0; c < 3; ++c) { Ep[u][c] = 0.f; Hp[u][c] = 0.f; }
-        }
+        for (int c = 0; c < 3; ++c) { Ep[u][c] = qn[c * Np]; Hp[u][c] = qn[(3 + c) * Np]; }
+        ZPv[u] = P.mat[nbv[u] * 3 + 2];
       }
     }
   };
@@ -413,35 +427,43 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_stage_kernel(const StagePara
       }
     }
   };
-  auto load_geo = [&](int tile, float* gb) {
+  // geometry and material of a tile: raw loads first, arithmetic later.
+  // Thread tid < 4 ne handles face tid&3 of element tid>>2, tid < 9 ne one
+  // metric entry, tid < 3 ne one material entry.
+  static_assert(16 * T <= kTcThreads, "one geometry item per thread");
+  // geometry and material of a tile, loaded a tile ahead and stored after
+  // this tile's flux: normal and Fscale (16 per element), metric (9), 1/eps,
+  // 1/mu, Z (3); thread tid carries at most one item of each
+  auto load_geo_raw = [&](int tile, float& nv, double& mv, float& matv) {
     const int b = tile / tiles_per_batch;
     const int t0 = (tile - b * tiles_per_batch) * T;
     const int ne = min(T, P.n_elem - t0);
     const int eg0 = P.e_begin + t0;
-    for (int idx = tid; idx < ne * 4; idx += kTcThreads) {
-      const int e = idx >> 2, f = idx & 3;
-      const double* g = P.geo + (int64_t)(eg0 + e) * 9;
-      double gx, gy, gz;
-      if (f == 0) { gx = -g[6]; gy = -g[7]; gz = -g[8]; }
-      else if (f == 1) { gx = -g[3]; gy = -g[4]; gz = -g[5]; }
-      else if (f == 2) { gx = g[0] + g[3] + g[6]; gy = g[1] + g[4] + g[7]; gz = g[2] + g[5] + g[8]; }
-      else { gx = -g[0]; gy = -g[1]; gz = -g[2]; }
-      const double mag = sqrt(gx * gx + gy * gy + gz * gz);
-      float* nn = gb + e * 28 + f * 4;
-      nn[0] = (float)(gx / mag); nn[1] = (float)(gy / mag); nn[2] = (float)(gz / mag);
-      nn[3] = (float)mag;
-    }
-    for (int idx = tid; idx < ne * 9; idx += kTcThreads) {
-      const int e = idx / 9, k = idx - e * 9;
-      gb[e * 28 + 16 + k] = (float)P.geo[(int64_t)eg0 * 9 + idx];
-    }
+    if (tid < ne * 16) nv = P.fnrm[(int64_t)eg0 * 16 + tid];
+    if (tid < ne * 9) mv = P.geo[(int64_t)eg0 * 9 + tid];
+    if (tid < ne * 3) matv = P.mat[eg0 * 3 + tid];
+  };
+  // layout per element (28 floats): n, Fscale of the 4 faces | metric (9) |
+  // 1/eps, 1/mu, Z
+  auto store_geo = [&](int tile, float nv, double mv, float matv, float* gb) {
+    const int b = tile / tiles_per_batch;
+    const int t0 = (tile - b * tiles_per_batch) * T;
+    const int ne = min(T, P.n_elem - t0);
+    if (tid < ne * 16) gb[(tid >> 4) * 28 + (tid & 15)] = nv;
+    if (tid < ne * 9) gb[(tid / 9) * 28 + 16 + tid % 9] = (float)mv;
+    if (tid < ne * 3) gb[(tid / 3) * 28 + 25 + tid % 3] = matv;
   };
   float Ep[FT][3], Hp[FT][3], ZPv[FT];
+  int nbv[FT], codev[FT];
   float sgv[PML ? EH : 1][3];
+  float nv = 0.f, matv = 0.f;
+  double mv = 0.0;
   if ((int)blockIdx.x < ntiles) {
-    load_nbr(blockIdx.x, Ep, Hp, ZPv);
+    load_nbr_idx(blockIdx.x, nbv, codev);
+    load_nbr_val(blockIdx.x, nbv, codev, Ep, Hp, ZPv);
     load_sig(blockIdx.x, sgv);
-    load_geo(blockIdx.x, geo);
+    load_geo_raw(blockIdx.x, nv, mv, matv);
+    store_geo(blockIdx.x, nv, mv, matv, geo);
   }
 
   int it = 0;
@@ -470,6 +492,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_stage_kernel(const StagePara
     float* resp = P.resp + (int64_t)b * P.strideP;
 
     if (tid == 0) flags[0] = 0;
+    if (next < ntiles) {
+      load_nbr_idx(next, nbv, codev);   // consumed after this tile's flux
+      load_geo_raw(next, nv, mv, matv);
+    }
     asm volatile("cp.async.wait_group 1;" ::: "memory");   // this tile's copies landed
     __syncthreads();
     for (int s = tid; s < P.nsrc; s += kTcThreads) {
@@ -487,6 +513,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_stage_kernel(const StagePara
         *reinterpret_cast<float*>(smem + PL::oBF + cofs(6 * T + e * 6 + c, j, PL::SBB_V, PL::LB)) =
             to_tf32(SP[idx]);
     }
+    // ---- volume and V_q products need only the field operand: start them now
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (tid == 0) {
+      constexpr uint32_t idV = idesc_tf32(128, PL::NV);
+      for (int d = 0; d < 3; ++d) {
+        const uint32_t oa = d == 0 ? PL::oDr : (d == 1 ? PL::oDs : PL::oDt);
+        const uint32_t col = d == 0 ? PL::cDr : (d == 1 ? PL::cDs : PL::cDt);
+        for (int k = 0; k < NpK / 8; ++k)
+          mma_tf32(tmem + col, make_desc(sbase + oa + 256 * k, 128, PL::SBO_V),
+                   make_desc(sbase + PL::oBF + 2 * PL::LB * k, PL::LB, PL::SBB_V), idV, k > 0);
+      }
+      if (PML) {
+        constexpr uint32_t idQ = idesc_tf32(128, PL::NQ);
+        for (int k = 0; k < NpK / 8; ++k)
+          mma_tf32(tmem + PL::cVq, make_desc(sbase + PL::oVq + 256 * k, 128, PL::SBO_V),
+                   make_desc(sbase + PL::oBF + 2 * PL::LB * k, PL::LB, PL::SBB_V), idQ, k > 0);
+      }
+    }
     // ---- upwind flux, scaled by Fscale, into the B operand of LIFT
 #pragma unroll
     for (int u = 0; u < FT; ++u) {
@@ -494,7 +541,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_stage_kernel(const StagePara
       if (task >= ne * NF) continue;
       const int e = task / NF, fm = task - e * NF;
       const int f = fm / Nfp;
-      const int eg = eg0 + e;
       const int ni = Fmask[fm];
       const float* nn = geo + e * 28 + f * 4;
       const float nx = nn[0], ny = nn[1], nz = nn[2], fsc = nn[3];
@@ -502,7 +548,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_stage_kernel(const StagePara
       float Em[3], Hm[3], Eo[3], Ho[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) { Em[c] = sq[c * Np]; Hm[c] = sq[(3 + c) * Np]; }
-      const float ZM = P.mat[eg * 3 + 2];
+      const float ZM = geo[e * 28 + 27];
       float ZP = ZPv[u];
       if (ZP < 0.f) {   // perfect electric conductor: mirror state
         ZP = ZM;
@@ -534,33 +580,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_stage_kernel(const StagePara
             to_tf32(fo[c]);
     }
     if (next < ntiles) {
-      load_nbr(next, Ep, Hp, ZPv);
-      load_geo(next, geo_next);
+      load_nbr_val(next, nbv, codev, Ep, Hp, ZPv);
+      store_geo(next, nv, mv, matv, geo_next);
     }
     fence_async_smem();
     fence_before();
     __syncthreads();
     fence_after();
 
-    // ---- products: volume (3), LIFT, V_q
+    // ---- LIFT product; one commit covers every product issued so far
     if (tid == 0) {
       constexpr uint32_t idV = idesc_tf32(128, PL::NV);
-      for (int d = 0; d < 3; ++d) {
-        const uint32_t oa = d == 0 ? PL::oDr : (d == 1 ? PL::oDs : PL::oDt);
-        const uint32_t col = d == 0 ? PL::cDr : (d == 1 ? PL::cDs : PL::cDt);
-        for (int k = 0; k < NpK / 8; ++k)
-          mma_tf32(tmem + col, make_desc(sbase + oa + 256 * k, 128, PL::SBO_V),
-                   make_desc(sbase + PL::oBF + 2 * PL::LB * k, PL::LB, PL::SBB_V), idV, k > 0);
-      }
       for (int k = 0; k < NFK / 8; ++k)
         mma_tf32(tmem + PL::cL, make_desc(sbase + PL::oL + 256 * k, 128, PL::SBO_L),
                  make_desc(sbase + PL::oBFL + 2 * PL::LB * k, PL::LB, PL::SBB_L), idV, k > 0);
-      if (PML) {
-        constexpr uint32_t idQ = idesc_tf32(128, PL::NQ);
-        for (int k = 0; k < NpK / 8; ++k)
-          mma_tf32(tmem + PL::cVq, make_desc(sbase + PL::oVq + 256 * k, 128, PL::SBO_V),
-                   make_desc(sbase + PL::oBF + 2 * PL::LB * k, PL::LB, PL::SBB_V), idQ, k > 0);
-      }
       mma_commit(saddr(mbar));
     }
     bool ok = mbar_wait(saddr(mbar), phase);
@@ -658,7 +691,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_stage_kernel(const StagePara
 #pragma unroll
         for (int c = 0; c < 3; ++c) CH[c] -= jt * (float)sd.dir[c] * w;
       }
-      const float ie = P.mat[eg * 3 + 0], im = P.mat[eg * 3 + 1];
+      const float ie = geo[e * 28 + 25], im = geo[e * 28 + 26];
       const float rhs[6] = {ie * CH[0], ie * CH[1], ie * CH[2], -im * CE[0], -im * CE[1], -im * CE[2]};
       if (!PML) {
 #pragma unroll
