@@ -161,6 +161,25 @@ __device__ __forceinline__ void tld_6x4(uint32_t a0, uint32_t a1, uint32_t a2, u
   tld_6x2(a2, a3, v + 12);
 }
 
+// named barrier 1 among the compute warps (warp-aligned, nthreads a multiple of 32)
+__device__ __forceinline__ void cbar_sync(int nthreads) {
+  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+// the same barrier with an AND reduction of a per-thread flag
+__device__ __forceinline__ bool cbar_and(int nthreads, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "r"(nthreads)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+
 // 4-byte asynchronous global -> shared copies
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(saddr(dst)), "l"(src) : "memory");
@@ -209,10 +228,10 @@ struct Plan {
   // A operands
   static constexpr uint32_t oPq = 0;
   static constexpr uint32_t oL = PML ? oPq + G_p * SBO_Q : 0;
-  static constexpr uint32_t oDr = oL + G_p * SBO_L;
-  static constexpr uint32_t oDs = oDr + G_p * SBO_V;
-  static constexpr uint32_t oDt = oDs + G_p * SBO_V;
-  static constexpr uint32_t oVq = oDt + G_p * SBO_V;
+  // Dr, Ds, Dt stacked as one operator of 3 Np rows (row d Np + i)
+  static constexpr int RV = rup8(3 * Np);
+  static constexpr uint32_t oVol = oL + G_p * SBO_L;
+  static constexpr uint32_t oVq = oVol + (RV / 8) * SBO_V;
   // B operands
   static constexpr uint32_t oBF = PML ? oVq + 16 * SBO_V : oVq;
   static constexpr int ROWS_F = PML ? NQ : NV;        // E,H (+ P) rows
@@ -226,62 +245,86 @@ struct Plan {
   static constexpr uint32_t SET = (PML ? 4 : 2) * TSB;  // q, res (+ P, res of P)
   static constexpr uint32_t oST = oGeo + 2 * T * 28 * 4;  // two staging sets
   static constexpr uint32_t oMisc = oST + 2 * SET;
+  // misc: 8 mbarriers | TMEM slot | flags | tile source list (64) | cached
+  // (batch, element) of the first 64 sources
+  static constexpr uint32_t MISC_BYTES = 1024;
   // epilogue scratch: the node rows of the products copied out of TMEM so that
   // every warp can share the per-node work.  PML: the volume/LIFT columns go
   // to the field-operand buffers (free once the first products are done), the
   // P_q columns to the (t, z) buffer (free once P_q is done).
   static constexpr uint32_t DV_BYTES = T * 24 * Np * 4;
   static constexpr uint32_t DP_BYTES = T * 12 * Np * 4;
-  static constexpr uint32_t oDV = PML ? oBF : oMisc + 64 * 4 + 64;
+  static constexpr uint32_t oDV = PML ? oBF : oMisc + MISC_BYTES;
   static constexpr uint32_t oDP = oBTZ;
   static_assert(!PML || oDV + DV_BYTES <= oBTZ, "volume/LIFT dump");
   static_assert(!PML || oDP + DP_BYTES <= oRS, "P_q dump");
-  static constexpr uint32_t bytes_used = PML ? oMisc + 64 * 4 + 64 : oDV + DV_BYTES;
+  static constexpr uint32_t bytes_used = PML ? oMisc + MISC_BYTES : oDV + DV_BYTES;
   // residency follows the tensor-memory budget of 512 columns per SM: one PML
-  // block (512 columns) or two non-PML blocks (256 each) per SM, enforced by
-  // the shared-memory request so that no block waits in tcgen05.alloc
+  // block (512 columns) per SM, enforced by the shared-memory request so that
+  // no block waits in tcgen05.alloc; non-PML blocks (128 columns) are limited
+  // to two per SM by their shared memory and registers
   static constexpr uint32_t min_bytes = PML ? 116 * 1024 : 100 * 1024;
   static constexpr uint32_t bytes = bytes_used < min_bytes ? min_bytes : bytes_used;
-  static constexpr uint32_t TMEM_COLS = PML ? 512 : 256;
-  // TMEM column bases
-  static constexpr uint32_t cDr = 0, cDs = NV, cDt = 2 * NV, cL = 3 * NV;
-  static constexpr uint32_t cVq = 4 * NV, cPq = 4 * NV + NQ;
-  static_assert(!PML || 4 * NV + 2 * NQ <= 512, "TMEM columns");
-  static_assert(PML || 4 * NV <= 256, "TMEM columns");
+  static constexpr uint32_t TMEM_COLS = PML ? 512 : 128;
+  // TMEM column bases: stacked derivatives (lanes d Np + i), LIFT, V_q, P_q
+  static constexpr uint32_t cV = 0, cL = NV;
+  static constexpr uint32_t cVq = 2 * NV, cPq = 2 * NV + NQ;
+  static_assert(!PML || 2 * NV + 2 * NQ <= 512, "TMEM columns");
+  static_assert(PML || 2 * NV <= 128, "TMEM columns");
+  static_assert(3 * Np <= 128, "stacked derivative operators fit one M=128 tile");
   static_assert(Nq <= 128 || !PML, "V_q rows must fit one M=128 tile");
   static_assert(Np <= 64, "node rows");
   // every A operand read (128 rows from its start) stays inside the block
   static_assert(oPq + 16 * SBO_Q <= bytes || !PML, "P_q span");
   static_assert(oL + 16 * SBO_L <= bytes, "LIFT span");
-  static_assert(oDt + 16 * SBO_V <= bytes, "Dt span");
+  static_assert(oVol + 16 * SBO_V <= bytes, "volume operator span");
   static_assert(bytes <= 227 * 1024, "shared memory");
 };
 
-constexpr int kTcThreads = 256;
+// Warp roles.  The compute warps (16 in a PML block, one block per SM; 8 in a
+// non-PML block, two per SM) stage the tile, build the operands, compute the
+// flux and run the epilogues; they synchronise among themselves on a named
+// barrier.  One extra MMA warp, whose lane 0 issues every product, waits for
+// "operand ready" mbarriers the compute warps arrive on and commits each
+// product to a "product done" mbarrier, so that issuing the products (about
+// a hundred cycles per instruction for the issuing thread) stays off the
+// compute warps' path.
+template <bool PML>
+struct TcWarps {
+  static constexpr int compute = PML ? 16 : 8;
+  static constexpr int threads = 32 * (compute + 1);
+};
 
-// PML blocks own all 512 TMEM columns of an SM (one block per SM); non-PML
-// blocks take 256, two per SM, so they must fit two blocks' registers.
 template <int N, bool PML>
-__global__ void __launch_bounds__(kTcThreads, PML ? 1 : 2) tc_stage_kernel(const StageParams<float> P) {
+__global__ void __launch_bounds__(TcWarps<PML>::threads, PML ? 1 : 2) tc_stage_kernel(const StageParams<float> P) {
   using PL = Plan<N, PML>;
+  constexpr int NW = TcWarps<PML>::compute;
+  constexpr int kTcThreads = 32 * NW;          // compute threads
+  constexpr int kAll = TcWarps<PML>::threads;
+  constexpr int NGRP = NW / 4;                 // warps sharing a TMEM lane quadrant
   constexpr int Np = PL::Np, Nfp = PL::Nfp, NF = PL::NF, Nq = PL::Nq, T = PL::T;
-  constexpr int NpK = PL::NpK, NFK = PL::NFK, NqK = PL::NqK, NpP = PL::NpP;
+  constexpr int NpK = PL::NpK, NFK = PL::NFK, NqK = PL::NqK;
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int quad = warp & 3, half = warp >> 2;   // TMEM lane quadrant, element half
+  const bool mma_warp = warp == NW;
+  const int quad = warp & 3, grp = warp >> 2;   // TMEM lane quadrant, element group
   const uint32_t sbase = saddr(smem);
   float* RS = reinterpret_cast<float*>(smem + PL::oRS);     // [T][6][NpP]
   float* geo = reinterpret_cast<float*>(smem + PL::oGeo);   // [2][T][28]: n,Fscale x4 | metric
+  // mbarriers: products done [0] volume (+ V_q), [1] LIFT, [2] P_q; operands
+  // ready [3] fields, [4] flux, [5] (t, z); [6] final drain of the MMA warp
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + PL::oMisc);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + PL::oMisc + 8);
-  int* flags = reinterpret_cast<int*>(smem + PL::oMisc + 16);   // [0] source count
-  int* srcl = reinterpret_cast<int*>(smem + PL::oMisc + 64);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + PL::oMisc + 64);
+  int* flags = reinterpret_cast<int*>(smem + PL::oMisc + 68);   // [0] source count
+  int* srcl = reinterpret_cast<int*>(smem + PL::oMisc + 80);
+  int* srcc = reinterpret_cast<int*>(smem + PL::oMisc + 336);   // [64][2] batch, element
+  constexpr int kSrcCache = 64;
   const float* tops = reinterpret_cast<const float*>(P.tcops);
   const unsigned char* Fmask = P.tabs;
   const unsigned char* fperm = P.tabs + NF;
 
   // ---- prologue: zero the operand buffers, stage the operators
-  for (uint32_t i = tid; i < PL::oGeo / 16; i += kTcThreads)
+  for (uint32_t i = tid; i < PL::oGeo / 16; i += kAll)
     reinterpret_cast<float4*>(smem)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   __syncthreads();
   {
@@ -290,28 +333,31 @@ __global__ void __launch_bounds__(kTcThreads, PML ? 1 : 2) tc_stage_kernel(const
     const float* gL = gDr + 3 * Np * Np;
     const float* gVq = gL + Np * NF;
     const float* gPq = gVq + Nq * Np;
-    for (int idx = tid; idx < 3 * Np * Np; idx += kTcThreads) {
-      const int d = idx / (Np * Np), r = idx - d * Np * Np, i = r / Np, j = r - i * Np;
-      const uint32_t base = d == 0 ? PL::oDr : (d == 1 ? PL::oDs : PL::oDt);
-      *reinterpret_cast<float*>(smem + base + cofs(i, j, PL::SBO_V, PL::LA)) = gDr[idx];
+    for (int idx = tid; idx < 3 * Np * Np; idx += kAll) {
+      const int row = idx / Np, j = idx - row * Np;   // row d Np + i of [Dr; Ds; Dt]
+      *reinterpret_cast<float*>(smem + PL::oVol + cofs(row, j, PL::SBO_V, PL::LA)) = gDr[idx];
     }
-    for (int idx = tid; idx < Np * NF; idx += kTcThreads) {
+    for (int idx = tid; idx < Np * NF; idx += kAll) {
       const int i = idx / NF, f = idx - i * NF;
       *reinterpret_cast<float*>(smem + PL::oL + cofs(i, f, PL::SBO_L, PL::LA)) = gL[idx];
     }
     if (PML) {
-      for (int idx = tid; idx < Nq * Np; idx += kTcThreads) {
+      for (int idx = tid; idx < Nq * Np; idx += kAll) {
         const int q = idx / Np, j = idx - q * Np;
         *reinterpret_cast<float*>(smem + PL::oVq + cofs(q, j, PL::SBO_V, PL::LA)) = gVq[idx];
       }
-      for (int idx = tid; idx < Np * Nq; idx += kTcThreads) {
+      for (int idx = tid; idx < Np * Nq; idx += kAll) {
         const int i = idx / Nq, q = idx - i * Nq;
         *reinterpret_cast<float*>(smem + PL::oPq + cofs(i, q, PL::SBO_Q, PL::LA)) = gPq[idx];
       }
     }
   }
+  for (int s = tid; s < min(P.nsrc, kSrcCache); s += kAll) {
+    srcc[2 * s] = P.src[s].batch;
+    srcc[2 * s + 1] = P.src[s].elem;
+  }
   if (tid == 0) {
-    mbar_init(saddr(mbar), 1);
+    for (int i = 0; i < 7; ++i) mbar_init(saddr(mbar + i), i >= 3 && i <= 5 ? NW : 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tmem_alloc(saddr(tmem_slot), PL::TMEM_COLS);
@@ -321,8 +367,25 @@ __global__ void __launch_bounds__(kTcThreads, PML ? 1 : 2) tc_stage_kernel(const
   fence_after();
   const uint32_t tmem = *tmem_slot;
   const uint32_t lane_base = static_cast<uint32_t>(quad * 32) << 16;
-  uint32_t phase = 0;
+  uint32_t phase[3] = {0, 0, 0};   // parity of each product barrier's next completion
   bool failed = false;
+  // bounded wait of every compute thread for product barrier i; false if any
+  // thread gave up
+  auto wait_bar = [&](int i) -> bool {
+    const bool ok = mbar_wait(saddr(mbar + i), phase[i]);
+    if (ok) phase[i] ^= 1;
+    const bool all = cbar_and(kTcThreads, ok);
+    fence_after();
+    return all;
+  };
+  // a compute warp's operand writes are complete: make them visible to the
+  // tensor core and count the warp on "operand ready" barrier i
+  auto signal_ready = [&](int i) {
+    fence_async_smem();
+    fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(saddr(mbar + i));
+  };
 
   const double tbase = P.t_dev ? *P.t_dev : P.t;
   const double tst = tbase + P.rk_c * P.dt;
@@ -359,13 +422,13 @@ __global__ void __launch_bounds__(kTcThreads, PML ? 1 : 2) tc_stage_kernel(const
       }
     }
   };
-  if ((int)blockIdx.x < ntiles) stage_tile(blockIdx.x, 0);
+  if (!mma_warp && (int)blockIdx.x < ntiles) stage_tile(blockIdx.x, 0);
   asm volatile("cp.async.commit_group;" ::: "memory");
 
   // per-tile scattered loads (neighbour traces, sigma samples, geometry),
   // issued one tile ahead so their latency overlaps the previous tile's work
   constexpr int NqP = (Nq + 3) & ~3;
-  constexpr int EH = (T + 1) / 2;
+  constexpr int EH = (T + NGRP - 1) / NGRP;
   // level 1 (no use of the loaded values): neighbour ids and face codes
   auto load_nbr_idx = [&](int tile, int (&nbv)[FT], int (&codev)[FT]) {
     const int b = tile / tiles_per_batch;
@@ -417,7 +480,7 @@ __global__ void __launch_bounds__(kTcThreads, PML ? 1 : 2) tc_stage_kernel(const
     const int q = quad * 32 + lane;
 #pragma unroll
     for (int k = 0; k < (PML ? EH : 1); ++k) {
-      const int e = half + 2 * k;
+      const int e = grp + NGRP * k;
       sgv[k][0] = sgv[k][1] = sgv[k][2] = 0.f;
       if (e < ne && q < Nq) {
         const int64_t sb = (int64_t)(ep0 + e) * 3 * NqP + q;
@@ -453,6 +516,53 @@ __global__ void __launch_bounds__(kTcThreads, PML ? 1 : 2) tc_stage_kernel(const
     if (tid < ne * 9) gb[(tid / 9) * 28 + 16 + tid % 9] = (float)mv;
     if (tid < ne * 3) gb[(tid / 3) * 28 + 25 + tid % 3] = matv;
   };
+  if (mma_warp) {
+    // ---- MMA warp: lane 0 issues every product of every tile of this block
+    if (lane == 0) {
+      uint32_t rph[3] = {0, 0, 0};   // parity of the operand-ready barriers 3, 4, 5
+      bool issued = false, mfail = false;
+      auto wait_ready = [&](int i) -> bool {
+        const bool ok = mbar_wait(saddr(mbar + 3 + i), rph[i]);
+        rph[i] ^= 1;
+        fence_after();
+        return ok;
+      };
+      constexpr uint32_t idV = idesc_tf32(128, PL::NV);
+      constexpr uint32_t idQ = idesc_tf32(128, PL::NQ);
+      for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        if (!wait_ready(0)) { mfail = true; break; }
+        for (int k = 0; k < NpK / 8; ++k)
+          mma_tf32(tmem + PL::cV, make_desc(sbase + PL::oVol + 256 * k, 128, PL::SBO_V),
+                   make_desc(sbase + PL::oBF + 2 * PL::LB * k, PL::LB, PL::SBB_V), idV, k > 0);
+        if (PML) {
+          for (int k = 0; k < NpK / 8; ++k)
+            mma_tf32(tmem + PL::cVq, make_desc(sbase + PL::oVq + 256 * k, 128, PL::SBO_V),
+                     make_desc(sbase + PL::oBF + 2 * PL::LB * k, PL::LB, PL::SBB_V), idQ, k > 0);
+          mma_commit(saddr(mbar + 0));
+        }
+        issued = true;
+        if (!wait_ready(1)) { mfail = true; break; }
+        for (int k = 0; k < NFK / 8; ++k)
+          mma_tf32(tmem + PL::cL, make_desc(sbase + PL::oL + 256 * k, 128, PL::SBO_L),
+                   make_desc(sbase + PL::oBFL + 2 * PL::LB * k, PL::LB, PL::SBB_L), idV, k > 0);
+        mma_commit(saddr(mbar + 1));
+        if (PML) {
+          if (!wait_ready(2)) { mfail = true; break; }
+          for (int k = 0; k < NqK / 8; ++k)
+            mma_tf32(tmem + PL::cPq, make_desc(sbase + PL::oPq + 256 * k, 128, PL::SBO_Q),
+                     make_desc(sbase + PL::oBTZ + 2 * PL::LB * k, PL::LB, PL::SBB_Q), idQ, k > 0);
+          mma_commit(saddr(mbar + 2));
+        }
+      }
+      if (mfail) atomicExch(P.err, 1);
+      // every product this thread issued completes before the memory is released
+      if (issued) {
+        mma_commit(saddr(mbar + 6));
+        mbar_wait(saddr(mbar + 6), 0);
+      }
+    }
+    __syncwarp();
+  } else {
   float Ep[FT][3], Hp[FT][3], ZPv[FT];
   int nbv[FT], codev[FT];
   float sgv[PML ? EH : 1][3];
@@ -485,7 +595,6 @@ __global__ void __launch_bounds__(kTcThreads, PML ? 1 : 2) tc_stage_kernel(const
     const int ne = min(T, P.n_elem - t0);
     const int eg0 = P.e_begin + t0;
     const int ep0 = eg0 - P.K0;
-    const int nval = ne * 6 * Np;
     float* qout = P.qout + (int64_t)b * P.strideQ;
     float* resq = P.resq + (int64_t)b * P.strideQ;
     float* pio = P.p + (int64_t)b * P.strideP;
@@ -497,43 +606,36 @@ __global__ void __launch_bounds__(kTcThreads, PML ? 1 : 2) tc_stage_kernel(const
       load_geo_raw(next, nv, mv, matv);
     }
     asm volatile("cp.async.wait_group 1;" ::: "memory");   // this tile's copies landed
-    __syncthreads();
+    cbar_sync(kTcThreads);
     for (int s = tid; s < P.nsrc; s += kTcThreads) {
-      const SrcDev& sd = P.src[s];
-      if (sd.batch == b && sd.elem >= eg0 && sd.elem < eg0 + ne) {
+      const int sb = s < kSrcCache ? srcc[2 * s] : P.src[s].batch;
+      const int se = s < kSrcCache ? srcc[2 * s + 1] : P.src[s].elem;
+      if (sb == b && se >= eg0 && se < eg0 + ne) {
         const int slot = atomicAdd(&flags[0], 1);
         if (slot < 64) srcl[slot] = s;
       }
     }
-    // ---- B operand of the field products (TF32-rounded), from the staged blocks
-    for (int idx = tid; idx < nval; idx += kTcThreads) {
-      const int e = idx / (6 * Np), r = idx - e * 6 * Np, c = r / Np, j = r - c * Np;
-      *reinterpret_cast<float*>(smem + PL::oBF + cofs(e * 6 + c, j, PL::SBB_V, PL::LB)) = to_tf32(SQ[idx]);
-      if (PML)
-        *reinterpret_cast<float*>(smem + PL::oBF + cofs(6 * T + e * 6 + c, j, PL::SBB_V, PL::LB)) =
-            to_tf32(SP[idx]);
-    }
-    // ---- volume and V_q products need only the field operand: start them now
-    fence_async_smem();
-    fence_before();
-    __syncthreads();
-    fence_after();
-    if (tid == 0) {
-      constexpr uint32_t idV = idesc_tf32(128, PL::NV);
-      for (int d = 0; d < 3; ++d) {
-        const uint32_t oa = d == 0 ? PL::oDr : (d == 1 ? PL::oDs : PL::oDt);
-        const uint32_t col = d == 0 ? PL::cDr : (d == 1 ? PL::cDs : PL::cDt);
-        for (int k = 0; k < NpK / 8; ++k)
-          mma_tf32(tmem + col, make_desc(sbase + oa + 256 * k, 128, PL::SBO_V),
-                   make_desc(sbase + PL::oBF + 2 * PL::LB * k, PL::LB, PL::SBB_V), idV, k > 0);
-      }
-      if (PML) {
-        constexpr uint32_t idQ = idesc_tf32(128, PL::NQ);
-        for (int k = 0; k < NpK / 8; ++k)
-          mma_tf32(tmem + PL::cVq, make_desc(sbase + PL::oVq + 256 * k, 128, PL::SBO_V),
-                   make_desc(sbase + PL::oBF + 2 * PL::LB * k, PL::LB, PL::SBB_V), idQ, k > 0);
+    // ---- B operand of the field products (TF32-rounded), from the staged
+    // blocks: one 16-byte core-matrix row (4 consecutive nodes of one
+    // (element, component) row) per task; rows of missing elements are skipped
+    {
+      constexpr int G4 = (Np + 3) / 4;
+      constexpr int NTASK = PL::ROWS_F * G4;
+      for (int task = tid; task < NTASK; task += kTcThreads) {
+        const int row = task / G4, g = task - row * G4;
+        const int rr = PML && row >= 6 * T ? row - 6 * T : row;
+        if (rr >= ne * 6) continue;
+        const float* src = (PML && row >= 6 * T ? SP : SQ) + rr * Np + 4 * g;
+        float4 v;
+        v.x = to_tf32(src[0]);
+        v.y = 4 * g + 1 < Np ? to_tf32(src[1]) : 0.f;
+        v.z = 4 * g + 2 < Np ? to_tf32(src[2]) : 0.f;
+        v.w = 4 * g + 3 < Np ? to_tf32(src[3]) : 0.f;
+        *reinterpret_cast<float4*>(smem + PL::oBF + cofs(row, 4 * g, PL::SBB_V, PL::LB)) = v;
       }
     }
+    // ---- the volume and V_q products need only the field operand
+    signal_ready(3);
     // ---- upwind flux, scaled by Fscale, into the B operand of LIFT
 #pragma unroll
     for (int u = 0; u < FT; ++u) {
@@ -579,81 +681,79 @@ __global__ void __launch_bounds__(kTcThreads, PML ? 1 : 2) tc_stage_kernel(const
         *reinterpret_cast<float*>(smem + PL::oBFL + cofs(e * 6 + c, fm, PL::SBB_L, PL::LB)) =
             to_tf32(fo[c]);
     }
+    signal_ready(4);   // LIFT operand
     if (next < ntiles) {
       load_nbr_val(next, nbv, codev, Ep, Hp, ZPv);
       store_geo(next, nv, mv, matv, geo_next);
     }
-    fence_async_smem();
-    fence_before();
-    __syncthreads();
-    fence_after();
 
-    // ---- LIFT product; one commit covers every product issued so far
-    if (tid == 0) {
-      constexpr uint32_t idV = idesc_tf32(128, PL::NV);
-      for (int k = 0; k < NFK / 8; ++k)
-        mma_tf32(tmem + PL::cL, make_desc(sbase + PL::oL + 256 * k, 128, PL::SBO_L),
-                 make_desc(sbase + PL::oBFL + 2 * PL::LB * k, PL::LB, PL::SBB_L), idV, k > 0);
-      mma_commit(saddr(mbar));
+    if (PML) {
+      if (!wait_bar(0)) { failed = true; break; }   // volume and V_q products
+      // ---- epilogue A1: eq. 9 at the quadrature points -> B of P_q
+      {
+        const int q = quad * 32 + lane;     // quadrature point of this lane
+        const float ie0 = 1.f / (float)P.eps0;
+#pragma unroll
+        for (int k = 0; k < EH; ++k) {       // warp-uniform loop over this group's elements
+          const int e = grp + NGRP * k;
+          if (e >= T) break;
+          float v[12];
+          tld_6x2(tmem + lane_base + PL::cVq + e * 6, tmem + lane_base + PL::cVq + 6 * T + e * 6, v);
+          if (e >= ne || q >= NqK) continue;
+          const float* sg = sgv[k];
+          float o[12];
+#pragma unroll
+          for (int u = 0; u < 3; ++u) {
+            const float su = sg[u], sv = sg[(u + 1) % 3], sw = sg[(u + 2) % 3];
+            // eq. 9 with kappa = 1: a = 1, b = (sv + sw - su)/eps0, c = sv sw/eps0^2 - b su/eps0
+            const float bc = (sv + sw - su) * ie0;
+            const float cc = sv * sw * ie0 * ie0 - bc * su * ie0;
+            const float dd = su * ie0;
+            o[u] = bc * v[u] + cc * v[6 + u];
+            o[3 + u] = bc * v[3 + u] + cc * v[9 + u];
+            o[6 + u] = v[u] - dd * v[6 + u];
+            o[9 + u] = v[3 + u] - dd * v[9 + u];
+          }
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            *reinterpret_cast<float*>(smem + PL::oBTZ + cofs(e * 6 + c, q, PL::SBB_Q, PL::LB)) =
+                to_tf32(o[c]);
+            *reinterpret_cast<float*>(smem + PL::oBTZ + cofs(6 * T + e * 6 + c, q, PL::SBB_Q, PL::LB)) =
+                to_tf32(o[6 + c]);
+          }
+        }
+      }
+      if (next < ntiles) load_sig(next, sgv);
+      signal_ready(5);   // P_q operand; the product overlaps the epilogue below
     }
-    bool ok = mbar_wait(saddr(mbar), phase);
-    phase ^= 1;
-    if (!__syncthreads_and(ok)) { failed = true; break; }
-    fence_after();
+    if (!wait_bar(1)) { failed = true; break; }
     const int nsrc_l = min(flags[0], 64);
 
-    // ---- epilogue A1 (PML): eq. 9 at the quadrature points -> B of P_q
-    if (PML) {
-      const int q = quad * 32 + lane;     // quadrature point of this lane
-      const float ie0 = 1.f / (float)P.eps0;
-#pragma unroll
-      for (int k = 0; k < EH; ++k) {       // warp-uniform loop over this half's elements
-        const int e = half + 2 * k;
-        if (e >= T) break;
-        float v[12];
-        tld_6x2(tmem + lane_base + PL::cVq + e * 6, tmem + lane_base + PL::cVq + 6 * T + e * 6, v);
-        if (e >= ne || q >= NqK) continue;
-        const float* sg = sgv[k];
-        float o[12];
-#pragma unroll
-        for (int u = 0; u < 3; ++u) {
-          const float su = sg[u], sv = sg[(u + 1) % 3], sw = sg[(u + 2) % 3];
-          // eq. 9 with kappa = 1: a = 1, b = (sv + sw - su)/eps0, c = sv sw/eps0^2 - b su/eps0
-          const float bc = (sv + sw - su) * ie0;
-          const float cc = sv * sw * ie0 * ie0 - bc * su * ie0;
-          const float dd = su * ie0;
-          o[u] = bc * v[u] + cc * v[6 + u];
-          o[3 + u] = bc * v[3 + u] + cc * v[9 + u];
-          o[6 + u] = v[u] - dd * v[6 + u];
-          o[9 + u] = v[3 + u] - dd * v[9 + u];
-        }
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-          *reinterpret_cast<float*>(smem + PL::oBTZ + cofs(e * 6 + c, q, PL::SBB_Q, PL::LB)) =
-              to_tf32(o[c]);
-          *reinterpret_cast<float*>(smem + PL::oBTZ + cofs(6 * T + e * 6 + c, q, PL::SBB_Q, PL::LB)) =
-              to_tf32(o[6 + c]);
-        }
-      }
-    }
-
-    if (next < ntiles) load_sig(next, sgv);
-
-    // ---- volume/LIFT columns of the node lanes -> shared memory
+    // ---- derivative and LIFT columns -> shared memory.  Lane d Np + i holds
+    // the d-th derivative at node i, lane i the LIFT term at node i.
     float* DV = reinterpret_cast<float*>(smem + PL::oDV);   // [T][24][Np]
-    if (quad * 32 < Np) {
-      const int i = quad * 32 + lane;
-      for (int e = half; e < T; e += 2) {
-        float d[24];   // dr | ds | dt | lift, 6 components each
-        tld_6x4(tmem + lane_base + PL::cDr + e * 6, tmem + lane_base + PL::cDs + e * 6,
-                tmem + lane_base + PL::cDt + e * 6, tmem + lane_base + PL::cL + e * 6, d);
-        if (e >= ne || i >= Np) continue;
+    if (quad * 32 < 3 * Np) {
+      const int L = quad * 32 + lane;
+      const int d = L / Np, i = L - d * Np;
+      for (int e = grp; e < T; e += NGRP) {
+        float v[12];   // derivative d of the 6 components | LIFT of the 6 components
+        if (quad * 32 < Np)
+          tld_6x2(tmem + lane_base + PL::cV + e * 6, tmem + lane_base + PL::cL + e * 6, v);
+        else
+          tld6(tmem + lane_base + PL::cV + e * 6, v);
+        if (e >= ne) continue;
+        if (L < 3 * Np) {
 #pragma unroll
-        for (int k = 0; k < 24; ++k) DV[(e * 24 + k) * Np + i] = d[k];
+          for (int c = 0; c < 6; ++c) DV[(e * 24 + d * 6 + c) * Np + i] = v[c];
+        }
+        if (quad * 32 < Np && L < Np) {
+#pragma unroll
+          for (int c = 0; c < 6; ++c) DV[(e * 24 + 18 + c) * Np + i] = v[6 + c];
+        }
       }
     }
     fence_before();
-    __syncthreads();
+    cbar_sync(kTcThreads);
     fence_after();
 
     // ---- epilogue A2 (all warps): curl + LIFT, rhs of E and H per (element, node)
@@ -704,33 +804,19 @@ __global__ void __launch_bounds__(kTcThreads, PML ? 1 : 2) tc_stage_kernel(const
         }
       } else {
 #pragma unroll
-        for (int c = 0; c < 6; ++c) RS[(e * 6 + c) * NpP + i] = rhs[c];
+        for (int c = 0; c < 6; ++c) RS[(e * 6 + c) * Np + i] = rhs[c];
       }
     }
 
     if (PML) {
-      // ---- P_q product
-      fence_async_smem();
-      fence_before();
-      __syncthreads();
-      fence_after();
-      if (tid == 0) {
-        constexpr uint32_t idQ = idesc_tf32(128, PL::NQ);
-        for (int k = 0; k < NqK / 8; ++k)
-          mma_tf32(tmem + PL::cPq, make_desc(sbase + PL::oPq + 256 * k, 128, PL::SBO_Q),
-                   make_desc(sbase + PL::oBTZ + 2 * PL::LB * k, PL::LB, PL::SBB_Q), idQ, k > 0);
-        mma_commit(saddr(mbar));
-      }
-      ok = mbar_wait(saddr(mbar), phase);
-      phase ^= 1;
-      if (!__syncthreads_and(ok)) { failed = true; break; }
-      fence_after();
+      // ---- the P_q product has had the volume/LIFT epilogue to complete
+      if (!wait_bar(2)) { failed = true; break; }
       fence_async_smem();   // the (t, z) buffer is reused below
       // ---- P_q columns of the node lanes -> shared memory
       float* DP = reinterpret_cast<float*>(smem + PL::oDP);   // [T][12][Np]
       if (quad * 32 < Np) {
         const int i = quad * 32 + lane;
-        for (int e = half; e < T; e += 2) {
+        for (int e = grp; e < T; e += NGRP) {
           float v[12];   // s | rhs of P
           tld_6x2(tmem + lane_base + PL::cPq + e * 6, tmem + lane_base + PL::cPq + 6 * T + e * 6, v);
           if (e >= ne || i >= Np) continue;
@@ -739,33 +825,47 @@ __global__ void __launch_bounds__(kTcThreads, PML ? 1 : 2) tc_stage_kernel(const
         }
       }
       fence_before();
-      __syncthreads();
+      cbar_sync(kTcThreads);
       fence_after();
-      // ---- epilogue B (all warps): Runge-Kutta update of E, H, P^E, P^H
-      for (int task = tid; task < ne * 6 * Np; task += kTcThreads) {
-        const int e = task / (6 * Np), r = task - e * 6 * Np, c = r / Np, i = r - c * Np;
-        const int li = task;   // == (e * 6 + c) * Np + i
+      // ---- epilogue B (all warps): Runge-Kutta update of E, H, P^E, P^H, two
+      // consecutive values of one element block per task (6 Np is even, so a
+      // pair never straddles two elements and stays 8-byte aligned)
+      for (int t2 = tid; t2 < ne * 3 * Np; t2 += kTcThreads) {
+        const int li = 2 * t2;                  // (e * 6 + c) * Np + i
+        const int e = li / (6 * Np);
+        const int di = li + e * 6 * Np;         // (e * 12 + c) * Np + i
+        const float2 sr = *reinterpret_cast<const float2*>(SR + li);
+        const float2 sq = *reinterpret_cast<const float2*>(SQ + li);
+        const float2 rs = *reinterpret_cast<const float2*>(RS + li);
+        const float2 ds = *reinterpret_cast<const float2*>(DP + di);
+        const float2 dz = *reinterpret_cast<const float2*>(DP + di + 6 * Np);
+        const float2 srp = *reinterpret_cast<const float2*>(SRP + li);
+        const float2 sp = *reinterpret_cast<const float2*>(SP + li);
+        float2 rr, qn, rp, pn;
+        rr.x = rka * sr.x + rdt * (rs.x - ds.x);
+        rr.y = rka * sr.y + rdt * (rs.y - ds.y);
+        qn.x = sq.x + rkb * rr.x;
+        qn.y = sq.y + rkb * rr.y;
+        rp.x = rka * srp.x + rdt * dz.x;
+        rp.y = rka * srp.y + rdt * dz.y;
+        pn.x = sp.x + rkb * rp.x;
+        pn.y = sp.y + rkb * rp.y;
         const int64_t gi = (int64_t)eg0 * 6 * Np + li;
-        const float rr = rka * SR[li] + rdt * (RS[(e * 6 + c) * NpP + i] - DP[(e * 12 + c) * Np + i]);
-        resq[gi] = rr;
-        qout[gi] = SQ[li] + rkb * rr;
         const int64_t pi = (int64_t)ep0 * 6 * Np + li;
-        const float rp = rka * SRP[li] + rdt * DP[(e * 12 + 6 + c) * Np + i];
-        resp[pi] = rp;
-        pio[pi] = SP[li] + rkb * rp;
+        *reinterpret_cast<float2*>(resq + gi) = rr;
+        *reinterpret_cast<float2*>(qout + gi) = qn;
+        *reinterpret_cast<float2*>(resp + pi) = rp;
+        *reinterpret_cast<float2*>(pio + pi) = pn;
       }
     }
     fence_before();
-    __syncthreads();
+    cbar_sync(kTcThreads);
     fence_after();
   }
 
   asm volatile("cp.async.wait_group 0;" ::: "memory");
-  if (failed) {
-    if (tid == 0) atomicExch(P.err, 1);
-    // let any product still in flight finish before the memory is released
-    mbar_wait(saddr(mbar), phase);
-  }
+  if (failed && tid == 0) atomicExch(P.err, 1);
+  }   // compute warps
   fence_before();
   __syncthreads();
   fence_after();
@@ -794,7 +894,7 @@ cudaError_t launch_n(const StageParams<float>& P, int nb, cudaStream_t s) {
   const long long tiles = (long long)((P.n_elem + PL::T - 1) / PL::T) * nb;
   const int per_sm = 512 / (int)PL::TMEM_COLS;
   const int grid = (int)std::min<long long>(tiles, (long long)per_sm * sms);
-  tc_stage_kernel<N, PML><<<grid, kTcThreads, PL::bytes, s>>>(Q);
+  tc_stage_kernel<N, PML><<<grid, TcWarps<PML>::threads, PL::bytes, s>>>(Q);
   return cudaGetLastError();
 }
 
