@@ -57,9 +57,22 @@ typedef enum {
  * coefficient sampling and the objective sums are evaluated in double. */
 typedef enum { WADG_FP64 = 0, WADG_FP32 = 1, WADG_TF32 = 2, WADG_BF16 = 3 } wadg_precision;
 
-/* PML implementation.  WAA: eqs. 26-29 (the paper's method).  STORED: the
- * per-element mass matrices of eqs. 10-15 (reserved).  EC: element-constant
- * coefficients (reserved). */
+/* PML implementation.
+ *   WAA     eqs. 26-29, the weight-adjusted terms with the coefficients
+ *           sampled at the volume quadrature nodes (the paper's method).
+ *   STORED  eqs. 10-13 with per-element weighted mass matrices (eq. 15):
+ *           for kappa = 1 the library stores M_k^-1 M_k^{b_u}, M_k^-1 M_k^{c_u}
+ *           and M_k^-1 M_k^{d_u} per PML element and axis (9 N_p^2 values;
+ *           (M^a)^-1 M_k and M_k^-1 M^{1/kappa} are the identity), built in
+ *           double by a Stroud rule with N + 6 points per direction.  The
+ *           reference "exact" scheme the WAA approximates; CUDA-core kernels
+ *           in every precision (a TF32 context runs its PML class on the FP32
+ *           CUDA-core kernel).  EUNSUPPORTED when kappa_max != 1.
+ *   EC      the WAA kernels with element-constant coefficients: every
+ *           quadrature node of an element takes the profile's value at the
+ *           element centroid (the piecewise-constant paving the paper
+ *           compares against; for element-constant coefficients the WAA and
+ *           stored schemes coincide, eq. 18). */
 typedef enum { WADG_PML_WAA = 0, WADG_PML_STORED = 1, WADG_PML_EC = 2 } wadg_pml_scheme;
 
 /* Stretching profiles of Section III, per axis u in {x, y, z}:
@@ -113,9 +126,11 @@ wadg_status wadg_set_materials(wadg_ctx* ctx, const double* eps_r, const double*
  * profile is active (sigma_max > 0 or kappa_max != 1); only PML elements
  * carry P^E, P^H.  The coefficients are sampled in double at the volume
  * quadrature nodes of each PML element (eq. 20 samples alpha_k(r_q)) and
- * stored per element as sigma_u (and kappa_u when kappa_max != 1).  Pass
- * NULL to remove the PML.  Only WADG_PML_WAA is implemented (EUNSUPPORTED
- * otherwise).  Resets the state and re-maps sources and probes. */
+ * stored per element as sigma_u (and kappa_u when kappa_max != 1); the
+ * stored-matrix scheme holds its operators instead (see wadg_pml_scheme).
+ * Pass NULL to remove the PML.  EINVAL for an unknown scheme, EUNSUPPORTED
+ * for kappa_max != 1 with the stored scheme or with a TF32 context.  Resets
+ * the state and re-maps sources and probes. */
 wadg_status wadg_set_pml_profile(wadg_ctx* ctx, const wadg_pml_profile* prof,
                                  wadg_pml_scheme scheme);
 
@@ -170,8 +185,9 @@ wadg_status wadg_profile_stage(wadg_ctx* ctx, int reps, double dt, double* ms_ou
  * On return the state is the forward state after nsteps steps (as after
  * wadg_run_steps).  Outputs (any may be NULL): J_out[n_batch],
  * dJ_deps[n_batch][K] (caller element order), dJ_dsigma_max[n_batch][3],
- * dJ_dp_sigma[n_batch][3].  EUNSUPPORTED for the TF32 precision or
- * kappa_max != 1; ESTATE without probes.  Device memory: about
+ * dJ_dp_sigma[n_batch][3].  EUNSUPPORTED for the TF32 precision,
+ * kappa_max != 1 or a PML scheme other than WADG_PML_WAA; ESTATE without
+ * probes.  Device memory: about
  * (nsteps/ckpt_every + ckpt_every + 12) copies of the state. */
 wadg_status wadg_adjoint(wadg_ctx* ctx, int64_t nsteps, double dt, int32_t ckpt_every,
                          double* J_out, double* dJ_deps, double* dJ_dsigma_max,
@@ -205,8 +221,10 @@ wadg_status wadg_stable_dt(const wadg_ctx* ctx, double cfl, double* dt_out);
 wadg_status wadg_objective(wadg_ctx* ctx, double* J_out);
 
 /* Device bytes held for the field state (q, res and the P fields), for the
- * per-element PML coefficient samples, for the reference operators, and for
- * the per-element geometry and connectivity.  Any pointer may be NULL. */
+ * per-element PML coefficients (the samples of the weight-adjusted and
+ * element-constant schemes, the operators of the stored-matrix scheme), for
+ * the reference operators, and for the per-element geometry and
+ * connectivity.  Any pointer may be NULL. */
 wadg_status wadg_memory_report(const wadg_ctx* ctx, size_t* bytes_state,
                                size_t* bytes_pml_coeff, size_t* bytes_operators,
                                size_t* bytes_geometry);

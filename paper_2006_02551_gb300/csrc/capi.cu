@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/wadg.h"
@@ -76,6 +77,7 @@ struct wadg_ctx {
   bool has_prof = false;
   wadg_pml_profile prof{};
   bool kappa = false;
+  wadg_pml_scheme scheme = WADG_PML_WAA;
 
   std::vector<int64_t> perm, iperm;  // internal -> user, user -> internal
   int64_t K0 = 0, K1 = 0;
@@ -83,6 +85,7 @@ struct wadg_ctx {
   // device
   DevPtr q[2], rq, p, rp, geo, fnrm, mat, nbr, code, sig, kap, ops, tabs, verts;
   DevPtr src, srcw, pr_elem, pr_ell, pr_out, obj, tdev, stepdev, flag, tcops, errflag;
+  DevPtr stored;     // stored-matrix scheme: per PML element operators
   bool tc = false;   // tensor-core stage kernels (TF32)
   int cur = 0;
   int nsrc = 0, nprobe = 0;
@@ -242,6 +245,51 @@ wadg_status upload_ops(wadg_ctx* ctx) {
   return WADG_OK;
 }
 
+// Stored-matrix scheme (eqs. 10-13, kappa = 1): per PML element and axis the
+// operators M_k^-1 M_k^{alpha} = P_h diag(alpha(x_h)) V_h, alpha = b_u, c_u,
+// d_u, by a Stroud rule with N + 6 points per direction (exact to degree
+// 2N + 11; the Jacobian cancels).  Built on the device in double precision.
+template <typename Real>
+wadg_status build_stored_ops(wadg_ctx* ctx, const double* dprof) {
+  const RefOps& R = ctx->ref;
+  const int Np = R.Np, NpP = (Np + 3) & ~3;
+  std::vector<double> r, s_, t, w;
+  stroud_rule(R.N + 6, r, s_, t, w);
+  const int Nh = static_cast<int>(r.size());
+  std::vector<double> rh(3 * (size_t)Nh), Vh((size_t)Nh * Np), Ph((size_t)Np * Nh);
+  for (int h = 0; h < Nh; ++h) {
+    rh[3 * h] = r[h];
+    rh[3 * h + 1] = s_[h];
+    rh[3 * h + 2] = t[h];
+    std::vector<double> l = R.lagrange_at(r[h], s_[h], t[h]);
+    for (int j = 0; j < Np; ++j) Vh[(size_t)h * Np + j] = l[j];
+  }
+  for (int i = 0; i < Np; ++i)
+    for (int h = 0; h < Nh; ++h) {
+      double a = 0.0;
+      for (int j = 0; j < Np; ++j) a += R.Minv[i * Np + j] * Vh[(size_t)h * Np + j];
+      Ph[(size_t)i * Nh + h] = a * w[h];
+    }
+  DevPtr drh, dVh, dPh;
+  CK(dalloc(drh, rh.size() * 8));
+  CK(dalloc(dVh, Vh.size() * 8));
+  CK(dalloc(dPh, Ph.size() * 8));
+  CK(cudaMemcpy(drh.p, rh.data(), rh.size() * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dVh.p, Vh.data(), Vh.size() * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dPh.p, Ph.data(), Ph.size() * 8, cudaMemcpyHostToDevice));
+  const size_t bytes = (size_t)ctx->K1 * 9 * Np * NpP * sizeof(Real);
+  CK(dalloc(ctx->stored, bytes));
+  CK(cudaMemsetAsync(ctx->stored.p, 0, bytes, ctx->stream));
+  CK((launch_stored_ops<Real>(R.N, (int)ctx->K1, (int)ctx->K0, (const double*)ctx->verts.p, dprof,
+                              (const double*)drh.p, (const double*)dPh.p, (const double*)dVh.p,
+                              Nh, (Real*)ctx->stored.p, ctx->stream)));
+  CK(cudaStreamSynchronize(ctx->stream));
+  dfree(drh);
+  dfree(dVh);
+  dfree(dPh);
+  return WADG_OK;
+}
+
 template <typename Real>
 wadg_status rebuild_typed(wadg_ctx* ctx) {
   const int64_t K = ctx->K;
@@ -385,10 +433,24 @@ wadg_status rebuild_typed(wadg_ctx* ctx) {
     if (ctx->kappa) CK(dalloc(ctx->kap, sb));
     CK((launch_pml_samples<Real>(Nq, (int)ctx->K1, (int)ctx->K0, (const double*)ctx->verts.p,
                                  (const double*)drq.p, (const double*)dprof.p,
-                                 (Real*)ctx->sig.p, (Real*)ctx->kap.p, ctx->stream)));
+                                 (Real*)ctx->sig.p, (Real*)ctx->kap.p,
+                                 ctx->scheme == WADG_PML_EC, ctx->stream)));
     CK(cudaStreamSynchronize(ctx->stream));
     dfree(drq);
+    if (ctx->scheme == WADG_PML_STORED) {
+      wadg_status st = build_stored_ops<Real>(ctx, (const double*)dprof.p);
+      if (st != WADG_OK) {
+        dfree(dprof);
+        return st;
+      }
+      dfree(ctx->sig);   // the stored operators replace the coefficient samples
+      dfree(ctx->kap);
+    } else {
+      dfree(ctx->stored);
+    }
     dfree(dprof);
+  } else {
+    dfree(ctx->stored);
   }
   CK(cudaStreamSynchronize(ctx->stream));
   return WADG_OK;
@@ -485,6 +547,7 @@ StageParams<Real> stage_params(wadg_ctx* ctx, int stage, double dt, double t, bo
   P.sig = (const Real*)ctx->sig.p;
   P.kap = (const Real*)ctx->kap.p;
   P.ops = (const Real*)ctx->ops.p;
+  P.stored = (const Real*)ctx->stored.p;
   P.tabs = (const unsigned char*)ctx->tabs.p;
   P.strideQ = ctx->K * 6 * Np;
   P.strideP = ctx->K1 * 6 * Np;
@@ -507,6 +570,17 @@ StageParams<Real> stage_params(wadg_ctx* ctx, int stage, double dt, double t, bo
   return P;
 }
 
+// the PML-class launch of a stage: the stored-matrix kernel, the tensor-core
+// kernel (TF32 contexts) or the CUDA-core kernel
+template <typename Real>
+cudaError_t launch_pml_class(wadg_ctx* ctx, const StageParams<Real>& P) {
+  if (ctx->scheme == WADG_PML_STORED) return launch_stage_stored<Real>(ctx->N, P, ctx->nb, ctx->stream);
+  if constexpr (std::is_same<Real, float>::value) {
+    if (ctx->tc) return launch_stage_tc(ctx->N, true, P, ctx->nb, ctx->stream);
+  }
+  return launch_stage<Real>(ctx->N, true, ctx->kappa, P, ctx->nb, ctx->stream);
+}
+
 template <typename Real>
 wadg_status issue_stage(wadg_ctx* ctx, int stage, double dt, double t, bool use_tdev) {
   if (ctx->tc) {
@@ -514,7 +588,7 @@ wadg_status issue_stage(wadg_ctx* ctx, int stage, double dt, double t, bool use_
     CK(launch_stage_tc(ctx->N, false, A, ctx->nb, ctx->stream));
     if (ctx->K1 > 0) {
       StageParams<float> B = stage_params<float>(ctx, stage, dt, t, use_tdev, true);
-      CK(launch_stage_tc(ctx->N, true, B, ctx->nb, ctx->stream));
+      CK(launch_pml_class<float>(ctx, B));
     }
     ctx->cur ^= 1;
     return WADG_OK;
@@ -523,7 +597,7 @@ wadg_status issue_stage(wadg_ctx* ctx, int stage, double dt, double t, bool use_
   CK(launch_stage<Real>(ctx->N, false, false, A, ctx->nb, ctx->stream));
   if (ctx->K1 > 0) {
     StageParams<Real> B = stage_params<Real>(ctx, stage, dt, t, use_tdev, true);
-    CK(launch_stage<Real>(ctx->N, true, ctx->kappa, B, ctx->nb, ctx->stream));
+    CK(launch_pml_class<Real>(ctx, B));
   }
   ctx->cur ^= 1;
   return WADG_OK;
@@ -698,6 +772,8 @@ wadg_status wadg_create(int N, wadg_precision prec, int32_t n_batch, int device,
     cudaError_t ce = ctx->rs == 8 ? configure_stage_kernels<double>(N)
                                   : configure_stage_kernels<float>(N);
     if (ce == cudaSuccess && ctx->tc) ce = configure_tc_kernels(N);
+    if (ce == cudaSuccess)
+      ce = ctx->rs == 8 ? configure_stored_kernels<double>(N) : configure_stored_kernels<float>(N);
     if (ce == cudaSuccess && !ctx->tc)
       ce = ctx->rs == 8 ? configure_adjoint_kernels<double>(N) : configure_adjoint_kernels<float>(N);
     if (ce != cudaSuccess) s = fail(ctx, WADG_ECUDA, "kernel set-up: %s", cudaGetErrorString(ce));
@@ -732,7 +808,7 @@ wadg_status wadg_destroy(wadg_ctx* ctx) {
                     &ctx->nbr, &ctx->code, &ctx->sig, &ctx->kap, &ctx->ops, &ctx->tabs,
                     &ctx->verts, &ctx->src, &ctx->srcw, &ctx->pr_elem, &ctx->pr_ell,
                     &ctx->pr_out, &ctx->obj, &ctx->tdev, &ctx->stepdev, &ctx->flag,
-                    &ctx->tcops, &ctx->errflag})
+                    &ctx->tcops, &ctx->errflag, &ctx->stored})
     dfree(*d);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
@@ -874,8 +950,8 @@ wadg_status wadg_set_pml_profile(wadg_ctx* ctx, const wadg_pml_profile* prof,
   wadg_status s = need_mesh(ctx);
   if (s != WADG_OK) return s;
   cudaSetDevice(ctx->device);
-  if (scheme != WADG_PML_WAA)
-    return fail(ctx, WADG_EUNSUPPORTED, "only the weight-adjusted PML scheme is built");
+  if (scheme != WADG_PML_WAA && scheme != WADG_PML_STORED && scheme != WADG_PML_EC)
+    return fail(ctx, WADG_EINVAL, "unknown PML scheme %d", (int)scheme);
   if (prof) {
     for (int u = 0; u < 3; ++u) {
       if (!(prof->L[u] > 0) || prof->sigma_max[u] < 0 || !(prof->kappa_max[u] >= 1.0) ||
@@ -886,14 +962,18 @@ wadg_status wadg_set_pml_profile(wadg_ctx* ctx, const wadg_pml_profile* prof,
     bool kap = false;
     for (int u = 0; u < 3; ++u)
       if (prof->kappa_max[u] != 1.0) kap = true;
-    if (kap && ctx->tc)
+    if (kap && ctx->tc && scheme != WADG_PML_STORED)
       return fail(ctx, WADG_EUNSUPPORTED, "kappa_max != 1 is not built for the TF32 stage");
+    if (kap && scheme == WADG_PML_STORED)
+      return fail(ctx, WADG_EUNSUPPORTED, "the stored-matrix scheme is built for kappa = 1");
     ctx->has_prof = true;
     ctx->prof = *prof;
     ctx->kappa = kap;
+    ctx->scheme = scheme;
   } else {
     ctx->has_prof = false;
     ctx->kappa = false;
+    ctx->scheme = WADG_PML_WAA;
   }
   s = rebuild(ctx);
   if (s != WADG_OK) return s;
@@ -1015,15 +1095,15 @@ wadg_status wadg_profile_stage(wadg_ctx* ctx, int reps, double dt, double* ms_ou
     for (int cls = 0; cls < 2; ++cls) {
       if (cls == 1 && ctx->K1 == 0) continue;
       CK(cudaEventRecord(ev[2 * cls], ctx->stream));
-      if (ctx->tc) {
-        StageParams<float> P = stage_params<float>(ctx, stage, dt, ctx->t, false, cls == 1);
-        CK(launch_stage_tc(ctx->N, cls == 1, P, ctx->nb, ctx->stream));
-      } else if (ctx->rs == 8) {
+      if (ctx->rs == 8) {
         StageParams<double> P = stage_params<double>(ctx, stage, dt, ctx->t, false, cls == 1);
-        CK(launch_stage<double>(ctx->N, cls == 1, ctx->kappa, P, ctx->nb, ctx->stream));
+        if (cls == 1) CK(launch_pml_class<double>(ctx, P));
+        else CK(launch_stage<double>(ctx->N, false, false, P, ctx->nb, ctx->stream));
       } else {
         StageParams<float> P = stage_params<float>(ctx, stage, dt, ctx->t, false, cls == 1);
-        CK(launch_stage<float>(ctx->N, cls == 1, ctx->kappa, P, ctx->nb, ctx->stream));
+        if (cls == 1) CK(launch_pml_class<float>(ctx, P));
+        else if (ctx->tc) CK(launch_stage_tc(ctx->N, false, P, ctx->nb, ctx->stream));
+        else CK(launch_stage<float>(ctx->N, false, false, P, ctx->nb, ctx->stream));
       }
       CK(cudaEventRecord(ev[2 * cls + 1], ctx->stream));
     }
@@ -1223,6 +1303,8 @@ wadg_status wadg_adjoint(wadg_ctx* ctx, int64_t nsteps, double dt, int32_t ckpt_
   if (nsteps < 1 || !(dt > 0) || ckpt_every < 1) return fail(ctx, WADG_EINVAL, "bad arguments");
   if (ctx->tc) return fail(ctx, WADG_EUNSUPPORTED, "the adjoint runs on the FP64/FP32 kernels");
   if (ctx->kappa) return fail(ctx, WADG_EUNSUPPORTED, "the adjoint is built for kappa = 1");
+  if (ctx->scheme != WADG_PML_WAA)
+    return fail(ctx, WADG_EUNSUPPORTED, "the adjoint is built for the weight-adjusted scheme");
   if (ctx->nprobe < 1) return fail(ctx, WADG_ESTATE, "the objective needs probes");
   cudaSetDevice(ctx->device);
   const size_t need = (size_t)std::min<int64_t>(ckpt_every, 4096) * ctx->nprobe * 6 * ctx->nb * 8;
@@ -1259,7 +1341,9 @@ wadg_status wadg_memory_report(const wadg_ctx* ctx, size_t* bytes_state, size_t*
                                size_t* bytes_operators, size_t* bytes_geometry) {
   if (!ctx) return fail(nullptr, WADG_EINVAL, "null context");
   if (bytes_state) *bytes_state = ctx->q[0].bytes + ctx->q[1].bytes + ctx->rq.bytes + ctx->p.bytes + ctx->rp.bytes;
-  if (bytes_pml_coeff) *bytes_pml_coeff = ctx->sig.bytes + ctx->kap.bytes;
+  if (bytes_pml_coeff)
+    *bytes_pml_coeff = ctx->scheme == WADG_PML_STORED ? ctx->stored.bytes
+                                                       : ctx->sig.bytes + ctx->kap.bytes;
   if (bytes_operators) *bytes_operators = ctx->ops.bytes + ctx->tabs.bytes;
   if (bytes_geometry)
     *bytes_geometry = ctx->geo.bytes + ctx->fnrm.bytes + ctx->mat.bytes + ctx->nbr.bytes + ctx->code.bytes;
@@ -1362,7 +1446,7 @@ wadg_status noalloc_stage(wadg_ctx* ctx, int stage, double dt, const double* tde
     if (ctx->K1 > 0) {
       StageParams<float> B = stage_params<float>(ctx, stage, dt, 0.0, false, true);
       B.t_dev = tdev;
-      CK(launch_stage_tc(ctx->N, true, B, ctx->nb, ctx->stream));
+      CK(launch_pml_class<float>(ctx, B));
     }
   } else {
     StageParams<Real> A = stage_params<Real>(ctx, stage, dt, 0.0, false, false);
@@ -1371,7 +1455,7 @@ wadg_status noalloc_stage(wadg_ctx* ctx, int stage, double dt, const double* tde
     if (ctx->K1 > 0) {
       StageParams<Real> B = stage_params<Real>(ctx, stage, dt, 0.0, false, true);
       B.t_dev = tdev;
-      CK(launch_stage<Real>(ctx->N, true, ctx->kappa, B, ctx->nb, ctx->stream));
+      CK(launch_pml_class<Real>(ctx, B));
     }
   }
   ctx->cur ^= 1;

@@ -108,7 +108,7 @@ __device__ __forceinline__ void lds2(const double* p, double* v) {
 // Stage kernel.  Threads work on register tiles: 4 nodes x 3 components x 3
 // reference derivatives (curl), 4 quadrature points x 12 components (V_q),
 // 4 nodes x 4 components (P_q).  All operator reads come from shared memory.
-template <typename Real, int N, bool PML, bool KAPPA>
+template <typename Real, int N, bool PML, bool KAPPA, bool STORED = false>
 __global__ void __launch_bounds__(Tile<Real, N, PML>::THREADS)
 stage_kernel(const StageParams<Real> P) {
   using D = Dims<N>;
@@ -349,7 +349,65 @@ stage_kernel(const StageParams<Real> P) {
         for (int n = 0; n < 4; ++n) RS[(e * NpP + 4 * iq + n) * 6 + oc + c] = out[c][n];
     }
   }
-  if (PML) {
+  if (PML && STORED) {
+  __syncthreads();   // RS complete
+
+  // ---- stored-matrix scheme (eqs. 10-13 with kappa = 1, so (M^a)^-1 M_k and
+  // M_k^-1 M^{1/kappa} are the identity): per axis u, 4 nodes per task,
+  //   rhs_E = r_E - B_u E_u - C_u P^E_u     rhs_P^E = E_u - D_u P^E_u
+  //   rhs_H = r_H - B_u H_u - C_u P^H_u     rhs_P^H = H_u - D_u P^H_u
+  // with B_u, C_u, D_u = M_k^-1 M_k^{b_u, c_u, d_u} read from global memory
+  for (int task = tid; task < ne * 3 * NIQ; task += NT) {
+    const int e = task / (3 * NIQ), r = task - e * 3 * NIQ, u = r / NIQ, iq = r - u * NIQ;
+    const int eg = eg0 + e;
+    const Real* Bm = P.stored + ((int64_t)(ep0 + e) * 9 + u * 3) * Np * NpP + 4 * iq;
+    const Real* Cm = Bm + Np * NpP;
+    const Real* Dm = Cm + Np * NpP;
+    Real aE[4], aH[4], dE[4], dH[4];
+#pragma unroll
+    for (int n = 0; n < 4; ++n) aE[n] = aH[n] = dE[n] = dH[n] = 0;
+    const Real* fe = F + e * Np * 12;
+#pragma unroll 5
+    for (int j = 0; j < Np; ++j) {
+      Real bb[4], cc[4], dd[4];
+      ld4(Bm + j * NpP, bb);
+      ld4(Cm + j * NpP, cc);
+      ld4(Dm + j * NpP, dd);
+      const Real Ej = fe[j * 12 + u], Hj = fe[j * 12 + 3 + u];
+      const Real PEj = fe[j * 12 + 6 + u], PHj = fe[j * 12 + 9 + u];
+#pragma unroll
+      for (int n = 0; n < 4; ++n) {
+        aE[n] += bb[n] * Ej + cc[n] * PEj;
+        aH[n] += bb[n] * Hj + cc[n] * PHj;
+        dE[n] += dd[n] * PEj;
+        dH[n] += dd[n] * PHj;
+      }
+    }
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+      const int i = 4 * iq + n;
+      if (i >= Np) continue;
+      const Real* Fi = F + (e * Np + i) * 12;
+      const Real rhs[4] = {RS[(e * NpP + i) * 6 + u] - aE[n], RS[(e * NpP + i) * 6 + 3 + u] - aH[n],
+                           Fi[u] - dE[n], Fi[3 + u] - dH[n]};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {   // E_u, H_u
+        const int64_t gi = ((int64_t)eg * 6 + 3 * h + u) * Np + i;
+        const Real rr = rka * resq[gi] + rdt * rhs[h];
+        resq[gi] = rr;
+        qout[gi] = Fi[3 * h + u] + rkb * rr;
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {   // P^E_u, P^H_u
+        const int64_t pi = ((int64_t)(eg - P.K0) * 6 + 3 * h + u) * Np + i;
+        const Real rr = rka * resp[pi] + rdt * rhs[2 + h];
+        resp[pi] = rr;
+        pio[pi] = Fi[6 + 3 * h + u] + rkb * rr;
+      }
+    }
+  }
+  }  // stored
+  if (PML && !STORED) {
   __syncthreads();   // FL is reused as TZ below
 
   // ---- phase 3: V_q of the 12 fields at 4 quadrature points; eq. 9 pointwise
@@ -539,15 +597,15 @@ stage_kernel(const StageParams<Real> P) {
   }  // tile loop
 }
 
-template <typename Real, int N, bool PML, bool KAPPA>
+template <typename Real, int N, bool PML, bool KAPPA, bool STORED = false>
 static cudaError_t configure_one() {
   using TL = Tile<Real, N, PML>;
-  return cudaFuncSetAttribute(stage_kernel<Real, N, PML, KAPPA>,
+  return cudaFuncSetAttribute(stage_kernel<Real, N, PML, KAPPA, STORED>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL::smem);
 }
 
 // resident blocks per SM of one stage-kernel instance (cached per instance)
-template <typename Real, int N, bool PML, bool KAPPA>
+template <typename Real, int N, bool PML, bool KAPPA, bool STORED = false>
 static int resident_blocks() {
   static int cached = 0;
   if (cached == 0) {
@@ -555,7 +613,7 @@ static int resident_blocks() {
     int nb = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stage_kernel<Real, N, PML, KAPPA>,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stage_kernel<Real, N, PML, KAPPA, STORED>,
                                                       TL::THREADS, TL::smem) != cudaSuccess ||
         nb < 1)
       nb = 1;
@@ -564,15 +622,16 @@ static int resident_blocks() {
   return cached;
 }
 
-template <typename Real, int N, bool PML, bool KAPPA>
+template <typename Real, int N, bool PML, bool KAPPA, bool STORED = false>
 static cudaError_t launch_one(const StageParams<Real>& P, int nb, cudaStream_t s) {
   using TL = Tile<Real, N, PML>;
   if (P.n_elem <= 0) return cudaSuccess;
   StageParams<Real> Q = P;
   Q.nb = nb;
   const long long tiles = (long long)((P.n_elem + TL::T - 1) / TL::T) * nb;
-  const int grid = (int)std::min<long long>(tiles, resident_blocks<Real, N, PML, KAPPA>());
-  stage_kernel<Real, N, PML, KAPPA><<<grid, TL::THREADS, TL::smem, s>>>(Q);
+  const int grid =
+      (int)std::min<long long>(tiles, resident_blocks<Real, N, PML, KAPPA, STORED>());
+  stage_kernel<Real, N, PML, KAPPA, STORED><<<grid, TL::THREADS, TL::smem, s>>>(Q);
   return cudaGetLastError();
 }
 
@@ -623,6 +682,161 @@ template cudaError_t launch_stage<double>(int, bool, bool, const StageParams<dou
 template cudaError_t launch_stage<float>(int, bool, bool, const StageParams<float>&, int,
                                          cudaStream_t);
 
+// ------------------------------------------------------- stored-matrix scheme
+template <typename Real>
+cudaError_t configure_stored_kernels(int N) {
+  switch (N) {
+    case 1: return configure_one<Real, 1, true, false, true>();
+    case 2: return configure_one<Real, 2, true, false, true>();
+    case 3: return configure_one<Real, 3, true, false, true>();
+    case 4: return configure_one<Real, 4, true, false, true>();
+    case 5: return configure_one<Real, 5, true, false, true>();
+    default: return cudaErrorInvalidValue;
+  }
+}
+template cudaError_t configure_stored_kernels<double>(int);
+template cudaError_t configure_stored_kernels<float>(int);
+
+template <typename Real>
+cudaError_t launch_stage_stored(int N, const StageParams<Real>& P, int nb, cudaStream_t s) {
+  switch (N) {
+    case 1: return launch_one<Real, 1, true, false, true>(P, nb, s);
+    case 2: return launch_one<Real, 2, true, false, true>(P, nb, s);
+    case 3: return launch_one<Real, 3, true, false, true>(P, nb, s);
+    case 4: return launch_one<Real, 4, true, false, true>(P, nb, s);
+    case 5: return launch_one<Real, 5, true, false, true>(P, nb, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template cudaError_t launch_stage_stored<double>(int, const StageParams<double>&, int, cudaStream_t);
+template cudaError_t launch_stage_stored<float>(int, const StageParams<float>&, int, cudaStream_t);
+
+// Stored operators M_k^-1 M_k^{alpha} = P_h diag(alpha(x_h)) V_h for alpha in
+// {b_u, c_u, d_u} of eq. 9 (kappa = 1), u = x, y, z, of TE elements per block,
+// in double precision.  The rule's points are processed in chunks staged in
+// shared memory (P_h and V_h columns, the nine coefficient samples of each
+// element); every thread accumulates ENT entries (i, j) of the nine operators
+// of each of its block's elements in registers.
+template <int N>
+struct StoredSetup {
+  static constexpr int Np = (N + 1) * (N + 2) * (N + 3) / 6;
+  static constexpr int NpP = (Np + 3) & ~3;
+  static constexpr int THREADS = 256;
+  static constexpr int ENT = (Np * Np + THREADS - 1) / THREADS;
+  static constexpr int TE = ENT <= 2 ? 4 : (ENT <= 5 ? 2 : 1);
+  static constexpr int HC = 32;
+};
+
+template <typename Real, int N>
+__global__ void __launch_bounds__(StoredSetup<N>::THREADS)
+stored_ops_kernel(int K1, int K0, int Nh, const double* verts, const double* prof,
+                  const double* rh, const double* Ph, const double* Vh, Real* out) {
+  using S = StoredSetup<N>;
+  constexpr int Np = S::Np, NpP = S::NpP, NT = S::THREADS, ENT = S::ENT, TE = S::TE, HC = S::HC;
+  __shared__ double PhC[Np][HC];
+  __shared__ double VhC[HC][Np];
+  __shared__ double al[TE][9][HC];   // [element][3 u + kind][point]: b_u, c_u, d_u
+  const int tid = threadIdx.x;
+  const int e0 = blockIdx.x * TE;
+  double acc[TE][9][ENT];
+#pragma unroll
+  for (int t = 0; t < TE; ++t)
+#pragma unroll
+    for (int m = 0; m < 9; ++m)
+#pragma unroll
+      for (int k = 0; k < ENT; ++k) acc[t][m][k] = 0.0;
+  const double ie0 = 1.0 / prof[15];
+  for (int h0 = 0; h0 < Nh; h0 += HC) {
+    __syncthreads();   // previous chunk consumed
+    for (int idx = tid; idx < Np * HC; idx += NT) {
+      const int i = idx / HC, hh = idx - i * HC;
+      PhC[i][hh] = h0 + hh < Nh ? Ph[(int64_t)i * Nh + h0 + hh] : 0.0;
+    }
+    for (int idx = tid; idx < HC * Np; idx += NT) {
+      const int hh = idx / Np, j = idx - hh * Np;
+      VhC[hh][j] = h0 + hh < Nh ? Vh[(int64_t)(h0 + hh) * Np + j] : 0.0;
+    }
+    for (int idx = tid; idx < TE * HC; idx += NT) {
+      const int t = idx / HC, hh = idx - t * HC;
+      double sg[3] = {0.0, 0.0, 0.0};
+      if (e0 + t < K1 && h0 + hh < Nh) {
+        const double* v = verts + (int64_t)(K0 + e0 + t) * 12;
+        const double r = rh[(h0 + hh) * 3], s_ = rh[(h0 + hh) * 3 + 1], tt = rh[(h0 + hh) * 3 + 2];
+        const double l0 = -0.5 * (1 + r + s_ + tt), l1 = 0.5 * (1 + r), l2 = 0.5 * (1 + s_),
+                     l3 = 0.5 * (1 + tt);
+        for (int u = 0; u < 3; ++u) {
+          const double x = l0 * v[u] + l1 * v[3 + u] + l2 * v[6 + u] + l3 * v[9 + u];
+          const double d = (fabs(x) - prof[u]) / prof[3 + u];
+          sg[u] = d > 0 ? prof[6 + u] * pow(d, prof[9 + u]) : 0.0;
+        }
+      }
+      for (int u = 0; u < 3; ++u) {
+        const double su = sg[u], sv = sg[(u + 1) % 3], sw = sg[(u + 2) % 3];
+        const double b = (sv + sw - su) * ie0;              // eq. 9, kappa = 1
+        al[t][3 * u][hh] = b;
+        al[t][3 * u + 1][hh] = sv * sw * ie0 * ie0 - b * su * ie0;
+        al[t][3 * u + 2][hh] = su * ie0;
+      }
+    }
+    __syncthreads();
+    for (int hh = 0; hh < HC; ++hh) {
+#pragma unroll
+      for (int k = 0; k < ENT; ++k) {
+        const int ent = tid + k * NT;
+        if (ent >= Np * Np) continue;
+        const int i = ent / Np, j = ent - i * Np;
+        const double w = PhC[i][hh] * VhC[hh][j];
+#pragma unroll
+        for (int t = 0; t < TE; ++t)
+#pragma unroll
+          for (int m = 0; m < 9; ++m) acc[t][m][k] += w * al[t][m][hh];
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < TE; ++t) {
+    if (e0 + t >= K1) continue;
+#pragma unroll
+    for (int k = 0; k < ENT; ++k) {
+      const int ent = tid + k * NT;
+      if (ent >= Np * Np) continue;
+      const int i = ent / Np, j = ent - i * Np;
+#pragma unroll
+      for (int m = 0; m < 9; ++m)   // transposed: row j of the stored block is column j
+        out[(((int64_t)(e0 + t) * 9 + m) * Np + j) * NpP + i] = (Real)acc[t][m][k];
+    }
+  }
+}
+
+template <typename Real>
+cudaError_t launch_stored_ops(int N, int K1, int K0, const double* verts, const double* prof,
+                              const double* rh, const double* Ph, const double* Vh, int Nh,
+                              Real* out, cudaStream_t s) {
+  if (K1 <= 0) return cudaSuccess;
+#define WADG_STORED_CASE(NN)                                                              \
+  case NN: {                                                                              \
+    using S = StoredSetup<NN>;                                                            \
+    stored_ops_kernel<Real, NN><<<(K1 + S::TE - 1) / S::TE, S::THREADS, 0, s>>>(          \
+        K1, K0, Nh, verts, prof, rh, Ph, Vh, out);                                        \
+    return cudaGetLastError();                                                            \
+  }
+  switch (N) {
+    WADG_STORED_CASE(1)
+    WADG_STORED_CASE(2)
+    WADG_STORED_CASE(3)
+    WADG_STORED_CASE(4)
+    WADG_STORED_CASE(5)
+    default: return cudaErrorInvalidValue;
+  }
+#undef WADG_STORED_CASE
+}
+template cudaError_t launch_stored_ops<double>(int, int, int, const double*, const double*,
+                                               const double*, const double*, const double*, int,
+                                               double*, cudaStream_t);
+template cudaError_t launch_stored_ops<float>(int, int, int, const double*, const double*,
+                                              const double*, const double*, const double*, int,
+                                              float*, cudaStream_t);
+
 // ------------------------------------------------------------------ probes
 template <typename Real>
 __global__ void probe_kernel(const ProbeParams P) {
@@ -671,7 +885,7 @@ cudaError_t launch_advance(double* t_dev, int64_t* step_dev, double dt, cudaStre
 template <typename Real>
 __global__ void pml_samples_kernel(int Nq, int NqP, int K1, int K0, const double* verts,
                                    const double* rq, const double* prof, Real* sig,
-                                   Real* kap) {
+                                   Real* kap, bool element_constant) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)K1 * NqP) return;
   const int e = (int)(idx / NqP), q = (int)(idx - (int64_t)e * NqP);
@@ -683,7 +897,10 @@ __global__ void pml_samples_kernel(int Nq, int NqP, int K1, int K0, const double
     return;
   }
   const double* v = verts + (int64_t)(K0 + e) * 12;
-  const double r = rq[q * 3], s = rq[q * 3 + 1], t = rq[q * 3 + 2];
+  // the quadrature node, or the centroid for element-constant coefficients
+  const double r = element_constant ? -0.5 : rq[q * 3];
+  const double s = element_constant ? -0.5 : rq[q * 3 + 1];
+  const double t = element_constant ? -0.5 : rq[q * 3 + 2];
   const double l0 = -0.5 * (1 + r + s + t), l1 = 0.5 * (1 + r), l2 = 0.5 * (1 + s),
                l3 = 0.5 * (1 + t);
   for (int u = 0; u < 3; ++u) {
@@ -698,19 +915,22 @@ __global__ void pml_samples_kernel(int Nq, int NqP, int K1, int K0, const double
 
 template <typename Real>
 cudaError_t launch_pml_samples(int Nq, int K1, int K0, const double* verts, const double* rq,
-                               const double* prof, Real* sig, Real* kap, cudaStream_t s) {
+                               const double* prof, Real* sig, Real* kap, bool element_constant,
+                               cudaStream_t s) {
   const int NqP = (Nq + 3) & ~3;
   const int64_t n = (int64_t)K1 * NqP;
   if (n == 0) return cudaSuccess;
   const int th = 256;
   pml_samples_kernel<Real><<<(unsigned)((n + th - 1) / th), th, 0, s>>>(Nq, NqP, K1, K0, verts,
-                                                                       rq, prof, sig, kap);
+                                                                       rq, prof, sig, kap,
+                                                                       element_constant);
   return cudaGetLastError();
 }
 template cudaError_t launch_pml_samples<double>(int, int, int, const double*, const double*,
-                                                const double*, double*, double*, cudaStream_t);
+                                                const double*, double*, double*, bool,
+                                                cudaStream_t);
 template cudaError_t launch_pml_samples<float>(int, int, int, const double*, const double*,
-                                               const double*, float*, float*, cudaStream_t);
+                                               const double*, float*, float*, bool, cudaStream_t);
 
 template <typename Real>
 __global__ void check_finite_kernel(const Real* a, int64_t n, int* flag) {

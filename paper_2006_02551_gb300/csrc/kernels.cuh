@@ -12,7 +12,12 @@
 //   material mat[e][3]             1/eps, 1/mu, Z = sqrt(mu/eps)
 //   faces    nbr[e][4] (-1: PEC), code[e][4] = neighbour face * 6 + rotation
 //   PML      sig[e'][3][Nq] (and kap[e'][3][Nq])  sigma_u, kappa_u at the
-//            quadrature nodes of each PML element
+//            quadrature nodes of each PML element (weight-adjusted scheme;
+//            with element-constant coefficients every node holds the value
+//            at the centroid)
+//            stored[e'][3][3][Np][NpP]  stored-matrix scheme: per axis u the
+//            operators M_k^-1 M_k^{b_u}, M_k^-1 M_k^{c_u}, M_k^-1 M_k^{d_u},
+//            transposed (column j of the operator is row j here)
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -40,6 +45,7 @@ struct StageParams {
   const unsigned char* code;
   const Real* sig;
   const Real* kap;
+  const Real* stored;       // stored-matrix operators (stored-matrix scheme only)
   const Real* ops;          // DrT | DsT | DtT | LIFTT | VqT | PqT
   const unsigned char* tabs;  // Fmask[4 Nfp] | fperm[4*24*Nfp]
   int64_t strideQ;          // elements*6*Np per batch (all elements)
@@ -121,7 +127,19 @@ cudaError_t launch_advance(double* t_dev, int64_t* step_dev, double dt, cudaStre
 template <typename Real>
 cudaError_t launch_pml_samples(int Nq, int K1, int K0, const double* verts,
                                const double* rq /*[Nq][3]*/, const double* prof /*16*/,
-                               Real* sig, Real* kap, cudaStream_t s);
+                               Real* sig, Real* kap, bool element_constant, cudaStream_t s);
+// kappa = 1 stored-matrix scheme: the PML class with the per-element
+// operators, and their construction in double precision from the sigma
+// profile at the points of a high-degree rule (rh [Nh][3] reference points,
+// Ph [Np][Nh] = M^-1 V_h^T W_h, Vh [Nh][Np]; prof as for launch_pml_samples)
+template <typename Real>
+cudaError_t launch_stage_stored(int N, const StageParams<Real>& P, int nb, cudaStream_t s);
+template <typename Real>
+cudaError_t configure_stored_kernels(int N);
+template <typename Real>
+cudaError_t launch_stored_ops(int N, int K1, int K0, const double* verts, const double* prof,
+                              const double* rh, const double* Ph, const double* Vh, int Nh,
+                              Real* out, cudaStream_t s);
 template <typename Real>
 cudaError_t launch_check_finite(const Real* a, int64_t n, int* flag, cudaStream_t s);
 

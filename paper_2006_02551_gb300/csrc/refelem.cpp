@@ -223,6 +223,26 @@ std::vector<double> RefOps::lagrange_at(double rr, double ss, double tt) const {
   return out;
 }
 
+void stroud_rule(int n, std::vector<double>& r, std::vector<double>& s, std::vector<double>& t,
+                 std::vector<double>& w) {
+  // conical product of Gauss-Jacobi rules with weights (1-x)^0, (1-x)^1,
+  // (1-x)^2 on the collapsed coordinates: n^3 points, degree 2n - 1
+  std::vector<double> xa, wa, xb, wb, xc, wc;
+  gauss_jacobi(n, 0, 0, xa, wa);
+  gauss_jacobi(n, 1, 0, xb, wb);
+  gauss_jacobi(n, 2, 0, xc, wc);
+  r.clear(); s.clear(); t.clear(); w.clear();
+  for (int ia = 0; ia < n; ++ia)
+    for (int ib = 0; ib < n; ++ib)
+      for (int ic = 0; ic < n; ++ic) {
+        const double a = xa[ia], b = xb[ib], c = xc[ic];
+        r.push_back(0.25 * (1 + a) * (1 - b) * (1 - c) - 1.0);
+        s.push_back(0.5 * (1 + b) * (1 - c) - 1.0);
+        t.push_back(c);
+        w.push_back(wa[ia] * wb[ib] * wc[ic] / 8.0);
+      }
+}
+
 bool build_ref_ops(int N, RefOps& o, const char** err) {
   if (N < 1 || N > 6) {
     *err = "polynomial order N must be in 1..6";
@@ -302,19 +322,7 @@ bool build_ref_ops(int N, RefOps& o, const char** err) {
   }
   o.LIFT = matmul(o.Minv, E, Np, Np, 4 * Nfp);
   // volume quadrature of degree 2N+1
-  const int n1 = N + 1;
-  std::vector<double> xc, wc;
-  gauss_jacobi(n1, 2, 0, xc, wc);
-  o.rq.clear(); o.sq.clear(); o.tq.clear(); o.wq.clear();
-  for (int ia = 0; ia < n1; ++ia)
-    for (int ib = 0; ib < n1; ++ib)
-      for (int ic = 0; ic < n1; ++ic) {
-        double a = xa[ia], b = xb[ib], c = xc[ic];
-        o.rq.push_back(0.25 * (1 + a) * (1 - b) * (1 - c) - 1.0);
-        o.sq.push_back(0.5 * (1 + b) * (1 - c) - 1.0);
-        o.tq.push_back(c);
-        o.wq.push_back(wa[ia] * wb[ib] * wc[ic] / 8.0);
-      }
+  stroud_rule(N + 1, o.rq, o.sq, o.tq, o.wq);
   o.Nq = static_cast<int>(o.rq.size());
   const int Nq = o.Nq;
   o.Vq.assign(static_cast<size_t>(Nq) * Np, 0.0);

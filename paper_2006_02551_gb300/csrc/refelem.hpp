@@ -29,6 +29,11 @@ struct RefOps {
   std::vector<double> lagrange_at(double r, double s, double t) const;  // [Np]
 };
 
+// Stroud conical-product rule on the reference tetrahedron with n points per
+// collapsed direction (n^3 points, exact for polynomials of degree 2n - 1).
+void stroud_rule(int n, std::vector<double>& r, std::vector<double>& s, std::vector<double>& t,
+                 std::vector<double>& w);
+
 // Builds all operators; returns false (and a message) on failure.
 bool build_ref_ops(int N, RefOps& out, const char** err);
 

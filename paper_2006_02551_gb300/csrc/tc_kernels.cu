@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(TcWarps<PML>::threads, PML ? 1 : 2) tc_stage_k
   const uint32_t sbase = saddr(smem);
   float* RS = reinterpret_cast<float*>(smem + PL::oRS);     // [T][6][NpP]
   float* geo = reinterpret_cast<float*>(smem + PL::oGeo);   // [2][T][28]: n,Fscale x4 | metric
-  // mbarriers: products done [0] volume (+ V_q), [1] LIFT, [2] P_q; operands
+  // mbarriers: products done [0] V_q, [1] volume + LIFT, [2] P_q; operands
   // ready [3] fields, [4] flux, [5] (t, z); [6] final drain of the MMA warp
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + PL::oMisc);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + PL::oMisc + 64);
@@ -531,15 +531,15 @@ __global__ void __launch_bounds__(TcWarps<PML>::threads, PML ? 1 : 2) tc_stage_k
       constexpr uint32_t idQ = idesc_tf32(128, PL::NQ);
       for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         if (!wait_ready(0)) { mfail = true; break; }
-        for (int k = 0; k < NpK / 8; ++k)
-          mma_tf32(tmem + PL::cV, make_desc(sbase + PL::oVol + 256 * k, 128, PL::SBO_V),
-                   make_desc(sbase + PL::oBF + 2 * PL::LB * k, PL::LB, PL::SBB_V), idV, k > 0);
-        if (PML) {
+        if (PML) {   // V_q first: the quadrature epilogue waits for it alone
           for (int k = 0; k < NpK / 8; ++k)
             mma_tf32(tmem + PL::cVq, make_desc(sbase + PL::oVq + 256 * k, 128, PL::SBO_V),
                      make_desc(sbase + PL::oBF + 2 * PL::LB * k, PL::LB, PL::SBB_V), idQ, k > 0);
           mma_commit(saddr(mbar + 0));
         }
+        for (int k = 0; k < NpK / 8; ++k)
+          mma_tf32(tmem + PL::cV, make_desc(sbase + PL::oVol + 256 * k, 128, PL::SBO_V),
+                   make_desc(sbase + PL::oBF + 2 * PL::LB * k, PL::LB, PL::SBB_V), idV, k > 0);
         issued = true;
         if (!wait_ready(1)) { mfail = true; break; }
         for (int k = 0; k < NFK / 8; ++k)
@@ -688,7 +688,7 @@ __global__ void __launch_bounds__(TcWarps<PML>::threads, PML ? 1 : 2) tc_stage_k
     }
 
     if (PML) {
-      if (!wait_bar(0)) { failed = true; break; }   // volume and V_q products
+      if (!wait_bar(0)) { failed = true; break; }   // V_q product
       // ---- epilogue A1: eq. 9 at the quadrature points -> B of P_q
       {
         const int q = quad * 32 + lane;     // quadrature point of this lane

@@ -61,16 +61,21 @@ def rel_err(q_lib, states_ref, mask):
 
 
 def make_pair(N, n_hex, jitter, seed, prof, precision="fp64", sources=(), probes=(),
-              eps=None, mu=None, n_batch=1):
+              eps=None, mu=None, n_batch=1, scheme="waa"):
+    """scheme: "waa", "stored" (eqs. 10-13) or "ec" (the weight-adjusted
+    scheme with the profile evaluated at each element's centroid)."""
     from paper_2006_02551_gb300 import Solver
     v, e = cube_tet_mesh(n_hex, jitter, seed)
     sim = Simulation(N, v, e, profile=prof, eps=eps, mu=mu, sources=sources,
-                     probes=probes, n_batch=n_batch)
+                     probes=probes, n_batch=n_batch,
+                     scheme="stored" if scheme == "stored" else "waa")
+    if scheme == "ec" and prof is not None:
+        sim.disc.set_profile(prof, element_constant_at=sim.geom.verts.mean(axis=1).T)
     s = Solver(N, precision, n_batch=n_batch)
     s.set_mesh(v, e)
     if eps is not None or mu is not None:
         s.set_materials(eps, mu)
-    s.set_pml(prof)
+    s.set_pml(prof, scheme)
     if sources:
         s.set_sources(sources)
     if probes:

@@ -1,0 +1,113 @@
+"""GPU parity of the other two PML schemes against the FP64 oracle:
+
+* the stored-matrix scheme of eqs. 10-13 (kappa = 1: per element and axis
+  the operators M_k^-1 M_k^{b_u, c_u, d_u}, built on the device from the
+  same Stroud rule with N + 6 points per direction that the oracle uses);
+* the element-constant coefficient variant (the weight-adjusted kernels with
+  the profile evaluated at the element centroid, the piecewise-constant
+  paving of the PML the paper compares with).
+
+Tolerances as in the weight-adjusted parity tests: 1e-12 (FP64), 1e-5 (FP32)
+relative L2; the TF32 context is checked on the stage increment (1e-2)."""
+import numpy as np
+import pytest
+
+from oracle import lserk
+from synthetic import PmlProfile, workload
+from tests.parity_util import make_pair, random_states, rel_err, to_lib
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+PML3 = PmlProfile(u0=0.75, L=0.25, sigma_max=20.0, p_sigma=3.0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2006_02551_gb300 import build
+    build.build()
+
+
+def one_stage(N, prec, scheme, prof=PML3, n_hex=None, stage=1):
+    # the oracle's stored operators cost K N_h N_p^2 per matrix: smaller
+    # meshes at the higher orders
+    n_hex = n_hex or {1: 4, 2: 4, 3: 4, 4: 3, 5: 2}[N]
+    s, sim, mask = make_pair(N, n_hex, 0.15, 3, prof, prec, scheme=scheme)
+    st = random_states(sim.K, sim.Np, 1, 17, mask)
+    q0 = to_lib(st)
+    s.set_state(q0, 0.0)
+    dt, t = 0.01, 0.21
+    s.rk_stage(stage, t, dt)
+    q, _ = s.get_state()
+    rhs = sim.rhs(st[0], t + lserk.RK_C[stage] * dt, 0)
+    for f in st[0]:
+        st[0][f] = st[0][f] + lserk.RK_B[stage] * dt * rhs[f]
+    s.close()
+    if prec == "tf32":   # error of the increment
+        r = to_lib(st)
+        sel = np.ones(r.shape[:3], bool)
+        sel[:, ~mask, 6:] = False
+        return float(np.linalg.norm((q - r)[sel]) / np.linalg.norm((r - q0)[sel]))
+    return rel_err(q, st, mask)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5])
+def test_one_stage_stored(N, prec):
+    err = one_stage(N, prec, "stored")
+    assert err < TOL[prec], err
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("N", [1, 3, 4])
+def test_one_stage_element_constant(N, prec):
+    err = one_stage(N, prec, "ec")
+    assert err < TOL[prec], err
+
+
+@pytest.mark.parametrize("scheme", ["stored", "ec"])
+def test_one_stage_tf32_context(scheme):
+    # stored: the PML class runs the FP32 CUDA-core kernel, the rest the
+    # tensor-core kernel; ec: both classes on the tensor-core kernels
+    err = one_stage(4, "tf32", scheme)
+    assert err < 1e-2, err
+
+
+@pytest.mark.parametrize("scheme", ["stored", "ec"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_small_workload_run(scheme, prec):
+    """The 384-tet N=3 workload with its dipole and probes through run_steps
+    (the CUDA-graph path), 100 steps."""
+    w = workload("cube4_n3")
+    s, sim, mask = make_pair(w.N, w.n_hex, w.jitter, w.mesh_seed, w.pml, prec,
+                             sources=w.sources, probes=w.probes, scheme=scheme)
+    dt = sim.stable_dt(1.0)
+    nst = 100
+    s.set_state(None, 0.0)
+    rec = s.run_steps(nst, dt)
+    q, _ = s.get_state()
+    st = sim.zero_state()
+    st, _, rec_ref, J_ref = sim.run(st, nst, dt)
+    err = rel_err(q, st, mask)
+    assert err < TOL[prec], err
+    perr = np.linalg.norm(rec - rec_ref) / np.linalg.norm(rec_ref)
+    assert perr < TOL[prec], perr
+    s.close()
+
+
+def test_stored_memory_and_errors():
+    from paper_2006_02551_gb300 import WadgError
+    w = workload("cube4_n3")
+    for prec, rs in (("fp64", 8), ("fp32", 4)):
+        s, sim, mask = make_pair(w.N, w.n_hex, w.jitter, w.mesh_seed, w.pml, prec,
+                                 probes=w.probes, scheme="stored")
+        Np = sim.Np
+        NpP = (Np + 3) & ~3
+        mem = s.memory_report()
+        assert mem["pml_coeff"] == int(mask.sum()) * 9 * Np * NpP * rs
+        with pytest.raises(WadgError):   # the adjoint is built for the WAA scheme
+            s.adjoint(5, 0.01, 5)
+        with pytest.raises(WadgError):   # stored scheme: kappa = 1 only
+            s.set_pml(PmlProfile(u0=0.75, L=0.25, sigma_max=20.0, p_sigma=3.0,
+                                 kappa_max=2.0), "stored")
+        s.close()
