@@ -107,13 +107,13 @@ class ClockSampler:
                 "samples": len(rows), "reasons": reasons}
 
 
-def setup_solver(w, precision, stream, device):
+def setup_solver(w, precision, stream, device, scheme="waa"):
     from paper_2006_02551_gb300 import Solver
     from synthetic import cube_tet_mesh
     v, e = cube_tet_mesh(w.n_hex, w.jitter, w.mesh_seed)
     s = Solver(w.N, precision, n_batch=w.n_batch, device=device, stream=stream)
     s.set_mesh(v, e)
-    s.set_pml(w.pml)
+    s.set_pml(w.pml, scheme)
     s.set_sources(list(w.sources))
     s.set_probes(list(w.probes))
     s.set_state(None, 0.0)
@@ -187,6 +187,8 @@ def main():
                     help="override the cube size of the workload (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
+    ap.add_argument("--no-stored", action="store_true",
+                    help="skip the stored-matrix scheme comparison run")
     ap.add_argument("--ref-hex", type=int, default=4,
                     help="cube size of the oracle sample for --impl reference")
     ap.add_argument("--cpu-hex", type=int, default=12,
@@ -351,6 +353,39 @@ def main():
             out_extra[prec] = rate
     else:
         s.close()
+
+    # the stored-matrix scheme (eqs. 10-13) on the same workload: FP32 state,
+    # CUDA-core PML kernel reading 9 N_p^2 operator values per PML element
+    if not args.no_stored and rank == 0 and w.pml.kappa_max == 1.0:
+        t0s = time.perf_counter()
+        ss = setup_solver(w, "fp32", sh, local, scheme="stored")
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0s
+        nrate = 50
+        ss.run_steps(3, dt, record=False)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ss.run_steps(nrate, dt, record=False)
+        e1.record(stream)
+        e1.synchronize()
+        mss = e0.elapsed_time(e1) / nrate
+        kss = ss.profile_stage(10, dt)
+        mems = ss.memory_report()
+        ss.close()
+        NpP = (Np + 3) & ~3
+        field_b = 4 * 4 * 12 * Np + 9 * 8 + 4 * 3 + 16
+        sb = K1 * w.n_batch * field_b + mems["pml_coeff"] * w.n_batch
+        out_extra["stored_scheme"] = {
+            "value": dofs / (mss * 1e-3), "unit": "DOF-updates/s", "ms_per_step": mss,
+            "precision": "fp32", "kernel_ms": {"std": kss[0], "pml": kss[1]},
+            "pml_coeff_bytes": mems["pml_coeff"],
+            "pml_coeff_bytes_per_pml_element": mems["pml_coeff"] / max(K1, 1),
+            "operators_per_pml_element": f"9 x {Np} x {NpP} (kappa = 1)",
+            "setup_s": setup_s,
+            "pml_kernel_hbm": {"bytes_per_launch": sb, "achieved_gbs": sb / (kss[1] * 1e-3) / 1e9,
+                               "peak_gbs": hbm, "frac": sb / (kss[1] * 1e-3) / 1e9 / hbm},
+            "vs_waa": {"memory_ratio": mems["pml_coeff"] / max(mem["pml_coeff"], 1),
+                       "time_ratio_vs_this_run": mss / (ms / args.steps)}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
