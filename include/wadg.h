@@ -116,6 +116,17 @@ wadg_status wadg_destroy(wadg_ctx* ctx);
 wadg_status wadg_set_mesh(wadg_ctx* ctx, int64_t nv, const double* vxyz, int64_t K,
                           const int64_t* etov);
 
+/* wadg_set_mesh with periodic boundaries: vcanon[nv] maps every vertex to a
+ * representative (0 <= vcanon[v] < nv); two faces whose vertices have the same
+ * representatives are neighbours, with their face nodes matched through that
+ * vertex correspondence (so the two faces must be translates of each other
+ * with the corresponding vertices in corresponding positions).  Used for the
+ * lateral boundaries of the normal-incidence plane-wave box (Section III).
+ * vcanon = NULL is wadg_set_mesh.  EINVAL as wadg_set_mesh, and for a
+ * representative out of range. */
+wadg_status wadg_set_mesh_periodic(wadg_ctx* ctx, int64_t nv, const double* vxyz, int64_t K,
+                                   const int64_t* etov, const int64_t* vcanon);
+
 /* Per-element relative permittivity and permeability eps_r[K], mu_r[K]
  * (caller element order, must be > 0); NULL means 1.  Enters the update
  * equations as eps_k, mu_k (eqs. 10, 11) and the upwind flux impedances. */

@@ -21,7 +21,10 @@ from .refelem import FACE_VERTS
 
 
 class Geometry:
-    def __init__(self, ref, vxyz, etov):
+    def __init__(self, ref, vxyz, etov, vcanon=None):
+        """vcanon: optional [nv] periodic identification of the vertices (two
+        faces whose vertices have the same representatives are neighbours,
+        their nodes matched up to the translation between the two faces)."""
         vxyz = np.asarray(vxyz, dtype=np.float64)
         etov = np.asarray(etov, dtype=np.int64)
         self.ref = ref
@@ -59,7 +62,7 @@ class Geometry:
             self.nz[:, f] = fn[f][:, 2] / mag
             self.sJ[:, f] = mag * self.J
         self.Fscale = self.sJ / self.J[:, None]
-        self._connect(etov)
+        self._connect(etov, None if vcanon is None else np.asarray(vcanon, np.int64))
 
     def map_points(self, r, s, t):
         v = self.verts
@@ -72,11 +75,13 @@ class Geometry:
                          + np.outer(v[:, 2, d], l3) + np.outer(v[:, 3, d], l4)
                          for d in range(3)])
 
-    def _connect(self, etov):
+    def _connect(self, etov, vcanon=None):
         ref = self.ref
         K, Np, Nfp = self.K, ref.Np, ref.Nfp
-        # faces sharing the same sorted vertex triple are neighbours
-        keys = np.sort(etov[:, np.array(FACE_VERTS)], axis=2).reshape(-1, 3)
+        # faces sharing the same sorted vertex triple (of periodic
+        # representatives, when given) are neighbours
+        ids = etov if vcanon is None else vcanon[etov]
+        keys = np.sort(ids[:, np.array(FACE_VERTS)], axis=2).reshape(-1, 3)
         order = np.lexsort((keys[:, 2], keys[:, 1], keys[:, 0]))
         ks = keys[order]
         same = np.all(ks[1:] == ks[:-1], axis=1)
@@ -102,9 +107,14 @@ class Geometry:
             k2, f2 = self.EToE[k1, f1], self.EToF[k1, f1]
             idM = k1[:, None] * Np + fm[f1]
             idP = k2[:, None] * Np + fm[f2]
+            # translation between the two faces (zero unless periodic)
+            fv = np.array(FACE_VERTS)
+            shift = (self.verts[k1[:, None], fv[f1]].mean(axis=1)
+                     - self.verts[k2[:, None], fv[f2]].mean(axis=1))      # (n, 3)
             d = np.zeros((k1.size, Nfp, Nfp))
             for c in range(3):
-                d += (X[c][idM][:, :, None] - X[c][idP][:, None, :]) ** 2
+                d += (X[c][idM][:, :, None] - shift[:, c, None, None]
+                      - X[c][idP][:, None, :]) ** 2
             match = np.argmin(d, axis=2)
             best = np.take_along_axis(d, match[:, :, None], axis=2)
             if np.any(np.sqrt(best) > tol):

@@ -35,9 +35,9 @@ def dipole_current(src, t):
 class Simulation:
     def __init__(self, N, vxyz, etov, profile=None, eps=None, mu=None,
                  sources=(), probes=(), n_batch=1, scheme="waa", alpha=1.0,
-                 stored_quad_points=None):
+                 stored_quad_points=None, vcanon=None):
         self.ref = ref_element(N)
-        self.geom = Geometry(self.ref, vxyz, etov)
+        self.geom = Geometry(self.ref, vxyz, etov, vcanon)
         self.disc = Discretization(self.ref, self.geom, eps, mu, profile,
                                    alpha, stored_quad_points)
         self.N, self.K, self.Np = N, self.geom.K, self.ref.Np

@@ -817,6 +817,11 @@ wadg_status wadg_destroy(wadg_ctx* ctx) {
 
 wadg_status wadg_set_mesh(wadg_ctx* ctx, int64_t nv, const double* vxyz, int64_t K,
                           const int64_t* etov) {
+  return wadg_set_mesh_periodic(ctx, nv, vxyz, K, etov, nullptr);
+}
+
+wadg_status wadg_set_mesh_periodic(wadg_ctx* ctx, int64_t nv, const double* vxyz, int64_t K,
+                                   const int64_t* etov, const int64_t* vcanon) {
   if (!ctx) return fail(nullptr, WADG_EINVAL, "null context");
   if (nv < 4 || K < 1 || !vxyz || !etov) return fail(ctx, WADG_EINVAL, "empty mesh");
   if (K > (int64_t)1 << 30) return fail(ctx, WADG_EINVAL, "too many elements");
@@ -825,6 +830,13 @@ wadg_status wadg_set_mesh(wadg_ctx* ctx, int64_t nv, const double* vxyz, int64_t
     if (etov[i] < 0 || etov[i] >= nv)
       return fail(ctx, WADG_EINVAL, "etov[%lld] = %lld out of range", (long long)i,
                   (long long)etov[i]);
+  if (vcanon)
+    for (int64_t i = 0; i < nv; ++i)
+      if (vcanon[i] < 0 || vcanon[i] >= nv)
+        return fail(ctx, WADG_EINVAL, "vcanon[%lld] = %lld out of range", (long long)i,
+                    (long long)vcanon[i]);
+  // face keys use the periodic representatives of the vertices
+  auto cv = [vcanon](int64_t v) { return vcanon ? vcanon[v] : v; };
   ctx->has_mesh = false;
   ctx->K = K;
   ctx->nv = nv;
@@ -887,7 +899,7 @@ wadg_status wadg_set_mesh(wadg_ctx* ctx, int64_t nv, const double* vxyz, int64_t
   for (int64_t k = 0; k < K; ++k)
     for (int f = 0; f < 4; ++f) {
       int64_t v3[3];
-      for (int i = 0; i < 3; ++i) v3[i] = etov[4 * k + kFaceVerts[f][i]];
+      for (int i = 0; i < 3; ++i) v3[i] = cv(etov[4 * k + kFaceVerts[f][i]]);
       std::sort(v3, v3 + 3);
       fk[4 * k + f] = {v3[0], v3[1], v3[2], 4 * k + f};
     }
@@ -912,8 +924,8 @@ wadg_status wadg_set_mesh(wadg_ctx* ctx, int64_t nv, const double* vxyz, int64_t
         int64_t k = me / 4, f = me % 4, k2 = ot / 4, f2 = ot % 4;
         int64_t gv[3], hv[3];
         for (int a = 0; a < 3; ++a) {
-          gv[a] = etov[4 * k + kFaceVerts[f][a]];
-          hv[a] = etov[4 * k2 + kFaceVerts[f2][a]];
+          gv[a] = cv(etov[4 * k + kFaceVerts[f][a]]);
+          hv[a] = cv(etov[4 * k2 + kFaceVerts[f2][a]]);
         }
         int rot = -1;
         for (int r = 0; r < 6 && rot < 0; ++r)

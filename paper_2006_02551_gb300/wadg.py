@@ -47,6 +47,7 @@ _SIG = {
     "wadg_create": [C.c_int, C.c_int, C.c_int32, C.c_int, _P, C.POINTER(_P)],
     "wadg_destroy": [_P],
     "wadg_set_mesh": [_P, C.c_int64, _D, C.c_int64, _I64],
+    "wadg_set_mesh_periodic": [_P, C.c_int64, _D, C.c_int64, _I64, _I64],
     "wadg_set_materials": [_P, _D, _D],
     "wadg_set_pml_profile": [_P, C.POINTER(wadg_pml_profile), C.c_int],
     "wadg_set_sources": [_P, C.c_int32, C.POINTER(wadg_dipole)],
@@ -150,11 +151,18 @@ class Solver:
     def _c(self, st):
         _check(st, self.ctx)
 
-    def set_mesh(self, vxyz, etov):
+    def set_mesh(self, vxyz, etov, vcanon=None):
+        """vcanon: optional periodic vertex representatives (wadg_set_mesh_periodic)."""
         v = np.ascontiguousarray(vxyz, dtype=np.float64)
         e = np.ascontiguousarray(etov, dtype=np.int64)
-        self._c(self.lib.wadg_set_mesh(self.ctx, v.shape[0], _ptr(v), e.shape[0],
-                                       e.ctypes.data_as(_I64)))
+        if vcanon is None:
+            self._c(self.lib.wadg_set_mesh(self.ctx, v.shape[0], _ptr(v), e.shape[0],
+                                           e.ctypes.data_as(_I64)))
+        else:
+            c = np.ascontiguousarray(vcanon, dtype=np.int64)
+            self._c(self.lib.wadg_set_mesh_periodic(self.ctx, v.shape[0], _ptr(v), e.shape[0],
+                                                    e.ctypes.data_as(_I64),
+                                                    c.ctypes.data_as(_I64)))
         self.K = e.shape[0]
 
     def set_materials(self, eps_r=None, mu_r=None):
