@@ -39,6 +39,28 @@ SM_MAX_MHZ = 2070.0
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (no measured figure available)
 
 
+# DRAM traffic per PML element of the TF32 PML stage kernel, from one
+# ncu --set full capture of the small case of the benchmark recipe (summary
+# and command in profiles/tc_stage_kernels_cube24_n4_full.md), valid for the
+# kernel source it was taken on (sha256 of csrc/tc_kernels.cu)
+TC_PML_TRAFFIC = {"sha256": "32e3ce971f6d2909e80441628067d6081273ab67d71296450c8b22540e95ff0b",
+                  "bytes_per_pml_element": 7585.0, "N": 4}
+
+
+def tc_pml_traffic(K1, N):
+    """Per-launch DRAM bytes of the PML kernel, or None once the kernel changed."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2006_02551_gb300", "csrc", "tc_kernels.cu")
+    try:
+        with open(src, "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+    if h != TC_PML_TRAFFIC["sha256"] or N != TC_PML_TRAFFIC["N"]:
+        return None
+    return TC_PML_TRAFFIC["bytes_per_pml_element"] * K1
+
+
 def describe(w):
     return (f"{w.name}: {w.n_hex}^3x6={w.K} jittered tets (+-{w.jitter}h, seed {w.mesh_seed}), "
             f"N={w.N}, cubic PML sigma_max={w.pml.sigma_max} shell {w.pml.L} "
@@ -277,8 +299,10 @@ def main():
     achieved_gbs = d_bytes / (d_ms * 1e-3) / 1e9
     if args.precision == "tf32":
         # tensor-core contractions: the stage is bound by HBM traffic
+        traffic = tc_pml_traffic(K1 * w.n_batch, N) if dom == "pml" else None
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
-                    "frac": achieved_gbs / hbm, "traffic": None,
+                    "frac": achieved_gbs / hbm, "traffic": traffic,
+                    "traffic_source": "profiles/tc_stage_kernels_cube24_n4_full.md (scaled by elements)",
                     "kernel": f"tc_stage_kernel<{dom}>",
                     "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                     "alu": {"achieved_tflops": achieved}}
