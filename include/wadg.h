@@ -261,6 +261,50 @@ wadg_status wadg_reference_operator(int N, int which, double* out, int64_t cap,
  * wadg_create / wadg_reference_operator when ctx is NULL). */
 const char* wadg_last_error(const wadg_ctx* ctx);
 
+/* ---------------------------------------------------------------- groups
+ * Several contexts advanced together (the batching form: meshes of uneven
+ * size and order in one launch per Runge-Kutta stage).  Every stage of every
+ * member and element class is one launch of a grouped CUDA-core kernel: its
+ * blocks start on the (member, class) items in proportion to their
+ * algorithmic flops and then take tiles from per-item counters until none
+ * are left, so the load balances itself; one step (the 5 stage launches and
+ * each member's probe and clock kernels) is captured in a CUDA graph.  Members: FP32
+ * contexts (WADG_FP32) with a mesh, the weight-adjusted or element-constant
+ * PML scheme, on one device; the group runs on the first member's stream.
+ * Each member keeps its own state, time, probes and records.  The group
+ * refers to its members: destroy the group before any member. */
+typedef struct wadg_group wadg_group;
+
+/* EINVAL for a null or repeated member or members on different devices,
+ * ESTATE for a member without a mesh, EUNSUPPORTED for a member that is not an
+ * FP32 context or uses the stored-matrix scheme. */
+wadg_status wadg_group_create(int32_t n, wadg_ctx* const* ctxs, wadg_group** out);
+wadg_status wadg_group_destroy(wadg_group* g);
+
+/* Tile sizes and grid: times `reps` grouped stage launches for every
+ * candidate (256 or 512 threads per block; elements per tile = the largest
+ * that fits / {1, 2, 4}; 1..4 blocks per SM within the occupancy limit) with
+ * the members' step sizes
+ * dt[n], keeps the fastest and writes its time per stage launch (ms) to
+ * ms_out (may be NULL).  The stages run on the members' current state, which
+ * is left undefined: call it before wadg_set_state. */
+wadg_status wadg_group_autotune(wadg_group* g, const double* dt, int32_t reps, double* ms_out);
+
+/* The current launch shape: total blocks, threads per block, blocks per SM,
+ * tile divisor, work items (any pointer may be NULL). */
+wadg_status wadg_group_info(const wadg_group* g, int32_t* nblocks, int32_t* threads,
+                            int32_t* blocks_per_sm, int32_t* tile_divisor, int32_t* nitems);
+
+/* nsteps steps of every member with its own dt[n]; probe_out[n] (entries may
+ * be NULL, or probe_out itself) receive each member's records laid out as in
+ * wadg_run_steps.  Gives each member the values wadg_run_steps would. */
+wadg_status wadg_group_run_steps(wadg_group* g, int64_t nsteps, const double* dt,
+                                 double* const* probe_out);
+
+/* Text of the last error of a group call (of the creating call for a NULL
+ * group). */
+const char* wadg_group_last_error(const wadg_group* g);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1542,3 +1542,362 @@ extern "C" wadg_status wadg_run_steps_noalloc(wadg_ctx* ctx, int64_t nsteps, dou
   if (hflag) return fail(ctx, WADG_ENONFINITE, "state became non-finite");
   return check_err_flag(ctx);
 }
+
+// ====================================================================== groups
+// Several contexts (meshes of any size and order, FP32 CUDA-core kernels)
+// advanced together: every Runge-Kutta stage of every member is one launch of
+// group_stage_kernel; its blocks start on the (member, element class) items in
+// proportion to the work and then take tiles from per-item counters until
+// none are left (dynamic balancing); one step (5 launches plus each member's
+// probe and clock kernels) is captured in a CUDA graph.
+struct wadg_group {
+  std::vector<wadg_ctx*> ctx;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int sms = 1;
+  int blocks_per_sm = 1;   // autotuned
+  int tile_div = 1;        // autotuned: tile = largest tile / tile_div
+  int threads = 256;       // autotuned: threads per block (256 or 512)
+  size_t smem = 0;
+  int nblocks = 0;
+  struct Item { int c; bool pml; int code; int tile; int64_t tiles; double work; };
+  std::vector<Item> items;
+  std::vector<int> first;
+  DevPtr dparams, dfirst, dcode;   // params [2 parities][5 stages][items]
+  DevPtr dntiles, dcounter;        // tiles per item, tile counters (zeroed per launch)
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+wadg_status gfail(wadg_group* g, wadg_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g->err = buf;
+  return s;
+}
+
+#define GCK(call)                                                                       \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return gfail(g, e_ == cudaErrorMemoryAllocation ? WADG_ENOMEM : WADG_ECUDA,       \
+                   "%s: %s", #call, cudaGetErrorString(e_));                            \
+  } while (0)
+
+void group_drop_graphs(wadg_group* g) {
+  for (auto& x : g->graph)
+    if (x) { cudaGraphExecDestroy(x); x = nullptr; }
+}
+
+// per-element flops of a stage (the algorithmic count used by the benchmark),
+// the weight of a work item in the block split
+double item_cost(int N, bool pml) {
+  const double Np = (N + 1) * (N + 2) * (N + 3) / 6.0, Nfp = (N + 1) * (N + 2) / 2.0;
+  const double Nq = (N + 1.0) * (N + 1.0) * (N + 1.0);
+  double f = 36 * Np * Np + 90 * Np + 240 * Nfp + 48 * Np * Nfp + 24 * Np;
+  if (pml) f += 48 * Nq * Np + 24 * Nq + 36 * Np;
+  return f;
+}
+
+// work items, tile sizes and the block split for the current tuning
+void group_plan(wadg_group* g) {
+  g->items.clear();
+  g->smem = 0;
+  for (int c = 0; c < (int)g->ctx.size(); ++c) {
+    wadg_ctx* x = g->ctx[c];
+    for (int cls = 0; cls < 2; ++cls) {
+      const int64_t ne = cls == 0 ? x->K0 : x->K1;
+      if (ne == 0) continue;
+      const bool pml = cls == 1;
+      wadg_group::Item it;
+      it.c = c;
+      it.pml = pml;
+      it.code = x->N * 4 + (pml ? (x->kappa ? 2 : 1) : 0);
+      const int tmax = group_tile_max(x->N, pml, g->threads);
+      it.tile = std::max(1, tmax / g->tile_div);
+      it.tiles = (ne + it.tile - 1) / it.tile * x->nb;
+      it.work = item_cost(x->N, pml) * (double)ne * x->nb;
+      g->items.push_back(it);
+      g->smem = std::max(g->smem, group_smem_bytes(x->N, pml, it.tile, g->threads));
+    }
+  }
+  double tot = 0.0;
+  for (auto& it : g->items) tot += it.work;
+  const int want = g->blocks_per_sm * g->sms;
+  g->first.assign(1, 0);
+  for (auto& it : g->items) {
+    int64_t nb = (int64_t)std::llround(want * it.work / std::max(tot, 1.0));
+    nb = std::max<int64_t>(1, std::min<int64_t>(nb, it.tiles));
+    g->first.push_back(g->first.back() + (int)nb);
+  }
+  g->nblocks = g->first.back();
+}
+
+// stage parameters of every item for both step parities and all 5 stages
+wadg_status group_upload(wadg_group* g, const double* dt) {
+  const int ni = (int)g->items.size();
+  std::vector<StageParams<float>> hp((size_t)2 * 5 * ni);
+  std::vector<int> cur0(g->ctx.size());
+  for (size_t c = 0; c < g->ctx.size(); ++c) cur0[c] = g->ctx[c]->cur;
+  for (int par = 0; par < 2; ++par)
+    for (int st = 0; st < 5; ++st)
+      for (int i = 0; i < ni; ++i) {
+        const auto& it = g->items[i];
+        wadg_ctx* x = g->ctx[it.c];
+        // every stage flips a member's buffers; a step (5 stages) flips them once
+        x->cur = cur0[it.c] ^ par ^ (st & 1);
+        StageParams<float> P = stage_params<float>(x, st, dt[it.c], 0.0, true, it.pml);
+        P.nb = x->nb;
+        P.tile_elems = it.tile;
+        hp[((size_t)par * 5 + st) * ni + i] = P;
+        x->cur = cur0[it.c];
+      }
+  std::vector<int> code(ni), ntiles(ni);
+  for (int i = 0; i < ni; ++i) {
+    code[i] = g->items[i].code;
+    ntiles[i] = (int)g->items[i].tiles;
+  }
+  GCK(dalloc(g->dntiles, ntiles.size() * sizeof(int)));
+  GCK(dalloc(g->dcounter, ntiles.size() * sizeof(int)));
+  GCK(cudaMemcpy(g->dntiles.p, ntiles.data(), ntiles.size() * sizeof(int), cudaMemcpyHostToDevice));
+  GCK(dalloc(g->dparams, hp.size() * sizeof(StageParams<float>)));
+  GCK(dalloc(g->dfirst, g->first.size() * sizeof(int)));
+  GCK(dalloc(g->dcode, code.size() * sizeof(int)));
+  GCK(cudaMemcpy(g->dparams.p, hp.data(), hp.size() * sizeof(StageParams<float>),
+                 cudaMemcpyHostToDevice));
+  GCK(cudaMemcpy(g->dfirst.p, g->first.data(), g->first.size() * sizeof(int),
+                 cudaMemcpyHostToDevice));
+  GCK(cudaMemcpy(g->dcode.p, code.data(), code.size() * sizeof(int), cudaMemcpyHostToDevice));
+  return WADG_OK;
+}
+
+GroupParams group_params(wadg_group* g, int par, int st) {
+  GroupParams G{};
+  G.p = (const StageParams<float>*)g->dparams.p + ((size_t)par * 5 + st) * g->items.size();
+  G.first = (const int*)g->dfirst.p;
+  G.code = (const int*)g->dcode.p;
+  G.ntiles = (const int*)g->dntiles.p;
+  G.counter = (int*)g->dcounter.p;
+  G.nitems = (int)g->items.size();
+  return G;
+}
+
+// one grouped stage launch: clear the tile counters, launch
+cudaError_t group_launch(wadg_group* g, int par, int st) {
+  cudaError_t e = cudaMemsetAsync(g->dcounter.p, 0, g->items.size() * sizeof(int), g->stream);
+  if (e != cudaSuccess) return e;
+  return launch_group_stage(group_params(g, par, st), g->nblocks, g->smem, g->threads, g->stream);
+}
+
+// one step of parity par: 5 grouped stage launches, then every member's probes
+// and clock
+wadg_status group_issue_step(wadg_group* g, int par, const double* dt) {
+  for (int st = 0; st < 5; ++st) GCK(group_launch(g, par, st));
+  for (size_t c = 0; c < g->ctx.size(); ++c) {
+    wadg_ctx* x = g->ctx[c];
+    if (x->nprobe > 0) {
+      ProbeParams pp{};
+      pp.q = x->q[x->cur ^ par ^ 1].p;   // the step's output buffer
+      pp.strideQ = x->K * 6 * x->ref.Np;
+      pp.nprobe = x->nprobe;
+      pp.nb = x->nb;
+      pp.Np = x->ref.Np;
+      pp.elem = (const int*)x->pr_elem.p;
+      pp.ell = (const double*)x->pr_ell.p;
+      pp.out = (double*)x->pr_out.p;
+      pp.obj = (double*)x->obj.p;
+      pp.step = (const int64_t*)x->stepdev.p;
+      GCK(launch_probes(false, pp, g->stream));
+    }
+    GCK(launch_advance((double*)x->tdev.p, (int64_t*)x->stepdev.p, dt[c], g->stream));
+  }
+  return WADG_OK;
+}
+
+wadg_status group_capture(wadg_group* g, const double* dt) {
+  group_drop_graphs(g);
+  for (int par = 0; par < 2; ++par) {
+    cudaGraph_t graph;
+    GCK(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
+    wadg_status st = group_issue_step(g, par, dt);
+    cudaError_t e = cudaStreamEndCapture(g->stream, &graph);
+    if (st != WADG_OK) return st;
+    GCK(e);
+    e = cudaGraphInstantiate(&g->graph[par], graph, 0);
+    cudaGraphDestroy(graph);
+    GCK(e);
+  }
+  return WADG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+wadg_status wadg_group_create(int32_t n, wadg_ctx* const* ctxs, wadg_group** out) {
+  if (!out || n < 1 || !ctxs) return fail(nullptr, WADG_EINVAL, "bad group arguments");
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    wadg_ctx* x = ctxs[i];
+    if (!x) return fail(nullptr, WADG_EINVAL, "null context %d", i);
+    if (!x->has_mesh) return fail(nullptr, WADG_ESTATE, "context %d has no mesh", i);
+    if (x->prec != WADG_FP32 || x->tc)
+      return fail(nullptr, WADG_EUNSUPPORTED, "groups run the FP32 CUDA-core kernels (context %d)", i);
+    if (x->scheme == WADG_PML_STORED)
+      return fail(nullptr, WADG_EUNSUPPORTED, "groups run the weight-adjusted kernels (context %d)", i);
+    if (x->device != ctxs[0]->device)
+      return fail(nullptr, WADG_EINVAL, "group members must share a device");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == x) return fail(nullptr, WADG_EINVAL, "context %d listed twice", i);
+  }
+  wadg_group* g = new wadg_group();
+  g->ctx.assign(ctxs, ctxs + n);
+  g->device = ctxs[0]->device;
+  g->stream = ctxs[0]->stream;
+  cudaSetDevice(g->device);
+  cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device);
+  if (g->sms < 1) g->sms = 1;
+  cudaError_t e = configure_group_kernel();
+  if (e != cudaSuccess) {
+    delete g;
+    return fail(nullptr, WADG_ECUDA, "group kernel set-up: %s", cudaGetErrorString(e));
+  }
+  group_plan(g);
+  g->blocks_per_sm = std::max(1, std::min(2, group_blocks_per_sm(g->smem, g->threads)));
+  group_plan(g);
+  *out = g;
+  return WADG_OK;
+}
+
+wadg_status wadg_group_destroy(wadg_group* g) {
+  if (!g) return WADG_OK;
+  cudaSetDevice(g->device);
+  group_drop_graphs(g);
+  dfree(g->dparams);
+  dfree(g->dfirst);
+  dfree(g->dcode);
+  dfree(g->dntiles);
+  dfree(g->dcounter);
+  delete g;
+  return WADG_OK;
+}
+
+wadg_status wadg_group_autotune(wadg_group* g, const double* dt, int32_t reps, double* ms_out) {
+  if (!g) return WADG_EINVAL;
+  if (!dt || reps < 1) return gfail(g, WADG_EINVAL, "bad arguments");
+  cudaSetDevice(g->device);
+  group_drop_graphs(g);
+  cudaEvent_t e0, e1;
+  GCK(cudaEventCreate(&e0));
+  GCK(cudaEventCreate(&e1));
+  double best = 1e300;
+  int best_bps = 1, best_div = 1, best_thr = 256;
+  for (int thr : {256, 512})
+  for (int div : {1, 2, 4}) {
+    g->threads = thr;
+    g->tile_div = div;
+    g->blocks_per_sm = 1;
+    group_plan(g);
+    const int occ = std::max(1, group_blocks_per_sm(g->smem, thr));
+    for (int bps = 1; bps <= std::min(occ, 4); ++bps) {
+      g->blocks_per_sm = bps;
+      group_plan(g);
+      wadg_status s = group_upload(g, dt);
+      if (s != WADG_OK) return s;
+      for (int st = 0; st < 5; ++st) GCK(group_launch(g, 0, st));   // one untimed step
+      GCK(cudaEventRecord(e0, g->stream));
+      for (int r = 0; r < reps; ++r) GCK(group_launch(g, 0, r % 5));
+      GCK(cudaEventRecord(e1, g->stream));
+      GCK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      GCK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) { best = ms; best_bps = bps; best_div = div; best_thr = thr; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  g->blocks_per_sm = best_bps;
+  g->tile_div = best_div;
+  g->threads = best_thr;
+  group_plan(g);
+  if (ms_out) *ms_out = best / reps;
+  return WADG_OK;
+}
+
+wadg_status wadg_group_info(const wadg_group* g, int32_t* nblocks, int32_t* threads,
+                            int32_t* blocks_per_sm, int32_t* tile_divisor, int32_t* nitems) {
+  if (!g) return WADG_EINVAL;
+  if (nblocks) *nblocks = g->nblocks;
+  if (threads) *threads = g->threads;
+  if (blocks_per_sm) *blocks_per_sm = g->blocks_per_sm;
+  if (tile_divisor) *tile_divisor = g->tile_div;
+  if (nitems) *nitems = (int32_t)g->items.size();
+  return WADG_OK;
+}
+
+wadg_status wadg_group_run_steps(wadg_group* g, int64_t nsteps, const double* dt,
+                                 double* const* probe_out) {
+  if (!g) return WADG_EINVAL;
+  if (!dt || nsteps < 0) return gfail(g, WADG_EINVAL, "bad arguments");
+  for (size_t c = 0; c < g->ctx.size(); ++c)
+    if (!(dt[c] > 0)) return gfail(g, WADG_EINVAL, "dt of member %d must be > 0", (int)c);
+  if (nsteps == 0) return WADG_OK;
+  cudaSetDevice(g->device);
+  const int64_t chunk = std::min<int64_t>(nsteps, 4096);
+  for (wadg_ctx* x : g->ctx) {
+    const size_t need = (size_t)chunk * x->nprobe * 6 * x->nb * 8;
+    if (x->nprobe > 0 && x->pr_out.bytes < need) {
+      invalidate_graphs(x);
+      cudaError_t e = dalloc(x->pr_out, need);
+      if (e != cudaSuccess) return gfail(g, WADG_ENOMEM, "probe records: %s", cudaGetErrorString(e));
+    }
+  }
+  // member buffers may have moved since the last call: rebuild the parameter
+  // tables and the graphs
+  group_plan(g);
+  wadg_status s = group_upload(g, dt);
+  if (s != WADG_OK) return s;
+  s = group_capture(g, dt);
+  if (s != WADG_OK) return s;
+  int64_t done = 0;
+  int par = 0;
+  while (done < nsteps) {
+    const int64_t n = std::min(chunk, nsteps - done);
+    for (size_t c = 0; c < g->ctx.size(); ++c) {
+      wadg_ctx* x = g->ctx[c];
+      const double tt = x->t + done * dt[c];
+      GCK(cudaMemcpyAsync(x->tdev.p, &tt, 8, cudaMemcpyHostToDevice, g->stream));
+      GCK(cudaMemsetAsync(x->stepdev.p, 0, 8, g->stream));
+    }
+    for (int64_t i = 0; i < n; ++i) {
+      GCK(cudaGraphLaunch(g->graph[par], g->stream));
+      par ^= 1;
+    }
+    for (size_t c = 0; c < g->ctx.size(); ++c) {
+      wadg_ctx* x = g->ctx[c];
+      const size_t rec = (size_t)x->nprobe * 6 * x->nb;
+      if (probe_out && probe_out[c] && rec)
+        GCK(cudaMemcpyAsync(probe_out[c] + (size_t)done * rec, x->pr_out.p, (size_t)n * rec * 8,
+                            cudaMemcpyDeviceToHost, g->stream));
+    }
+    GCK(cudaStreamSynchronize(g->stream));
+    done += n;
+  }
+  for (size_t c = 0; c < g->ctx.size(); ++c) {
+    wadg_ctx* x = g->ctx[c];
+    x->t += nsteps * dt[c];
+    if (nsteps & 1) x->cur ^= 1;   // each step flips the buffers once
+  }
+  return WADG_OK;
+}
+
+const char* wadg_group_last_error(const wadg_group* g) {
+  return g ? g->err.c_str() : g_err.c_str();
+}
+
+}  // extern "C"

@@ -36,10 +36,12 @@ struct Dims {
 
 // Launch configuration: persistent blocks, the reference operators staged in
 // shared memory once per block, tiles of T elements processed in a loop.
-template <typename Real, int N, bool PML>
+template <typename Real, int N, bool PML, int NT_ = 0>
 struct Tile {
   using D = Dims<N>;
-  static constexpr int THREADS = (sizeof(Real) == 4 && PML) ? 512 : 256;
+  // threads of a block: the single-class launches use 512 for FP32 PML tiles;
+  // the grouped launch fixes 256 for every class
+  static constexpr int THREADS = NT_ > 0 ? NT_ : ((sizeof(Real) == 4 && PML) ? 512 : 256);
   static constexpr int CF = PML ? 12 : 6;                  // field components held
   static constexpr int f_sz = D::Np * CF;                  // F[e][j][CF]
   static constexpr int u_sz = PML ? ((D::NF * 6 > D::NqP * 12) ? D::NF * 6 : D::NqP * 12)
@@ -108,15 +110,19 @@ __device__ __forceinline__ void lds2(const double* p, double* v) {
 // Stage kernel.  Threads work on register tiles: 4 nodes x 3 components x 3
 // reference derivatives (curl), 4 quadrature points x 12 components (V_q),
 // 4 nodes x 4 components (P_q).  All operator reads come from shared memory.
-template <typename Real, int N, bool PML, bool KAPPA, bool STORED = false>
-__global__ void __launch_bounds__(Tile<Real, N, PML>::THREADS)
-stage_kernel(const StageParams<Real> P) {
+// Body of the stage kernel for one element class of one context; smem_raw is
+// the block's dynamic shared memory.  Static schedule: block `bid` of `nblk`
+// takes tiles bid, bid + nblk, ...  Dynamic schedule (dyn != nullptr, the
+// grouped launch): the block takes tiles from the counter *dyn until they run
+// out.
+template <typename Real, int N, bool PML, bool KAPPA, bool STORED, int NT_>
+__device__ __forceinline__ void stage_body(const StageParams<Real>& P, unsigned char* smem_raw,
+                                           int bid, int nblk, int* dyn = nullptr) {
   using D = Dims<N>;
   constexpr int Np = D::Np, Nfp = D::Nfp, Nq = D::Nq, NF = D::NF;
   constexpr int NpP = D::NpP, NqP = D::NqP, NIQ = D::NIQ, NQQ = D::NQQ;
-  using TL = Tile<Real, N, PML>;
+  using TL = Tile<Real, N, PML, NT_>;
   constexpr int T = TL::T, CF = TL::CF, NT = TL::THREADS;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* sm = reinterpret_cast<Real*>(smem_raw);
   const Real* DrT = TL::OPS_SMEM ? sm : P.ops;   // operators
   const Real* DsT = DrT + Np * NpP;
@@ -124,12 +130,15 @@ stage_kernel(const StageParams<Real> P) {
   const Real* LIFTT = DtT + Np * NpP;
   const Real* VqT = LIFTT + NF * NpP;   // PML only
   const Real* PqT = VqT + Np * NqP;     // PML only
-  Real* F = sm + TL::ops_sz;         // [T][Np][CF]
-  Real* U = F + T * TL::f_sz;        // flux [T][NF][6] | tz [T][NqP][12]
-  Real* RS = U + T * TL::u_sz;       // [T][NpP][6]
-  Real* nrm = RS + T * TL::r_sz;     // [T][4][4]
-  Real* met = nrm + T * 16;          // [T][12] (9 used)
-  int* srcl = reinterpret_cast<int*>(met + T * 12);
+  // elements per tile: T, or fewer when the launch asks for smaller tiles
+  // (the shared-memory carve-up follows, so smaller tiles need less of it)
+  const int TE = P.tile_elems > 0 && P.tile_elems < T ? P.tile_elems : T;
+  Real* F = sm + TL::ops_sz;         // [TE][Np][CF]
+  Real* U = F + TE * TL::f_sz;       // flux [TE][NF][6] | tz [TE][NqP][12]
+  Real* RS = U + TE * TL::u_sz;      // [TE][NpP][6]
+  Real* nrm = RS + TE * TL::r_sz;    // [TE][4][4]
+  Real* met = nrm + TE * 16;         // [TE][12] (9 used)
+  int* srcl = reinterpret_cast<int*>(met + TE * 12);
   __shared__ int nsl;
 
   const unsigned char* Fmask = P.tabs;
@@ -147,13 +156,21 @@ stage_kernel(const StageParams<Real> P) {
   const double tbase = P.t_dev ? *P.t_dev : P.t;
   const double tst = tbase + P.rk_c * P.dt;
   const Real rka = (Real)P.rk_a, rkb = (Real)P.rk_b, rdt = (Real)P.dt;
-  const int tiles_per_batch = (P.n_elem + T - 1) / T;
+  const int tiles_per_batch = (P.n_elem + TE - 1) / TE;
   const int ntiles = tiles_per_batch * P.nb;
 
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  __shared__ int dyn_tile;
+  auto next_tile = [&](int cur) -> int {
+    if (!dyn) return cur < 0 ? bid : cur + nblk;
+    __syncthreads();   // every thread has read the previous value
+    if (tid == 0) dyn_tile = atomicAdd(dyn, 1);
+    __syncthreads();
+    return dyn_tile;
+  };
+  for (int tile = next_tile(-1); tile < ntiles; tile = next_tile(tile)) {
   const int b = tile / tiles_per_batch;
-  const int t0 = (tile - b * tiles_per_batch) * T;
-  const int ne = min(T, P.n_elem - t0);
+  const int t0 = (tile - b * tiles_per_batch) * TE;
+  const int ne = min(TE, P.n_elem - t0);
   const int eg0 = P.e_begin + t0;
   const int ep0 = eg0 - P.K0;
   const Real* qin = P.qin + (int64_t)b * P.strideQ;
@@ -598,6 +615,13 @@ stage_kernel(const StageParams<Real> P) {
 }
 
 template <typename Real, int N, bool PML, bool KAPPA, bool STORED = false>
+__global__ void __launch_bounds__(Tile<Real, N, PML>::THREADS)
+stage_kernel(const StageParams<Real> P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  stage_body<Real, N, PML, KAPPA, STORED, 0>(P, smem_raw, blockIdx.x, gridDim.x);
+}
+
+template <typename Real, int N, bool PML, bool KAPPA, bool STORED = false>
 static cudaError_t configure_one() {
   using TL = Tile<Real, N, PML>;
   return cudaFuncSetAttribute(stage_kernel<Real, N, PML, KAPPA, STORED>,
@@ -681,6 +705,123 @@ template cudaError_t launch_stage<double>(int, bool, bool, const StageParams<dou
                                           cudaStream_t);
 template cudaError_t launch_stage<float>(int, bool, bool, const StageParams<float>&, int,
                                          cudaStream_t);
+
+// ------------------------------------------------------------ grouped launch
+// One launch advances every element class of every context of a group by one
+// stage (FP32).  Every block starts on the (context, class) item the static
+// split gives it, takes that item's tiles from its counter, then moves on to
+// the items that still have tiles, restaging the operators once per item.
+// Two block shapes: 256 threads (two blocks per SM) or 512 (one).
+
+// dynamic shared memory of one item with `tile` elements per tile
+template <int N, bool PML, int NT>
+size_t group_smem_one(int tile) {
+  using TL = Tile<float, N, PML, NT>;
+  const int t = tile > 0 && tile < TL::T ? tile : TL::T;
+  return (size_t)(TL::ops_sz + t * TL::per_elem) * sizeof(float) + 64 * sizeof(int);
+}
+
+template <int NT>
+size_t group_smem_nt(int N, bool pml, int tile) {
+  switch (N) {
+    case 1: return pml ? group_smem_one<1, true, NT>(tile) : group_smem_one<1, false, NT>(tile);
+    case 2: return pml ? group_smem_one<2, true, NT>(tile) : group_smem_one<2, false, NT>(tile);
+    case 3: return pml ? group_smem_one<3, true, NT>(tile) : group_smem_one<3, false, NT>(tile);
+    case 4: return pml ? group_smem_one<4, true, NT>(tile) : group_smem_one<4, false, NT>(tile);
+    case 5: return pml ? group_smem_one<5, true, NT>(tile) : group_smem_one<5, false, NT>(tile);
+    default: return 0;
+  }
+}
+
+size_t group_smem_bytes(int N, bool pml, int tile, int threads) {
+  return threads == 512 ? group_smem_nt<512>(N, pml, tile) : group_smem_nt<256>(N, pml, tile);
+}
+
+template <int NT>
+int group_tile_nt(int N, bool pml) {
+  switch (N) {
+    case 1: return pml ? Tile<float, 1, true, NT>::T : Tile<float, 1, false, NT>::T;
+    case 2: return pml ? Tile<float, 2, true, NT>::T : Tile<float, 2, false, NT>::T;
+    case 3: return pml ? Tile<float, 3, true, NT>::T : Tile<float, 3, false, NT>::T;
+    case 4: return pml ? Tile<float, 4, true, NT>::T : Tile<float, 4, false, NT>::T;
+    case 5: return pml ? Tile<float, 5, true, NT>::T : Tile<float, 5, false, NT>::T;
+    default: return 0;
+  }
+}
+
+int group_tile_max(int N, bool pml, int threads) {
+  return threads == 512 ? group_tile_nt<512>(N, pml) : group_tile_nt<256>(N, pml);
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) group_stage_kernel(const GroupParams G) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ StageParams<float> P;
+  __shared__ int start;
+  __shared__ int go;
+  if (threadIdx.x == 0) {
+    int it = 0;
+    while (it + 1 < G.nitems && (int)blockIdx.x >= G.first[it + 1]) ++it;
+    start = it;
+  }
+  for (int k = 0; k < G.nitems; ++k) {
+    __syncthreads();   // start is set; the previous item's body is done with P and go
+    const int it = (start + k) % G.nitems;
+    // one thread decides whether the item still has tiles, so that the whole
+    // block takes the same path through the barriers
+    if (threadIdx.x == 0) {
+      go = *reinterpret_cast<volatile const int*>(G.counter + it) < G.ntiles[it];
+      if (go) P = G.p[it];
+    }
+    __syncthreads();
+    if (!go) continue;
+    int* dyn = G.counter + it;
+#define WADG_GROUP_CASE(NN)                                                               \
+  case NN * 4 + 0: stage_body<float, NN, false, false, false, NT>(P, smem_raw, 0, 1, dyn); break; \
+  case NN * 4 + 1: stage_body<float, NN, true, false, false, NT>(P, smem_raw, 0, 1, dyn); break;  \
+  case NN * 4 + 2: stage_body<float, NN, true, true, false, NT>(P, smem_raw, 0, 1, dyn); break;
+    switch (G.code[it]) {
+      WADG_GROUP_CASE(1)
+      WADG_GROUP_CASE(2)
+      WADG_GROUP_CASE(3)
+      WADG_GROUP_CASE(4)
+      WADG_GROUP_CASE(5)
+      default: break;
+    }
+#undef WADG_GROUP_CASE
+  }
+}
+
+cudaError_t configure_group_kernel() {
+  size_t m256 = 0, m512 = 0;
+  for (int N = 1; N <= 5; ++N)
+    for (int pml = 0; pml < 2; ++pml) {
+      m256 = std::max(m256, group_smem_bytes(N, pml != 0, 0, 256));
+      m512 = std::max(m512, group_smem_bytes(N, pml != 0, 0, 512));
+    }
+  cudaError_t e = cudaFuncSetAttribute(group_stage_kernel<256>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m256);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(group_stage_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)m512);
+}
+
+int group_blocks_per_sm(size_t smem, int threads) {
+  int nb = 0;
+  cudaError_t e = threads == 512
+      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, group_stage_kernel<512>, 512, smem)
+      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, group_stage_kernel<256>, 256, smem);
+  if (e != cudaSuccess || nb < 1) nb = 1;
+  return nb;
+}
+
+cudaError_t launch_group_stage(const GroupParams& G, int nblocks, size_t smem, int threads,
+                               cudaStream_t s) {
+  if (nblocks <= 0) return cudaSuccess;
+  if (threads == 512) group_stage_kernel<512><<<nblocks, 512, smem, s>>>(G);
+  else group_stage_kernel<256><<<nblocks, 256, smem, s>>>(G);
+  return cudaGetLastError();
+}
 
 // ------------------------------------------------------- stored-matrix scheme
 template <typename Real>

@@ -54,6 +54,7 @@ struct StageParams {
   int e_begin;              // first element of this launch's class
   int n_elem;               // elements of this launch's class
   int nb;                   // excitations (set by the launcher)
+  int tile_elems;           // CUDA-core kernels: elements per tile (0: the largest that fits)
   int nsrc;
   const SrcDev* src;
   const Real* src_w;        // [nsrc][Np]: M_k^{-1} l(r_s)
@@ -140,6 +141,27 @@ template <typename Real>
 cudaError_t launch_stored_ops(int N, int K1, int K0, const double* verts, const double* prof,
                               const double* rh, const double* Ph, const double* Vh, int Nh,
                               Real* out, cudaStream_t s);
+// grouped launch (FP32 CUDA-core kernels): item i runs order code[i] / 4 with
+// class code[i] % 4 (0 non-PML, 1 PML, 2 PML with kappa); blocks
+// [first[i], first[i+1]) start on item i, and every block takes tiles from
+// counter[i] (zeroed before the launch) until all ntiles[i] are taken, then
+// moves on to the next item with tiles left
+struct GroupParams {
+  const StageParams<float>* p;   // [nitems], device memory
+  const int* first;              // [nitems + 1], device memory
+  const int* code;               // [nitems], device memory
+  const int* ntiles;             // [nitems], device memory
+  int* counter;                  // [nitems], device memory
+  int nitems;
+};
+cudaError_t configure_group_kernel();
+// dynamic shared memory and largest tile (elements) of one item, blocks per
+// SM, launch; threads per block 256 or 512
+size_t group_smem_bytes(int N, bool pml, int tile, int threads);
+int group_tile_max(int N, bool pml, int threads);
+int group_blocks_per_sm(size_t smem, int threads);
+cudaError_t launch_group_stage(const GroupParams& G, int nblocks, size_t smem, int threads,
+                               cudaStream_t s);
 template <typename Real>
 cudaError_t launch_check_finite(const Real* a, int64_t n, int* flag, cudaStream_t s);
 

@@ -66,6 +66,12 @@ _SIG = {
     "wadg_mesh_info": [_P, _I64, _I64, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
     "wadg_synchronize": [_P],
     "wadg_reference_operator": [C.c_int, C.c_int, _D, C.c_int64, _I64],
+    "wadg_group_create": [C.c_int32, C.POINTER(_P), C.POINTER(_P)],
+    "wadg_group_destroy": [_P],
+    "wadg_group_autotune": [_P, _D, C.c_int32, _D],
+    "wadg_group_info": [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                        C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
+    "wadg_group_run_steps": [_P, C.c_int64, _D, C.POINTER(_D)],
 }
 
 _lib = None
@@ -86,12 +92,14 @@ def load(path: str = LIB_PATH):
         fn.restype = C.c_int
     lib.wadg_last_error.argtypes = [_P]
     lib.wadg_last_error.restype = C.c_char_p
+    lib.wadg_group_last_error.argtypes = [_P]
+    lib.wadg_group_last_error.restype = C.c_char_p
     _lib = lib
     return lib
 
 
 def exported_symbols():
-    return list(_SIG) + ["wadg_last_error"]
+    return list(_SIG) + ["wadg_last_error", "wadg_group_last_error"]
 
 
 def _ptr(a):
@@ -264,3 +272,60 @@ class Solver:
 
     def synchronize(self):
         self._c(self.lib.wadg_synchronize(self.ctx))
+
+
+class Group:
+    """Several FP32 solvers advanced together, one grouped launch per stage
+    (wadg_group_*).  Refers to the solvers: close it before them."""
+
+    def __init__(self, solvers):
+        self.lib = load()
+        self.solvers = list(solvers)
+        self.g = None
+        arr = (_P * len(self.solvers))(*[s.ctx for s in self.solvers])
+        g = _P()
+        st = self.lib.wadg_group_create(len(self.solvers), arr, C.byref(g))
+        if st != WADG_OK:
+            raise WadgError(st, (self.lib.wadg_group_last_error(None) or b"").decode())
+        self.g = g
+
+    def _c(self, st):
+        if st != WADG_OK:
+            msg = self.lib.wadg_group_last_error(self.g)
+            raise WadgError(st, (msg or b"").decode())
+
+    def close(self):
+        if self.g:
+            self.lib.wadg_group_destroy(self.g)
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def autotune(self, dts, reps=20):
+        d = np.ascontiguousarray(dts, np.float64)
+        ms = C.c_double()
+        self._c(self.lib.wadg_group_autotune(self.g, _ptr(d), reps, C.byref(ms)))
+        return ms.value
+
+    def info(self):
+        v = [C.c_int32() for _ in range(5)]
+        self._c(self.lib.wadg_group_info(self.g, *[C.byref(x) for x in v]))
+        return dict(blocks=v[0].value, threads=v[1].value, blocks_per_sm=v[2].value,
+                    tile_divisor=v[3].value, items=v[4].value)
+
+    def run_steps(self, nsteps, dts, record=True):
+        d = np.ascontiguousarray(dts, np.float64)
+        outs = []
+        ptrs = (_D * len(self.solvers))()
+        for i, s in enumerate(self.solvers):
+            o = None
+            if record and getattr(s, "n_probe", 0):
+                o = np.empty((nsteps, s.n_probe, 6, s.n_batch))
+                ptrs[i] = _ptr(o)
+            outs.append(o)
+        self._c(self.lib.wadg_group_run_steps(self.g, nsteps, _ptr(d), ptrs))
+        return outs

@@ -1,0 +1,93 @@
+"""Grouped launches (wadg_group_*): meshes of different size and order, one
+with two excitations, advanced by one launch per Runge-Kutta stage, give each
+member the state and probe records of its own wadg_run_steps (same per-element
+arithmetic; only the tile sizes and the grid differ), before and after the
+autotuner has picked the tile sizes and the grid."""
+import numpy as np
+import pytest
+
+from synthetic import Dipole, PmlProfile, cube_tet_mesh, workload
+
+pytestmark = pytest.mark.gpu
+
+PML = PmlProfile(u0=0.6, L=0.4, sigma_max=15.0, p_sigma=3.0)
+PROBES = [(0.3, 0.2, -0.1), (-0.45, 0.1, 0.35)]
+MEMBERS = [  # (N, n_hex, pml, n_batch)
+    (2, 5, True, 1),
+    (3, 4, True, 2),
+    (4, 3, False, 1),
+    (1, 6, True, 1),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2006_02551_gb300 import build
+    build.build()
+
+
+def make(N, n_hex, pml, nb, prec="fp32"):
+    from paper_2006_02551_gb300 import Solver
+    v, e = cube_tet_mesh(n_hex, 0.15, 10 + N)
+    s = Solver(N, prec, n_batch=nb)
+    s.set_mesh(v, e)
+    if pml:
+        s.set_pml(PML)
+    src = [Dipole(x=(0.05, -0.02, 0.03), dir=(0.0, 0.0, 1.0), t0=0.5, width=0.2, batch=0)]
+    if nb > 1:
+        src.append(Dipole(x=(-0.1, 0.08, 0.0), dir=(1.0, 0.0, 0.0), t0=0.4, width=0.15, batch=1))
+    s.set_sources(src)
+    s.set_probes(PROBES)
+    s.set_state(None, 0.0)
+    return s
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.mark.parametrize("tune", [False, True])
+def test_group_equals_single_runs(tune):
+    from paper_2006_02551_gb300 import Group
+    nsteps = 25
+    singles = [make(*m) for m in MEMBERS]
+    dts = [0.8 * s.stable_dt(1.0) for s in singles]
+    ref = []
+    for s, dt in zip(singles, dts):
+        rec = s.run_steps(nsteps, dt)
+        q, t = s.get_state()
+        ref.append((q, rec, t))
+        s.close()
+    members = [make(*m) for m in MEMBERS]
+    g = Group(members)
+    if tune:
+        g.autotune(dts, reps=10)
+        for s in members:
+            s.set_state(None, 0.0)   # the autotuner leaves the state undefined
+    info = g.info()
+    assert info["items"] == sum(2 if m[2] else 1 for m in MEMBERS)
+    # two calls, so the second starts from the other buffer parity
+    rec1 = g.run_steps(10, dts)
+    rec2 = g.run_steps(nsteps - 10, dts)
+    for i, s in enumerate(members):
+        q, t = s.get_state()
+        qr, recr, tr = ref[i]
+        assert abs(t - tr) < 1e-12
+        assert rel(q, qr) < 1e-6, (i, rel(q, qr))
+        rec = np.concatenate([rec1[i], rec2[i]])
+        assert rel(rec, recr) < 1e-6, (i, rel(rec, recr))
+    g.close()
+    for s in members:
+        s.close()
+
+
+def test_group_rejects_unsupported_members():
+    from paper_2006_02551_gb300 import Group, WadgError
+    a = make(3, 3, True, 1)
+    b = make(3, 3, True, 1, prec="tf32")
+    with pytest.raises(WadgError):
+        Group([a, b])
+    with pytest.raises(WadgError):
+        Group([a, a])
+    a.close()
+    b.close()
