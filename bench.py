@@ -197,6 +197,90 @@ def run_reference(args, w):
     print(json.dumps(line))
 
 
+def mesh_dofs(s):
+    i = s.info()
+    return i["Np"] * 6 * (i["K"] + i["K_pml"]) * s.n_batch
+
+
+def group_vs_sequential(meshes, pml, sh, local, stream, nst):
+    """The meshes [(n_hex, N)] advanced one after the other (run_steps each)
+    and together (one grouped launch per stage, autotuned): DOF-updates/s."""
+    import torch
+    from paper_2006_02551_gb300 import Group, Solver
+    from synthetic import cube_tet_mesh
+    ss = []
+    for n, N in meshes:
+        v, e = cube_tet_mesh(n, 0.2, 100 + n)
+        s = Solver(N, "fp32", device=local, stream=sh)
+        s.set_mesh(v, e)
+        s.set_pml(pml)
+        s.set_state(None, 0.0)
+        ss.append(s)
+    dts = [s.stable_dt(1.0) for s in ss]
+    dofs = sum(mesh_dofs(s) for s in ss)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for s, dt in zip(ss, dts):
+        s.run_steps(2, dt, record=False)
+    ev[0].record(stream)
+    for s, dt in zip(ss, dts):
+        s.run_steps(nst, dt, record=False)
+    ev[1].record(stream)
+    ev[1].synchronize()
+    seq = ev[0].elapsed_time(ev[1]) / nst
+    g = Group(ss)
+    g.autotune(dts, reps=20)
+    for s in ss:
+        s.set_state(None, 0.0)
+    g.run_steps(2, dts, record=False)
+    ev[2].record(stream)
+    g.run_steps(nst, dts, record=False)
+    ev[3].record(stream)
+    ev[3].synchronize()
+    grp = ev[2].elapsed_time(ev[3]) / nst
+    info = g.info()
+    g.close()
+    for s in ss:
+        s.close()
+    return {"meshes": len(meshes), "dofs_per_step": dofs,
+            "sequential": {"ms_per_step": seq, "value": dofs / (seq * 1e-3)},
+            "grouped": {"ms_per_step": grp, "value": dofs / (grp * 1e-3),
+                        "launches_per_step": 5, "autotuned": info}}
+
+
+def batching_runs(sh, local, stream):
+    """The batching form: 64 independent excitations on one 162,000-tet N=3
+    mesh (FP32, one launch per class and stage), and meshes of uneven size and
+    order in one grouped launch per stage against one launch sequence per
+    mesh (FP32)."""
+    import torch
+    from synthetic import workload
+    w = workload("cube30_n3_batch64")
+    s = setup_solver(w, "fp32", sh, local)
+    dt = s.stable_dt(1.0)
+    s.run_steps(1, dt, record=False)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nst = 3
+    e0.record(stream)
+    s.run_steps(nst, dt, record=False)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / nst
+    dofs = mesh_dofs(s)
+    s.close()
+    out = {"excitations": {"workload": describe(w), "precision": "fp32", "ms_per_step": ms,
+                           "value": dofs / (ms * 1e-3), "unit": "DOF-updates/s"}}
+    mixed = [(8 + round(16 * i / 15), 2 + (i % 3)) for i in range(16)]
+    out["mixed_meshes"] = dict(
+        recipe="16 meshes n^3 x 6 tets, n = 8 + round(16 i/15), N = 2 + (i mod 3), jitter 0.2h, "
+               "PML as the benchmark workload, FP32",
+        **group_vs_sequential(mixed, w.pml, sh, local, stream, 20))
+    small = [(4 + (i % 3), 2 + (i % 3)) for i in range(48)]
+    out["small_meshes"] = dict(
+        recipe="48 meshes n^3 x 6 tets, n = 4 + (i mod 3), N = 2 + (i mod 3), FP32",
+        **group_vs_sequential(small, w.pml, sh, local, stream, 20))
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -211,6 +295,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--no-stored", action="store_true",
                     help="skip the stored-matrix scheme comparison run")
+    ap.add_argument("--no-batching", action="store_true",
+                    help="skip the batching-form runs (excitation batch, grouped meshes)")
     ap.add_argument("--ref-hex", type=int, default=4,
                     help="cube size of the oracle sample for --impl reference")
     ap.add_argument("--cpu-hex", type=int, default=12,
@@ -410,6 +496,9 @@ def main():
                                "peak_gbs": hbm, "frac": sb / (kss[1] * 1e-3) / 1e9 / hbm},
             "vs_waa": {"memory_ratio": mems["pml_coeff"] / max(mem["pml_coeff"], 1),
                        "time_ratio_vs_this_run": mss / (ms / args.steps)}}
+
+    if not args.no_batching and rank == 0:
+        out_extra["batching"] = batching_runs(sh, local, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
