@@ -288,7 +288,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cube40_n4")
-    ap.add_argument("--precision", default="tf32", choices=["fp32", "fp64", "tf32"])
+    ap.add_argument("--precision", default="tf32", choices=["fp32", "fp64", "tf32", "bf16"])
     ap.add_argument("--hex", type=int, default=None,
                     help="override the cube size of the workload (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -383,9 +383,10 @@ def main():
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
     achieved = d_flops / (d_ms * 1e-3) / 1e12
     achieved_gbs = d_bytes / (d_ms * 1e-3) / 1e9
-    if args.precision == "tf32":
+    if args.precision in ("tf32", "bf16"):
         # tensor-core contractions: the stage is bound by HBM traffic
-        traffic = tc_pml_traffic(K1 * w.n_batch, N) if dom == "pml" else None
+        traffic = (tc_pml_traffic(K1 * w.n_batch, N)
+                   if dom == "pml" and args.precision == "tf32" else None)
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
                     "frac": achieved_gbs / hbm, "traffic": traffic,
                     "traffic_source": "profiles/tc_stage_kernels_cube24_n4_full.md (scaled by elements)",
@@ -430,8 +431,8 @@ def main():
         q_main, _ = s.get_state()
         s.close()
         others = {}
-        for prec in ("fp64", "fp32"):
-            if prec == args.precision:
+        for prec in ("fp64", "fp32", "bf16"):
+            if prec == args.precision or (prec == "bf16" and N > 4):
                 continue
             so = setup_solver(w, prec, sh, local)
             nrate = 20 if prec == "fp64" else 200
@@ -454,10 +455,11 @@ def main():
             acc = {"fields": "E,H", "steps": nst, "reference": "FP64 path on the GPU",
                    f"l2_rel_{args.precision}_vs_fp64":
                        float(np.linalg.norm(q_main[sel] - q64[sel]) / np.linalg.norm(q64[sel]))}
-            if "fp32" in others:
-                q32 = others["fp32"][1]
-                acc["l2_rel_fp32_vs_fp64"] = float(np.linalg.norm(q32[sel] - q64[sel]) /
-                                                   np.linalg.norm(q64[sel]))
+            for prec in ("fp32", "bf16"):
+                if prec in others:
+                    qo = others[prec][1]
+                    acc[f"l2_rel_{prec}_vs_fp64"] = float(np.linalg.norm(qo[sel] - q64[sel]) /
+                                                          np.linalg.norm(q64[sel]))
             out_extra["accuracy"] = acc
         for prec, (rate, _) in others.items():
             out_extra[prec] = rate
@@ -515,7 +517,8 @@ def main():
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None,
-                "dtype": {"fp32": "f32", "fp64": "f64", "tf32": "tf32 x tf32 -> f32"}[args.precision],
+                "dtype": {"fp32": "f32", "fp64": "f64", "tf32": "tf32 x tf32 -> f32",
+                          "bf16": "bf16 x bf16 -> f32"}[args.precision],
                 "data": "synthetic",
                 "config": {"workload": describe(w), "K": K, "K_pml": K1, "N": N, "Np": Np,
                            "Nq": Nq, "dofs_per_step": dofs, "precision": args.precision,

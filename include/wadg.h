@@ -54,7 +54,10 @@ typedef enum {
 /* Arithmetic of the stage kernels.  FP64: fields, operators and coefficients
  * in double.  FP32: fields, operators, coefficient samples in float; the
  * geometric factors stay double on the device and the source waveform, the
- * coefficient sampling and the objective sums are evaluated in double. */
+ * coefficient sampling and the objective sums are evaluated in double.
+ * TF32 / BF16 (N <= 4, kappa = 1): as FP32, with the reference-operator
+ * contractions (D_r, D_s, D_t, LIFT, V_q, P_q) on the tensor cores, operands
+ * rounded to TF32 or BF16 (nearest) and accumulated in FP32. */
 typedef enum { WADG_FP64 = 0, WADG_FP32 = 1, WADG_TF32 = 2, WADG_BF16 = 3 } wadg_precision;
 
 /* PML implementation.
@@ -66,7 +69,7 @@ typedef enum { WADG_FP64 = 0, WADG_FP32 = 1, WADG_TF32 = 2, WADG_BF16 = 3 } wadg
  *           (M^a)^-1 M_k and M_k^-1 M^{1/kappa} are the identity), built in
  *           double by a Stroud rule with N + 6 points per direction.  The
  *           reference "exact" scheme the WAA approximates; CUDA-core kernels
- *           in every precision (a TF32 context runs its PML class on the FP32
+ *           in every precision (a TF32/BF16 context runs its PML class on the FP32
  *           CUDA-core kernel).  EUNSUPPORTED when kappa_max != 1.
  *   EC      the WAA kernels with element-constant coefficients: every
  *           quadrature node of an element takes the profile's value at the
@@ -140,7 +143,7 @@ wadg_status wadg_set_materials(wadg_ctx* ctx, const double* eps_r, const double*
  * stored per element as sigma_u (and kappa_u when kappa_max != 1); the
  * stored-matrix scheme holds its operators instead (see wadg_pml_scheme).
  * Pass NULL to remove the PML.  EINVAL for an unknown scheme, EUNSUPPORTED
- * for kappa_max != 1 with the stored scheme or with a TF32 context.  Resets
+ * for kappa_max != 1 with the stored scheme or with a TF32/BF16 context.  Resets
  * the state and re-maps sources and probes. */
 wadg_status wadg_set_pml_profile(wadg_ctx* ctx, const wadg_pml_profile* prof,
                                  wadg_pml_scheme scheme);
@@ -196,7 +199,7 @@ wadg_status wadg_profile_stage(wadg_ctx* ctx, int reps, double dt, double* ms_ou
  * On return the state is the forward state after nsteps steps (as after
  * wadg_run_steps).  Outputs (any may be NULL): J_out[n_batch],
  * dJ_deps[n_batch][K] (caller element order), dJ_dsigma_max[n_batch][3],
- * dJ_dp_sigma[n_batch][3].  EUNSUPPORTED for the TF32 precision,
+ * dJ_dp_sigma[n_batch][3].  EUNSUPPORTED for the TF32 and BF16 precisions,
  * kappa_max != 1 or a PML scheme other than WADG_PML_WAA; ESTATE without
  * probes.  Device memory: about
  * (nsteps/ckpt_every + ckpt_every + 12) copies of the state. */

@@ -86,7 +86,8 @@ struct wadg_ctx {
   DevPtr q[2], rq, p, rp, geo, fnrm, mat, nbr, code, sig, kap, ops, tabs, verts;
   DevPtr src, srcw, pr_elem, pr_ell, pr_out, obj, tdev, stepdev, flag, tcops, errflag;
   DevPtr stored;     // stored-matrix scheme: per PML element operators
-  bool tc = false;   // tensor-core stage kernels (TF32)
+  bool tc = false;   // tensor-core stage kernels (TF32 or BF16 operands)
+  bool bf16 = false; // BF16 operands
   int cur = 0;
   int nsrc = 0, nprobe = 0;
   std::vector<wadg_dipole> src_user;
@@ -224,14 +225,18 @@ wadg_status upload_ops(wadg_ctx* ctx) {
   CK(cudaMemcpy(ctx->tabs.p, t.data(), t.size(), cudaMemcpyHostToDevice));
   if (ctx->tc) {
     // row-major Dr | Ds | Dt [Np][Np], LIFT [Np][NF], Vq [Nq][Np], Pq [Np][Nq],
-    // rounded to TF32 (nearest, ties away from zero)
+    // rounded to TF32 (nearest, ties away from zero); a BF16 context rounds
+    // the FP32 values once more on the device
     std::vector<float> tf;
+    const bool bf = ctx->bf16;
     auto push = [&](double v) {
       float f = (float)v;
-      uint32_t u;
-      std::memcpy(&u, &f, 4);
-      u = (u + 0x1000u) & 0xFFFFE000u;
-      std::memcpy(&f, &u, 4);
+      if (!bf) {
+        uint32_t u;
+        std::memcpy(&u, &f, 4);
+        u = (u + 0x1000u) & 0xFFFFE000u;
+        std::memcpy(&f, &u, 4);
+      }
       tf.push_back(f);
     };
     for (const std::vector<double>* D : {&R.Dr, &R.Ds, &R.Dt})
@@ -576,7 +581,7 @@ template <typename Real>
 cudaError_t launch_pml_class(wadg_ctx* ctx, const StageParams<Real>& P) {
   if (ctx->scheme == WADG_PML_STORED) return launch_stage_stored<Real>(ctx->N, P, ctx->nb, ctx->stream);
   if constexpr (std::is_same<Real, float>::value) {
-    if (ctx->tc) return launch_stage_tc(ctx->N, true, P, ctx->nb, ctx->stream);
+    if (ctx->tc) return launch_stage_tc(ctx->N, true, P, ctx->nb, ctx->stream, ctx->bf16);
   }
   return launch_stage<Real>(ctx->N, true, ctx->kappa, P, ctx->nb, ctx->stream);
 }
@@ -585,7 +590,7 @@ template <typename Real>
 wadg_status issue_stage(wadg_ctx* ctx, int stage, double dt, double t, bool use_tdev) {
   if (ctx->tc) {
     StageParams<float> A = stage_params<float>(ctx, stage, dt, t, use_tdev, false);
-    CK(launch_stage_tc(ctx->N, false, A, ctx->nb, ctx->stream));
+    CK(launch_stage_tc(ctx->N, false, A, ctx->nb, ctx->stream, ctx->bf16));
     if (ctx->K1 > 0) {
       StageParams<float> B = stage_params<float>(ctx, stage, dt, t, use_tdev, true);
       CK(launch_pml_class<float>(ctx, B));
@@ -733,13 +738,10 @@ wadg_status wadg_create(int N, wadg_precision prec, int32_t n_batch, int device,
   if (!out) return fail(nullptr, WADG_EINVAL, "out is NULL");
   *out = nullptr;
   if (N < 1 || N > 5) return fail(nullptr, WADG_EINVAL, "N must be in 1..5 (got %d)", N);
-  if (prec != WADG_FP64 && prec != WADG_FP32 && prec != WADG_TF32) {
-    if (prec == WADG_BF16)
-      return fail(nullptr, WADG_EUNSUPPORTED, "precision %d not available in this build", prec);
+  if (prec != WADG_FP64 && prec != WADG_FP32 && prec != WADG_TF32 && prec != WADG_BF16)
     return fail(nullptr, WADG_EINVAL, "unknown precision %d", prec);
-  }
-  if (prec == WADG_TF32 && !tc_supported(N, false))
-    return fail(nullptr, WADG_EUNSUPPORTED, "TF32 tensor-core stage is built for N <= 4");
+  if ((prec == WADG_TF32 || prec == WADG_BF16) && !tc_supported(N, false))
+    return fail(nullptr, WADG_EUNSUPPORTED, "the tensor-core stage is built for N <= 4");
   if (n_batch < 1) return fail(nullptr, WADG_EINVAL, "n_batch must be >= 1");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
@@ -752,7 +754,8 @@ wadg_status wadg_create(int N, wadg_precision prec, int32_t n_batch, int device,
   ctx->nb = n_batch;
   ctx->device = device;
   ctx->rs = prec == WADG_FP64 ? 8 : 4;
-  ctx->tc = prec == WADG_TF32;
+  ctx->tc = prec == WADG_TF32 || prec == WADG_BF16;
+  ctx->bf16 = prec == WADG_BF16;
   const char* e = nullptr;
   if (!build_ref_ops(N, ctx->ref, &e)) {
     delete ctx;
@@ -771,7 +774,7 @@ wadg_status wadg_create(int N, wadg_precision prec, int32_t n_batch, int device,
   if (s == WADG_OK) {
     cudaError_t ce = ctx->rs == 8 ? configure_stage_kernels<double>(N)
                                   : configure_stage_kernels<float>(N);
-    if (ce == cudaSuccess && ctx->tc) ce = configure_tc_kernels(N);
+    if (ce == cudaSuccess && ctx->tc) ce = configure_tc_kernels(N, ctx->bf16);
     if (ce == cudaSuccess)
       ce = ctx->rs == 8 ? configure_stored_kernels<double>(N) : configure_stored_kernels<float>(N);
     if (ce == cudaSuccess && !ctx->tc)
@@ -975,7 +978,7 @@ wadg_status wadg_set_pml_profile(wadg_ctx* ctx, const wadg_pml_profile* prof,
     for (int u = 0; u < 3; ++u)
       if (prof->kappa_max[u] != 1.0) kap = true;
     if (kap && ctx->tc && scheme != WADG_PML_STORED)
-      return fail(ctx, WADG_EUNSUPPORTED, "kappa_max != 1 is not built for the TF32 stage");
+      return fail(ctx, WADG_EUNSUPPORTED, "kappa_max != 1 is not built for the tensor-core stage");
     if (kap && scheme == WADG_PML_STORED)
       return fail(ctx, WADG_EUNSUPPORTED, "the stored-matrix scheme is built for kappa = 1");
     ctx->has_prof = true;
@@ -1114,7 +1117,7 @@ wadg_status wadg_profile_stage(wadg_ctx* ctx, int reps, double dt, double* ms_ou
       } else {
         StageParams<float> P = stage_params<float>(ctx, stage, dt, ctx->t, false, cls == 1);
         if (cls == 1) CK(launch_pml_class<float>(ctx, P));
-        else if (ctx->tc) CK(launch_stage_tc(ctx->N, false, P, ctx->nb, ctx->stream));
+        else if (ctx->tc) CK(launch_stage_tc(ctx->N, false, P, ctx->nb, ctx->stream, ctx->bf16));
         else CK(launch_stage<float>(ctx->N, false, false, P, ctx->nb, ctx->stream));
       }
       CK(cudaEventRecord(ev[2 * cls + 1], ctx->stream));
@@ -1454,7 +1457,7 @@ wadg_status noalloc_stage(wadg_ctx* ctx, int stage, double dt, const double* tde
   if (ctx->tc) {
     StageParams<float> A = stage_params<float>(ctx, stage, dt, 0.0, false, false);
     A.t_dev = tdev;
-    CK(launch_stage_tc(ctx->N, false, A, ctx->nb, ctx->stream));
+    CK(launch_stage_tc(ctx->N, false, A, ctx->nb, ctx->stream, ctx->bf16));
     if (ctx->K1 > 0) {
       StageParams<float> B = stage_params<float>(ctx, stage, dt, 0.0, false, true);
       B.t_dev = tdev;

@@ -120,10 +120,11 @@ cudaError_t launch_adjoint_stage(int N, const AdjParams<Real>& P, int nb, cudaSt
 template <typename Real>
 cudaError_t launch_adjoint_probes(const Real* q, int64_t strideQ, int nprobe, int nb, int Np,
                                   const int* elem, const double* ell, Real* lam, cudaStream_t s);
-// tensor-core (tcgen05, TF32) stage kernels
+// tensor-core (tcgen05) stage kernels: TF32 operands, or BF16 operands (bf16)
 bool tc_supported(int N, bool kappa);
-cudaError_t configure_tc_kernels(int N);
-cudaError_t launch_stage_tc(int N, bool pml, const StageParams<float>& P, int nb, cudaStream_t s);
+cudaError_t configure_tc_kernels(int N, bool bf16);
+cudaError_t launch_stage_tc(int N, bool pml, const StageParams<float>& P, int nb, cudaStream_t s,
+                            bool bf16);
 cudaError_t launch_advance(double* t_dev, int64_t* step_dev, double dt, cudaStream_t s);
 template <typename Real>
 cudaError_t launch_pml_samples(int Nq, int K1, int K0, const double* verts,

@@ -1,4 +1,4 @@
-// Tensor-core stage kernels for sm_103a (tcgen05, TF32 operands, FP32
+// Tensor-core stage kernels for sm_103a (tcgen05, TF32 or BF16 operands, FP32
 // accumulation in tensor memory, FP32 field state).
 //
 // Every reference-element contraction of the stage is one matrix product
@@ -23,6 +23,8 @@
 // Waits on the MMA-completion mbarrier are bounded; on timeout the kernel
 // records an error and stops after releasing its tensor memory.
 #include "kernels.cuh"
+
+#include <cuda_bf16.h>
 
 #include <algorithm>
 #include <cstdint>
@@ -49,6 +51,21 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t addr, uint32_t lbo, uint3
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
          (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+// instruction descriptor, kind::f16 with BF16 A and B: D f32, both K-major
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
 }
 
 __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
@@ -188,6 +205,15 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
+// operand element: TF32 held in 32 bits (4 per 16-byte core-matrix row, 8 K
+// per instruction) or BF16 (8 per core-matrix row, 16 K per instruction)
+template <bool BF>
+struct OpT {
+  static constexpr int ES = BF ? 2 : 4;    // bytes
+  static constexpr int CW = 16 / ES;       // K per core-matrix row
+  static constexpr int KS = 2 * CW;        // K per instruction
+};
+
 __device__ __forceinline__ float to_tf32(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -198,33 +224,47 @@ __device__ __forceinline__ float to_tf32(float x) {
 // matrices, K-adjacent core matrices lbo bytes apart, 8-row groups sbo apart.
 // The field operands use lbo = 144 (one 16-byte gap per core matrix) so that
 // consecutive K written by consecutive lanes fall on distinct banks.
+template <bool BF>
 __host__ __device__ constexpr uint32_t cofs(int r, int k, uint32_t sbo, uint32_t lbo) {
-  return static_cast<uint32_t>(r >> 3) * sbo + static_cast<uint32_t>(k >> 2) * lbo +
-         static_cast<uint32_t>(r & 7) * 16u + static_cast<uint32_t>(k & 3) * 4u;
+  using O = OpT<BF>;
+  return static_cast<uint32_t>(r >> 3) * sbo + static_cast<uint32_t>(k / O::CW) * lbo +
+         static_cast<uint32_t>(r & 7) * 16u + static_cast<uint32_t>(k % O::CW) * O::ES;
+}
+
+// one operand value, rounded to nearest in the operand type
+template <bool BF>
+__device__ __forceinline__ void put_op(unsigned char* p, float x) {
+  if constexpr (BF) *reinterpret_cast<__nv_bfloat16*>(p) = __float2bfloat16_rn(x);
+  else *reinterpret_cast<float*>(p) = to_tf32(x);
 }
 
 constexpr int rup8(int x) { return (x + 7) & ~7; }
 constexpr int rup16(int x) { return (x + 15) & ~15; }
 
 // Shared-memory plan of one tile (all offsets in bytes).
-template <int N, bool PML>
+template <int N, bool PML, bool BF = false>
 struct Plan {
+  using O = OpT<BF>;
   static constexpr int Np = (N + 1) * (N + 2) * (N + 3) / 6;
   static constexpr int Nfp = (N + 1) * (N + 2) / 2;
   static constexpr int NF = 4 * Nfp;
   static constexpr int Nq = (N + 1) * (N + 1) * (N + 1);
-  static constexpr int NpK = rup8(Np), NFK = rup8(NF), NqK = rup8(Nq);
+  __host__ __device__ static constexpr int rupK(int x) { return (x + O::KS - 1) / O::KS * O::KS; }
+  static constexpr int NpK = rupK(Np), NFK = rupK(NF), NqK = rupK(Nq);
   static constexpr int T = 8;                        // elements per tile
   static constexpr int NV = rup16(6 * T);            // columns of E,H products
   static constexpr int NQ = rup16(12 * T);           // columns of 12-component products
   static constexpr int G_p = NpK / 8;                // 8-row groups of an Np-row operator
   static constexpr uint32_t LA = 128, LB = 144;      // K strides of operator / field tiles
-  static constexpr uint32_t SBO_V = (NpK / 4) * LA;  // operators, K = Np
-  static constexpr uint32_t SBO_L = (NFK / 4) * LA;  // K = 4 Nfp
-  static constexpr uint32_t SBO_Q = (NqK / 4) * LA;  // K = Nq
-  static constexpr uint32_t SBB_V = (NpK / 4) * LB;  // field tiles
-  static constexpr uint32_t SBB_L = (NFK / 4) * LB;
-  static constexpr uint32_t SBB_Q = (NqK / 4) * LB;
+  static constexpr uint32_t SBO_V = (NpK / O::CW) * LA;  // operators, K = Np
+  static constexpr uint32_t SBO_L = (NFK / O::CW) * LA;  // K = 4 Nfp
+  static constexpr uint32_t SBO_Q = (NqK / O::CW) * LA;  // K = Nq
+  static constexpr uint32_t SBB_V = (NpK / O::CW) * LB;  // field tiles
+  static constexpr uint32_t SBB_L = (NFK / O::CW) * LB;
+  static constexpr uint32_t SBB_Q = (NqK / O::CW) * LB;
+  __host__ __device__ static constexpr uint32_t ofs(int r, int k, uint32_t sbo, uint32_t lbo) {
+    return cofs<BF>(r, k, sbo, lbo);
+  }
   // A operands
   static constexpr uint32_t oPq = 0;
   static constexpr uint32_t oL = PML ? oPq + G_p * SBO_Q : 0;
@@ -254,11 +294,14 @@ struct Plan {
   // P_q columns to the (t, z) buffer (free once P_q is done).
   static constexpr uint32_t DV_BYTES = T * 24 * Np * 4;
   static constexpr uint32_t DP_BYTES = T * 12 * Np * 4;
-  static constexpr uint32_t oDV = PML ? oBF : oMisc + MISC_BYTES;
+  // (BF16 operand buffers are too small for the volume/LIFT dump: it gets its
+  // own region)
+  static constexpr bool DV_ALIAS = PML && !BF;
+  static constexpr uint32_t oDV = DV_ALIAS ? oBF : oMisc + MISC_BYTES;
   static constexpr uint32_t oDP = oBTZ;
-  static_assert(!PML || oDV + DV_BYTES <= oBTZ, "volume/LIFT dump");
+  static_assert(!DV_ALIAS || oDV + DV_BYTES <= oBTZ, "volume/LIFT dump");
   static_assert(!PML || oDP + DP_BYTES <= oRS, "P_q dump");
-  static constexpr uint32_t bytes_used = PML ? oMisc + MISC_BYTES : oDV + DV_BYTES;
+  static constexpr uint32_t bytes_used = DV_ALIAS ? oMisc + MISC_BYTES : oDV + DV_BYTES;
   // residency follows the tensor-memory budget of 512 columns per SM: one PML
   // block (512 columns) per SM, enforced by the shared-memory request so that
   // no block waits in tcgen05.alloc; non-PML blocks (128 columns) are limited
@@ -295,9 +338,9 @@ struct TcWarps {
   static constexpr int threads = 32 * (compute + 1);
 };
 
-template <int N, bool PML>
+template <int N, bool PML, bool BF>
 __global__ void __launch_bounds__(TcWarps<PML>::threads, PML ? 1 : 2) tc_stage_kernel(const StageParams<float> P) {
-  using PL = Plan<N, PML>;
+  using PL = Plan<N, PML, BF>;
   constexpr int NW = TcWarps<PML>::compute;
   constexpr int kTcThreads = 32 * NW;          // compute threads
   constexpr int kAll = TcWarps<PML>::threads;
@@ -335,20 +378,20 @@ __global__ void __launch_bounds__(TcWarps<PML>::threads, PML ? 1 : 2) tc_stage_k
     const float* gPq = gVq + Nq * Np;
     for (int idx = tid; idx < 3 * Np * Np; idx += kAll) {
       const int row = idx / Np, j = idx - row * Np;   // row d Np + i of [Dr; Ds; Dt]
-      *reinterpret_cast<float*>(smem + PL::oVol + cofs(row, j, PL::SBO_V, PL::LA)) = gDr[idx];
+      put_op<BF>(smem + PL::oVol + PL::ofs(row, j, PL::SBO_V, PL::LA), gDr[idx]);
     }
     for (int idx = tid; idx < Np * NF; idx += kAll) {
       const int i = idx / NF, f = idx - i * NF;
-      *reinterpret_cast<float*>(smem + PL::oL + cofs(i, f, PL::SBO_L, PL::LA)) = gL[idx];
+      put_op<BF>(smem + PL::oL + PL::ofs(i, f, PL::SBO_L, PL::LA), gL[idx]);
     }
     if (PML) {
       for (int idx = tid; idx < Nq * Np; idx += kAll) {
         const int q = idx / Np, j = idx - q * Np;
-        *reinterpret_cast<float*>(smem + PL::oVq + cofs(q, j, PL::SBO_V, PL::LA)) = gVq[idx];
+        put_op<BF>(smem + PL::oVq + PL::ofs(q, j, PL::SBO_V, PL::LA), gVq[idx]);
       }
       for (int idx = tid; idx < Np * Nq; idx += kAll) {
         const int i = idx / Nq, q = idx - i * Nq;
-        *reinterpret_cast<float*>(smem + PL::oPq + cofs(i, q, PL::SBO_Q, PL::LA)) = gPq[idx];
+        put_op<BF>(smem + PL::oPq + PL::ofs(i, q, PL::SBO_Q, PL::LA), gPq[idx]);
       }
     }
   }
@@ -527,29 +570,34 @@ __global__ void __launch_bounds__(TcWarps<PML>::threads, PML ? 1 : 2) tc_stage_k
         fence_after();
         return ok;
       };
-      constexpr uint32_t idV = idesc_tf32(128, PL::NV);
-      constexpr uint32_t idQ = idesc_tf32(128, PL::NQ);
+      constexpr uint32_t idV = BF ? idesc_bf16(128, PL::NV) : idesc_tf32(128, PL::NV);
+      constexpr uint32_t idQ = BF ? idesc_bf16(128, PL::NQ) : idesc_tf32(128, PL::NQ);
+      constexpr int KS = PL::O::KS;
+      auto mma = [](uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+        if constexpr (BF) mma_bf16(d, a, b, id, acc);
+        else mma_tf32(d, a, b, id, acc);
+      };
       for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         if (!wait_ready(0)) { mfail = true; break; }
         if (PML) {   // V_q first: the quadrature epilogue waits for it alone
-          for (int k = 0; k < NpK / 8; ++k)
-            mma_tf32(tmem + PL::cVq, make_desc(sbase + PL::oVq + 256 * k, 128, PL::SBO_V),
+          for (int k = 0; k < NpK / KS; ++k)
+            mma(tmem + PL::cVq, make_desc(sbase + PL::oVq + 256 * k, 128, PL::SBO_V),
                      make_desc(sbase + PL::oBF + 2 * PL::LB * k, PL::LB, PL::SBB_V), idQ, k > 0);
           mma_commit(saddr(mbar + 0));
         }
-        for (int k = 0; k < NpK / 8; ++k)
-          mma_tf32(tmem + PL::cV, make_desc(sbase + PL::oVol + 256 * k, 128, PL::SBO_V),
+        for (int k = 0; k < NpK / KS; ++k)
+          mma(tmem + PL::cV, make_desc(sbase + PL::oVol + 256 * k, 128, PL::SBO_V),
                    make_desc(sbase + PL::oBF + 2 * PL::LB * k, PL::LB, PL::SBB_V), idV, k > 0);
         issued = true;
         if (!wait_ready(1)) { mfail = true; break; }
-        for (int k = 0; k < NFK / 8; ++k)
-          mma_tf32(tmem + PL::cL, make_desc(sbase + PL::oL + 256 * k, 128, PL::SBO_L),
+        for (int k = 0; k < NFK / KS; ++k)
+          mma(tmem + PL::cL, make_desc(sbase + PL::oL + 256 * k, 128, PL::SBO_L),
                    make_desc(sbase + PL::oBFL + 2 * PL::LB * k, PL::LB, PL::SBB_L), idV, k > 0);
         mma_commit(saddr(mbar + 1));
         if (PML) {
           if (!wait_ready(2)) { mfail = true; break; }
-          for (int k = 0; k < NqK / 8; ++k)
-            mma_tf32(tmem + PL::cPq, make_desc(sbase + PL::oPq + 256 * k, 128, PL::SBO_Q),
+          for (int k = 0; k < NqK / KS; ++k)
+            mma(tmem + PL::cPq, make_desc(sbase + PL::oPq + 256 * k, 128, PL::SBO_Q),
                      make_desc(sbase + PL::oBTZ + 2 * PL::LB * k, PL::LB, PL::SBB_Q), idQ, k > 0);
           mma_commit(saddr(mbar + 2));
         }
@@ -619,19 +667,33 @@ __global__ void __launch_bounds__(TcWarps<PML>::threads, PML ? 1 : 2) tc_stage_k
     // blocks: one 16-byte core-matrix row (4 consecutive nodes of one
     // (element, component) row) per task; rows of missing elements are skipped
     {
-      constexpr int G4 = (Np + 3) / 4;
+      constexpr int CW = PL::O::CW;
+      constexpr int G4 = (Np + CW - 1) / CW;
       constexpr int NTASK = PL::ROWS_F * G4;
       for (int task = tid; task < NTASK; task += kTcThreads) {
         const int row = task / G4, g = task - row * G4;
         const int rr = PML && row >= 6 * T ? row - 6 * T : row;
         if (rr >= ne * 6) continue;
-        const float* src = (PML && row >= 6 * T ? SP : SQ) + rr * Np + 4 * g;
-        float4 v;
-        v.x = to_tf32(src[0]);
-        v.y = 4 * g + 1 < Np ? to_tf32(src[1]) : 0.f;
-        v.z = 4 * g + 2 < Np ? to_tf32(src[2]) : 0.f;
-        v.w = 4 * g + 3 < Np ? to_tf32(src[3]) : 0.f;
-        *reinterpret_cast<float4*>(smem + PL::oBF + cofs(row, 4 * g, PL::SBB_V, PL::LB)) = v;
+        const float* src = (PML && row >= 6 * T ? SP : SQ) + rr * Np + CW * g;
+        unsigned char* dst = smem + PL::oBF + PL::ofs(row, CW * g, PL::SBB_V, PL::LB);
+        if constexpr (BF) {
+          uint32_t w[4];
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            const float a = CW * g + 2 * h < Np ? src[2 * h] : 0.f;
+            const float b = CW * g + 2 * h + 1 < Np ? src[2 * h + 1] : 0.f;
+            const __nv_bfloat162 v2 = __floats2bfloat162_rn(a, b);
+            w[h] = *reinterpret_cast<const uint32_t*>(&v2);
+          }
+          *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+        } else {
+          float4 v;
+          v.x = to_tf32(src[0]);
+          v.y = CW * g + 1 < Np ? to_tf32(src[1]) : 0.f;
+          v.z = CW * g + 2 < Np ? to_tf32(src[2]) : 0.f;
+          v.w = CW * g + 3 < Np ? to_tf32(src[3]) : 0.f;
+          *reinterpret_cast<float4*>(dst) = v;
+        }
       }
     }
     // ---- the volume and V_q products need only the field operand
@@ -678,8 +740,7 @@ __global__ void __launch_bounds__(TcWarps<PML>::threads, PML ? 1 : 2) tc_stage_k
       fo[5] = sE * (YP * cEz + al * (nz * ndH - dHz));
 #pragma unroll
       for (int c = 0; c < 6; ++c)
-        *reinterpret_cast<float*>(smem + PL::oBFL + cofs(e * 6 + c, fm, PL::SBB_L, PL::LB)) =
-            to_tf32(fo[c]);
+        put_op<BF>(smem + PL::oBFL + PL::ofs(e * 6 + c, fm, PL::SBB_L, PL::LB), fo[c]);
     }
     signal_ready(4);   // LIFT operand
     if (next < ntiles) {
@@ -716,10 +777,8 @@ __global__ void __launch_bounds__(TcWarps<PML>::threads, PML ? 1 : 2) tc_stage_k
           }
 #pragma unroll
           for (int c = 0; c < 6; ++c) {
-            *reinterpret_cast<float*>(smem + PL::oBTZ + cofs(e * 6 + c, q, PL::SBB_Q, PL::LB)) =
-                to_tf32(o[c]);
-            *reinterpret_cast<float*>(smem + PL::oBTZ + cofs(6 * T + e * 6 + c, q, PL::SBB_Q, PL::LB)) =
-                to_tf32(o[6 + c]);
+            put_op<BF>(smem + PL::oBTZ + PL::ofs(e * 6 + c, q, PL::SBB_Q, PL::LB), o[c]);
+            put_op<BF>(smem + PL::oBTZ + PL::ofs(6 * T + e * 6 + c, q, PL::SBB_Q, PL::LB), o[6 + c]);
           }
         }
       }
@@ -872,15 +931,16 @@ __global__ void __launch_bounds__(TcWarps<PML>::threads, PML ? 1 : 2) tc_stage_k
   if (warp == 0) tmem_dealloc(tmem, PL::TMEM_COLS);
 }
 
-template <int N, bool PML>
+template <int N, bool PML, bool BF>
 cudaError_t configure_n() {
-  return cudaFuncSetAttribute(tc_stage_kernel<N, PML>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)Plan<N, PML>::bytes);
+  return cudaFuncSetAttribute(tc_stage_kernel<N, PML, BF>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)Plan<N, PML, BF>::bytes);
 }
 
-template <int N, bool PML>
+template <int N, bool PML, bool BF>
 cudaError_t launch_n(const StageParams<float>& P, int nb, cudaStream_t s) {
-  using PL = Plan<N, PML>;
+  using PL = Plan<N, PML, BF>;
   if (P.n_elem <= 0) return cudaSuccess;
   static int sms = 0;
   if (sms == 0) {
@@ -894,7 +954,7 @@ cudaError_t launch_n(const StageParams<float>& P, int nb, cudaStream_t s) {
   const long long tiles = (long long)((P.n_elem + PL::T - 1) / PL::T) * nb;
   const int per_sm = 512 / (int)PL::TMEM_COLS;
   const int grid = (int)std::min<long long>(tiles, (long long)per_sm * sms);
-  tc_stage_kernel<N, PML><<<grid, TcWarps<PML>::threads, PL::bytes, s>>>(Q);
+  tc_stage_kernel<N, PML, BF><<<grid, TcWarps<PML>::threads, PL::bytes, s>>>(Q);
   return cudaGetLastError();
 }
 
@@ -902,26 +962,37 @@ cudaError_t launch_n(const StageParams<float>& P, int nb, cudaStream_t s) {
 
 bool tc_supported(int N, bool kappa) { return N >= 1 && N <= 4 && !kappa; }
 
-cudaError_t configure_tc_kernels(int N) {
+template <bool BF>
+cudaError_t configure_tc_bf(int N) {
   cudaError_t e = cudaErrorInvalidValue;
   switch (N) {
-    case 1: e = tc::configure_n<1, false>(); if (e == cudaSuccess) e = tc::configure_n<1, true>(); break;
-    case 2: e = tc::configure_n<2, false>(); if (e == cudaSuccess) e = tc::configure_n<2, true>(); break;
-    case 3: e = tc::configure_n<3, false>(); if (e == cudaSuccess) e = tc::configure_n<3, true>(); break;
-    case 4: e = tc::configure_n<4, false>(); if (e == cudaSuccess) e = tc::configure_n<4, true>(); break;
+    case 1: e = tc::configure_n<1, false, BF>(); if (e == cudaSuccess) e = tc::configure_n<1, true, BF>(); break;
+    case 2: e = tc::configure_n<2, false, BF>(); if (e == cudaSuccess) e = tc::configure_n<2, true, BF>(); break;
+    case 3: e = tc::configure_n<3, false, BF>(); if (e == cudaSuccess) e = tc::configure_n<3, true, BF>(); break;
+    case 4: e = tc::configure_n<4, false, BF>(); if (e == cudaSuccess) e = tc::configure_n<4, true, BF>(); break;
     default: break;
   }
   return e;
 }
 
-cudaError_t launch_stage_tc(int N, bool pml, const StageParams<float>& P, int nb, cudaStream_t s) {
+cudaError_t configure_tc_kernels(int N, bool bf16) {
+  return bf16 ? configure_tc_bf<true>(N) : configure_tc_bf<false>(N);
+}
+
+template <bool BF>
+cudaError_t launch_tc_bf(int N, bool pml, const StageParams<float>& P, int nb, cudaStream_t s) {
   switch (N) {
-    case 1: return pml ? tc::launch_n<1, true>(P, nb, s) : tc::launch_n<1, false>(P, nb, s);
-    case 2: return pml ? tc::launch_n<2, true>(P, nb, s) : tc::launch_n<2, false>(P, nb, s);
-    case 3: return pml ? tc::launch_n<3, true>(P, nb, s) : tc::launch_n<3, false>(P, nb, s);
-    case 4: return pml ? tc::launch_n<4, true>(P, nb, s) : tc::launch_n<4, false>(P, nb, s);
+    case 1: return pml ? tc::launch_n<1, true, BF>(P, nb, s) : tc::launch_n<1, false, BF>(P, nb, s);
+    case 2: return pml ? tc::launch_n<2, true, BF>(P, nb, s) : tc::launch_n<2, false, BF>(P, nb, s);
+    case 3: return pml ? tc::launch_n<3, true, BF>(P, nb, s) : tc::launch_n<3, false, BF>(P, nb, s);
+    case 4: return pml ? tc::launch_n<4, true, BF>(P, nb, s) : tc::launch_n<4, false, BF>(P, nb, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_stage_tc(int N, bool pml, const StageParams<float>& P, int nb, cudaStream_t s,
+                            bool bf16) {
+  return bf16 ? launch_tc_bf<true>(N, pml, P, nb, s) : launch_tc_bf<false>(N, pml, P, nb, s);
 }
 
 }  // namespace wadg

@@ -1,0 +1,78 @@
+"""GPU parity of the tensor-core stage path with BF16 operands (tcgen05
+kind::f16, FP32 accumulation and state) against the FP64 oracle.
+
+BF16 keeps 8 significant bits (relative rounding 2^-9 ~ 2e-3 per operand),
+four times coarser than TF32, so the right-hand side carries errors of a few
+1e-3 of its size.  One-stage cases compare the state increment with a bound of
+3e-2 relative to the oracle's increment; the whole run states its relative L2
+error and bounds it by 5e-2."""
+import numpy as np
+import pytest
+
+from oracle import lserk
+from synthetic import Dipole, PmlProfile, workload
+from tests.parity_util import make_pair, random_states, rel_err, to_lib
+
+pytestmark = pytest.mark.gpu
+
+PML3 = PmlProfile(u0=0.75, L=0.25, sigma_max=20.0, p_sigma=3.0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2006_02551_gb300 import build
+    build.build()
+
+
+def increment_error(N, prof, n_hex=4, stage=0, sources=(), n_batch=1, seed=0):
+    s, sim, mask = make_pair(N, n_hex, 0.15, seed, prof, "bf16", sources=sources,
+                             n_batch=n_batch)
+    st = random_states(sim.K, sim.Np, n_batch, 300 + seed, mask)
+    q0 = to_lib(st)
+    s.set_state(q0, 0.0)
+    dt, t = 0.01, 0.37
+    s.rk_stage(stage, t, dt)
+    q, _ = s.get_state()
+    for b in range(n_batch):
+        rhs = sim.rhs(st[b], t + lserk.RK_C[stage] * dt, b)
+        for f in st[b]:
+            st[b][f] = st[b][f] + lserk.RK_B[stage] * dt * rhs[f]
+    ref = to_lib(st)
+    sel = np.ones(ref.shape[:3], bool)
+    sel[:, ~mask, 6:] = False
+    err = np.linalg.norm((q - ref)[sel]) / np.linalg.norm((ref - q0)[sel])
+    s.close()
+    return err
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_bf16_one_stage_with_pml(N):
+    err = increment_error(N, PML3)
+    print(f"BF16 N={N} increment error {err:.3e}")
+    assert err < 3e-2, err
+
+
+def test_bf16_one_stage_without_pml_and_batched():
+    err = increment_error(4, None, n_hex=3, stage=2)
+    assert err < 3e-2, err
+    srcs = tuple(Dipole(x=(0.1 * b, -0.05 * b, 0.02), t0=0.4, width=0.25, batch=b)
+                 for b in range(3))
+    err = increment_error(3, PML3, n_hex=3, sources=srcs, stage=1, n_batch=3)
+    assert err < 3e-2, err
+
+
+def test_bf16_small_workload_full_run():
+    w = workload("cube4_n3")
+    s, sim, mask = make_pair(w.N, w.n_hex, w.jitter, w.mesh_seed, w.pml, "bf16",
+                             sources=w.sources, probes=w.probes)
+    dt = sim.stable_dt(1.0)
+    s.set_state(None, 0.0)
+    rec = s.run_steps(w.steps, dt)
+    q, _ = s.get_state()
+    st = sim.zero_state()
+    st, _, rec_ref, _ = sim.run(st, w.steps, dt)
+    err = rel_err(q, st, mask)
+    perr = np.linalg.norm(rec - rec_ref) / np.linalg.norm(rec_ref)
+    print(f"BF16 cube4_n3 200 steps: state rel L2 {err:.3e}, probes {perr:.3e}")
+    assert err < 5e-2 and perr < 5e-2, (err, perr)
+    s.close()
