@@ -251,7 +251,10 @@ struct Plan {
   static constexpr int Nq = (N + 1) * (N + 1) * (N + 1);
   __host__ __device__ static constexpr int rupK(int x) { return (x + O::KS - 1) / O::KS * O::KS; }
   static constexpr int NpK = rupK(Np), NFK = rupK(NF), NqK = rupK(Nq);
-  static constexpr int T = 8;                        // elements per tile
+  // elements per tile: 8; 4 for BF16 PML tiles, whose smaller operands then
+  // let two blocks share an SM
+  static constexpr bool PAIR = PML && BF;
+  static constexpr int T = PAIR ? 4 : 8;
   static constexpr int NV = rup16(6 * T);            // columns of E,H products
   static constexpr int NQ = rup16(12 * T);           // columns of 12-component products
   static constexpr int G_p = NpK / 8;                // 8-row groups of an Np-row operator
@@ -302,17 +305,18 @@ struct Plan {
   static_assert(!DV_ALIAS || oDV + DV_BYTES <= oBTZ, "volume/LIFT dump");
   static_assert(!PML || oDP + DP_BYTES <= oRS, "P_q dump");
   static constexpr uint32_t bytes_used = DV_ALIAS ? oMisc + MISC_BYTES : oDV + DV_BYTES;
-  // residency follows the tensor-memory budget of 512 columns per SM: one PML
-  // block (512 columns) per SM, enforced by the shared-memory request so that
-  // no block waits in tcgen05.alloc; non-PML blocks (128 columns) are limited
-  // to two per SM by their shared memory and registers
-  static constexpr uint32_t min_bytes = PML ? 116 * 1024 : 100 * 1024;
+  // residency follows the tensor-memory budget of 512 columns per SM: one
+  // TF32 PML block (512 columns) per SM, enforced by the shared-memory request
+  // so that no block waits in tcgen05.alloc; BF16 PML blocks (256 columns)
+  // and non-PML blocks (128 columns) two per SM (shared memory, registers)
+  static constexpr uint32_t min_bytes = PML && !PAIR ? 116 * 1024 : 100 * 1024;
   static constexpr uint32_t bytes = bytes_used < min_bytes ? min_bytes : bytes_used;
-  static constexpr uint32_t TMEM_COLS = PML ? 512 : 128;
+  static constexpr uint32_t TMEM_COLS = PML ? (PAIR ? 256 : 512) : 128;
   // TMEM column bases: stacked derivatives (lanes d Np + i), LIFT, V_q, P_q
   static constexpr uint32_t cV = 0, cL = NV;
   static constexpr uint32_t cVq = 2 * NV, cPq = 2 * NV + NQ;
-  static_assert(!PML || 2 * NV + 2 * NQ <= 512, "TMEM columns");
+  static_assert(!PML || 2 * NV + 2 * NQ <= TMEM_COLS, "TMEM columns");
+  static_assert(!PAIR || bytes <= 113 * 1024, "two BF16 PML blocks per SM");
   static_assert(PML || 2 * NV <= 128, "TMEM columns");
   static_assert(3 * Np <= 128, "stacked derivative operators fit one M=128 tile");
   static_assert(Nq <= 128 || !PML, "V_q rows must fit one M=128 tile");
@@ -324,26 +328,28 @@ struct Plan {
   static_assert(bytes <= 227 * 1024, "shared memory");
 };
 
-// Warp roles.  The compute warps (16 in a PML block, one block per SM; 8 in a
-// non-PML block, two per SM) stage the tile, build the operands, compute the
+// Warp roles.  The compute warps (16 in a TF32 PML block, one block per SM; 8
+// in a BF16 PML or a non-PML block, two per SM) stage the tile, build the operands, compute the
 // flux and run the epilogues; they synchronise among themselves on a named
 // barrier.  One extra MMA warp, whose lane 0 issues every product, waits for
 // "operand ready" mbarriers the compute warps arrive on and commits each
 // product to a "product done" mbarrier, so that issuing the products (about
 // a hundred cycles per instruction for the issuing thread) stays off the
 // compute warps' path.
-template <bool PML>
+template <bool PML, bool BF>
 struct TcWarps {
-  static constexpr int compute = PML ? 16 : 8;
+  static constexpr bool ONE = PML && !BF;   // one block per SM
+  static constexpr int compute = ONE ? 16 : 8;
   static constexpr int threads = 32 * (compute + 1);
 };
 
 template <int N, bool PML, bool BF>
-__global__ void __launch_bounds__(TcWarps<PML>::threads, PML ? 1 : 2) tc_stage_kernel(const StageParams<float> P) {
+__global__ void __launch_bounds__(TcWarps<PML, BF>::threads, TcWarps<PML, BF>::ONE ? 1 : 2)
+    tc_stage_kernel(const StageParams<float> P) {
   using PL = Plan<N, PML, BF>;
-  constexpr int NW = TcWarps<PML>::compute;
+  constexpr int NW = TcWarps<PML, BF>::compute;
   constexpr int kTcThreads = 32 * NW;          // compute threads
-  constexpr int kAll = TcWarps<PML>::threads;
+  constexpr int kAll = TcWarps<PML, BF>::threads;
   constexpr int NGRP = NW / 4;                 // warps sharing a TMEM lane quadrant
   constexpr int Np = PL::Np, Nfp = PL::Nfp, NF = PL::NF, Nq = PL::Nq, T = PL::T;
   constexpr int NpK = PL::NpK, NFK = PL::NFK, NqK = PL::NqK;
@@ -954,7 +960,7 @@ cudaError_t launch_n(const StageParams<float>& P, int nb, cudaStream_t s) {
   const long long tiles = (long long)((P.n_elem + PL::T - 1) / PL::T) * nb;
   const int per_sm = 512 / (int)PL::TMEM_COLS;
   const int grid = (int)std::min<long long>(tiles, (long long)per_sm * sms);
-  tc_stage_kernel<N, PML, BF><<<grid, TcWarps<PML>::threads, PL::bytes, s>>>(Q);
+  tc_stage_kernel<N, PML, BF><<<grid, TcWarps<PML, BF>::threads, PL::bytes, s>>>(Q);
   return cudaGetLastError();
 }
 
