@@ -281,6 +281,47 @@ def batching_runs(sh, local, stream):
     return out
 
 
+def precision_form_run(sh, local, stream):
+    """The precision form: 64^3 x 6 = 1,572,864 tets, N = 5, the contractions on
+    the tensor cores with BF16 operands and FP32 accumulation and state, against
+    the FP32 CUDA-core path (itself within 1.3e-7 of FP64): DOF-updates/s of
+    each and the relative L2 difference of E, H after 20 steps."""
+    import torch
+    from paper_2006_02551_gb300 import Solver
+    from synthetic import cube_tet_mesh, workload
+    w = workload("cube64_n5")
+    v, e = cube_tet_mesh(w.n_hex, w.jitter, w.mesh_seed)
+    out = {"workload": describe(w)}
+    states = {}
+    for prec, nrate in (("bf16", 20), ("fp32", 10)):
+        s = Solver(w.N, prec, device=local, stream=sh)
+        s.set_mesh(v, e)
+        s.set_pml(w.pml)
+        s.set_sources(list(w.sources))
+        s.set_probes(list(w.probes))
+        dt = s.stable_dt(1.0)
+        s.set_state(None, 0.0)
+        s.run_steps(2, dt, record=False)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.run_steps(nrate, dt, record=False)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / nrate
+        dofs = mesh_dofs(s)
+        s.set_state(None, 0.0)
+        s.run_steps(20, dt, record=False)
+        q, _ = s.get_state()
+        states[prec] = np.array(q[:, :, 0:6], dtype=np.float32)   # FP32 state either way
+        del q
+        out[prec] = {"ms_per_step": ms, "value": dofs / (ms * 1e-3), "unit": "DOF-updates/s"}
+        s.close()
+    out["dofs_per_step"] = dofs
+    out["l2_rel_bf16_vs_fp32_20_steps"] = float(
+        np.linalg.norm(states["bf16"] - states["fp32"]) / np.linalg.norm(states["fp32"]))
+    return out
+
+
 def gradient_run(sh, local, stream):
     """The differentiation form: J = sum over 8 probes and 2000 steps of |E|^2 on
     the 82,944-tet N=3 mesh with eps_r ~ U[1,4]; gradient with respect to every
@@ -336,6 +377,8 @@ def main():
                     help="skip the batching-form runs (excitation batch, grouped meshes)")
     ap.add_argument("--no-gradient", action="store_true",
                     help="skip the differentiation-form run (FP32 adjoint)")
+    ap.add_argument("--no-precision-form", action="store_true",
+                    help="skip the N = 5 precision-form run (BF16 vs FP32)")
     ap.add_argument("--ref-hex", type=int, default=4,
                     help="cube size of the oracle sample for --impl reference")
     ap.add_argument("--cpu-hex", type=int, default=12,
@@ -542,6 +585,8 @@ def main():
         out_extra["batching"] = batching_runs(sh, local, stream)
     if not args.no_gradient and rank == 0:
         out_extra["gradient"] = gradient_run(sh, local, stream)
+    if not args.no_precision_form and rank == 0:
+        out_extra["precision_form"] = precision_form_run(sh, local, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -740,8 +740,8 @@ wadg_status wadg_create(int N, wadg_precision prec, int32_t n_batch, int device,
   if (N < 1 || N > 5) return fail(nullptr, WADG_EINVAL, "N must be in 1..5 (got %d)", N);
   if (prec != WADG_FP64 && prec != WADG_FP32 && prec != WADG_TF32 && prec != WADG_BF16)
     return fail(nullptr, WADG_EINVAL, "unknown precision %d", prec);
-  if ((prec == WADG_TF32 || prec == WADG_BF16) && !tc_supported(N, false))
-    return fail(nullptr, WADG_EUNSUPPORTED, "the tensor-core stage is built for N <= 4");
+  if ((prec == WADG_TF32 || prec == WADG_BF16) && !tc_supported(N, false, prec == WADG_BF16))
+    return fail(nullptr, WADG_EUNSUPPORTED, "the tensor-core stage is built for N <= 4 (TF32), N <= 5 (BF16)");
   if (n_batch < 1) return fail(nullptr, WADG_EINVAL, "n_batch must be >= 1");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)

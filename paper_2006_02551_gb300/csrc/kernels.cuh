@@ -121,7 +121,7 @@ template <typename Real>
 cudaError_t launch_adjoint_probes(const Real* q, int64_t strideQ, int nprobe, int nb, int Np,
                                   const int* elem, const double* ell, Real* lam, cudaStream_t s);
 // tensor-core (tcgen05) stage kernels: TF32 operands, or BF16 operands (bf16)
-bool tc_supported(int N, bool kappa);
+bool tc_supported(int N, bool kappa, bool bf16);
 cudaError_t configure_tc_kernels(int N, bool bf16);
 cudaError_t launch_stage_tc(int N, bool pml, const StageParams<float>& P, int nb, cudaStream_t s,
                             bool bf16);

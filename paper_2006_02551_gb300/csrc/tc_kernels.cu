@@ -252,9 +252,11 @@ struct Plan {
   __host__ __device__ static constexpr int rupK(int x) { return (x + O::KS - 1) / O::KS * O::KS; }
   static constexpr int NpK = rupK(Np), NFK = rupK(NF), NqK = rupK(Nq);
   // elements per tile: 8; 4 for BF16 PML tiles, whose smaller operands then
-  // let two blocks share an SM
-  static constexpr bool PAIR = PML && BF;
-  static constexpr int T = PAIR ? 4 : 8;
+  // let two blocks share an SM (N <= 4) or fit at all (N = 5)
+  static constexpr bool PAIR = PML && BF && N <= 4;
+  static constexpr int T = PML && BF ? 4 : 8;
+  // one block per SM with 16 compute warps (TF32 PML; every BF16 N = 5 tile)
+  static constexpr bool ONE = PML ? !PAIR : (BF && N == 5);
   static constexpr int NV = rup16(6 * T);            // columns of E,H products
   static constexpr int NQ = rup16(12 * T);           // columns of 12-component products
   static constexpr int G_p = NpK / 8;                // 8-row groups of an Np-row operator
@@ -271,12 +273,18 @@ struct Plan {
   // A operands
   static constexpr uint32_t oPq = 0;
   static constexpr uint32_t oL = PML ? oPq + G_p * SBO_Q : 0;
-  // Dr, Ds, Dt stacked as one operator of 3 Np rows (row d Np + i)
+  // Dr, Ds, Dt stacked as one operator of 3 Np rows (row d Np + i), read as
+  // VT products of up to 128 rows: DPT derivatives per product (N <= 4: all
+  // three in one; N = 5: [Dr; Ds], then Dt)
+  static constexpr int DPT = (128 / Np) < 3 ? (128 / Np) : 3;
+  static constexpr int VT = (3 + DPT - 1) / DPT;
   static constexpr int RV = rup8(3 * Np);
   static constexpr uint32_t oVol = oL + G_p * SBO_L;
   static constexpr uint32_t oVq = oVol + (RV / 8) * SBO_V;
+  // V_q read as VQT products of 128 rows (quadrature points q and q + 128)
+  static constexpr int VQT = (Nq + 127) / 128;
   // B operands
-  static constexpr uint32_t oBF = PML ? oVq + 16 * SBO_V : oVq;
+  static constexpr uint32_t oBF = PML ? oVq + 16 * VQT * SBO_V : oVq;
   static constexpr int ROWS_F = PML ? NQ : NV;        // E,H (+ P) rows
   static constexpr uint32_t oBFL = oBF + (ROWS_F / 8) * SBB_V;
   static constexpr uint32_t oBTZ = oBFL + (NV / 8) * SBB_L;
@@ -309,22 +317,25 @@ struct Plan {
   // TF32 PML block (512 columns) per SM, enforced by the shared-memory request
   // so that no block waits in tcgen05.alloc; BF16 PML blocks (256 columns)
   // and non-PML blocks (128 columns) two per SM (shared memory, registers)
-  static constexpr uint32_t min_bytes = PML && !PAIR ? 116 * 1024 : 100 * 1024;
+  static constexpr uint32_t min_bytes = ONE ? 116 * 1024 : 100 * 1024;
   static constexpr uint32_t bytes = bytes_used < min_bytes ? min_bytes : bytes_used;
-  static constexpr uint32_t TMEM_COLS = PML ? (PAIR ? 256 : 512) : 128;
-  // TMEM column bases: stacked derivatives (lanes d Np + i), LIFT, V_q, P_q
-  static constexpr uint32_t cV = 0, cL = NV;
-  static constexpr uint32_t cVq = 2 * NV, cPq = 2 * NV + NQ;
-  static_assert(!PML || 2 * NV + 2 * NQ <= TMEM_COLS, "TMEM columns");
-  static_assert(!PAIR || bytes <= 113 * 1024, "two BF16 PML blocks per SM");
-  static_assert(PML || 2 * NV <= 128, "TMEM columns");
-  static_assert(3 * Np <= 128, "stacked derivative operators fit one M=128 tile");
-  static_assert(Nq <= 128 || !PML, "V_q rows must fit one M=128 tile");
+  // TMEM column bases: derivative products (lanes d Np + i of product v at
+  // cV + v NV), LIFT, V_q products (cVq + t NQ), P_q
+  static constexpr uint32_t cV = 0, cL = VT * NV;
+  static constexpr uint32_t cVq = cL + NV, cPq = cVq + VQT * NQ;
+  static constexpr uint32_t COLS = PML ? cPq + NQ : cL + NV;
+  static constexpr uint32_t TMEM_COLS = COLS <= 128 ? 128 : (COLS <= 256 ? 256 : 512);
+  static_assert(COLS <= 512, "TMEM columns");
+  static_assert(!PAIR || (bytes <= 113 * 1024 && TMEM_COLS <= 256), "two BF16 PML blocks per SM");
+  static_assert(ONE || TMEM_COLS <= 256, "two blocks per SM");
+  static_assert((DPT * Np) % 8 == 0 || VT == 1, "second derivative product starts on a row group");
+  static_assert(VT <= 2 && VQT <= 2, "at most two products per operator");
   static_assert(Np <= 64, "node rows");
   // every A operand read (128 rows from its start) stays inside the block
   static_assert(oPq + 16 * SBO_Q <= bytes || !PML, "P_q span");
   static_assert(oL + 16 * SBO_L <= bytes, "LIFT span");
-  static_assert(oVol + 16 * SBO_V <= bytes, "volume operator span");
+  static_assert(oVol + ((VT - 1) * DPT * Np / 8 + 16) * SBO_V <= bytes, "volume operator span");
+  static_assert(!PML || oVq + 16 * VQT * SBO_V <= bytes, "V_q span");
   static_assert(bytes <= 227 * 1024, "shared memory");
 };
 
@@ -336,20 +347,20 @@ struct Plan {
 // product to a "product done" mbarrier, so that issuing the products (about
 // a hundred cycles per instruction for the issuing thread) stays off the
 // compute warps' path.
-template <bool PML, bool BF>
+template <int N, bool PML, bool BF>
 struct TcWarps {
-  static constexpr bool ONE = PML && !BF;   // one block per SM
+  static constexpr bool ONE = Plan<N, PML, BF>::ONE;   // one block per SM
   static constexpr int compute = ONE ? 16 : 8;
   static constexpr int threads = 32 * (compute + 1);
 };
 
 template <int N, bool PML, bool BF>
-__global__ void __launch_bounds__(TcWarps<PML, BF>::threads, TcWarps<PML, BF>::ONE ? 1 : 2)
+__global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, BF>::ONE ? 1 : 2)
     tc_stage_kernel(const StageParams<float> P) {
   using PL = Plan<N, PML, BF>;
-  constexpr int NW = TcWarps<PML, BF>::compute;
+  constexpr int NW = TcWarps<N, PML, BF>::compute;
   constexpr int kTcThreads = 32 * NW;          // compute threads
-  constexpr int kAll = TcWarps<PML, BF>::threads;
+  constexpr int kAll = TcWarps<N, PML, BF>::threads;
   constexpr int NGRP = NW / 4;                 // warps sharing a TMEM lane quadrant
   constexpr int Np = PL::Np, Nfp = PL::Nfp, NF = PL::NF, Nq = PL::Nq, T = PL::T;
   constexpr int NpK = PL::NpK, NFK = PL::NFK, NqK = PL::NqK;
@@ -520,22 +531,26 @@ __global__ void __launch_bounds__(TcWarps<PML, BF>::threads, TcWarps<PML, BF>::O
       }
     }
   };
-  auto load_sig = [&](int tile, float (&sgv)[PML ? EH : 1][3]) {
+  constexpr int VQT = PL::VQT;
+  auto load_sig = [&](int tile, float (&sgv)[PML ? EH : 1][VQT][3]) {
     if (!PML) return;
     const int b = tile / tiles_per_batch;
     const int t0 = (tile - b * tiles_per_batch) * T;
     const int ne = min(T, P.n_elem - t0);
     const int ep0 = P.e_begin + t0 - P.K0;
-    const int q = quad * 32 + lane;
 #pragma unroll
     for (int k = 0; k < (PML ? EH : 1); ++k) {
       const int e = grp + NGRP * k;
-      sgv[k][0] = sgv[k][1] = sgv[k][2] = 0.f;
-      if (e < ne && q < Nq) {
-        const int64_t sb = (int64_t)(ep0 + e) * 3 * NqP + q;
-        sgv[k][0] = P.sig[sb];
-        sgv[k][1] = P.sig[sb + NqP];
-        sgv[k][2] = P.sig[sb + 2 * NqP];
+#pragma unroll
+      for (int t = 0; t < VQT; ++t) {
+        const int q = 128 * t + quad * 32 + lane;
+        sgv[k][t][0] = sgv[k][t][1] = sgv[k][t][2] = 0.f;
+        if (e < ne && q < Nq) {
+          const int64_t sb = (int64_t)(ep0 + e) * 3 * NqP + q;
+          sgv[k][t][0] = P.sig[sb];
+          sgv[k][t][1] = P.sig[sb + NqP];
+          sgv[k][t][2] = P.sig[sb + 2 * NqP];
+        }
       }
     }
   };
@@ -586,14 +601,19 @@ __global__ void __launch_bounds__(TcWarps<PML, BF>::threads, TcWarps<PML, BF>::O
       for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         if (!wait_ready(0)) { mfail = true; break; }
         if (PML) {   // V_q first: the quadrature epilogue waits for it alone
-          for (int k = 0; k < NpK / KS; ++k)
-            mma(tmem + PL::cVq, make_desc(sbase + PL::oVq + 256 * k, 128, PL::SBO_V),
-                     make_desc(sbase + PL::oBF + 2 * PL::LB * k, PL::LB, PL::SBB_V), idQ, k > 0);
+          for (int t = 0; t < PL::VQT; ++t)   // rows 128 t .. 128 t + 127
+            for (int k = 0; k < NpK / KS; ++k)
+              mma(tmem + PL::cVq + t * PL::NQ,
+                  make_desc(sbase + PL::oVq + 16 * t * PL::SBO_V + 256 * k, 128, PL::SBO_V),
+                  make_desc(sbase + PL::oBF + 2 * PL::LB * k, PL::LB, PL::SBB_V), idQ, k > 0);
           mma_commit(saddr(mbar + 0));
         }
-        for (int k = 0; k < NpK / KS; ++k)
-          mma(tmem + PL::cV, make_desc(sbase + PL::oVol + 256 * k, 128, PL::SBO_V),
-                   make_desc(sbase + PL::oBF + 2 * PL::LB * k, PL::LB, PL::SBB_V), idV, k > 0);
+        for (int v = 0; v < PL::VT; ++v)   // derivatives DPT v .. DPT v + DPT - 1
+          for (int k = 0; k < NpK / KS; ++k)
+            mma(tmem + PL::cV + v * PL::NV,
+                make_desc(sbase + PL::oVol + (v * PL::DPT * Np / 8) * PL::SBO_V + 256 * k, 128,
+                          PL::SBO_V),
+                make_desc(sbase + PL::oBF + 2 * PL::LB * k, PL::LB, PL::SBB_V), idV, k > 0);
         issued = true;
         if (!wait_ready(1)) { mfail = true; break; }
         for (int k = 0; k < NFK / KS; ++k)
@@ -619,7 +639,7 @@ __global__ void __launch_bounds__(TcWarps<PML, BF>::threads, TcWarps<PML, BF>::O
   } else {
   float Ep[FT][3], Hp[FT][3], ZPv[FT];
   int nbv[FT], codev[FT];
-  float sgv[PML ? EH : 1][3];
+  float sgv[PML ? EH : 1][VQT][3];
   float nv = 0.f, matv = 0.f;
   double mv = 0.0;
   if ((int)blockIdx.x < ntiles) {
@@ -758,16 +778,19 @@ __global__ void __launch_bounds__(TcWarps<PML, BF>::threads, TcWarps<PML, BF>::O
       if (!wait_bar(0)) { failed = true; break; }   // V_q product
       // ---- epilogue A1: eq. 9 at the quadrature points -> B of P_q
       {
-        const int q = quad * 32 + lane;     // quadrature point of this lane
         const float ie0 = 1.f / (float)P.eps0;
 #pragma unroll
+        for (int t = 0; t < VQT; ++t)         // V_q product t: points 128 t + lane row
+#pragma unroll
         for (int k = 0; k < EH; ++k) {       // warp-uniform loop over this group's elements
+          const int q = 128 * t + quad * 32 + lane;   // quadrature point of this lane
           const int e = grp + NGRP * k;
           if (e >= T) break;
           float v[12];
-          tld_6x2(tmem + lane_base + PL::cVq + e * 6, tmem + lane_base + PL::cVq + 6 * T + e * 6, v);
+          const uint32_t cq = PL::cVq + t * PL::NQ;
+          tld_6x2(tmem + lane_base + cq + e * 6, tmem + lane_base + cq + 6 * T + e * 6, v);
           if (e >= ne || q >= NqK) continue;
-          const float* sg = sgv[k];
+          const float* sg = sgv[k][t];
           float o[12];
 #pragma unroll
           for (int u = 0; u < 3; ++u) {
@@ -797,23 +820,53 @@ __global__ void __launch_bounds__(TcWarps<PML, BF>::threads, TcWarps<PML, BF>::O
     // ---- derivative and LIFT columns -> shared memory.  Lane d Np + i holds
     // the d-th derivative at node i, lane i the LIFT term at node i.
     float* DV = reinterpret_cast<float*>(smem + PL::oDV);   // [T][24][Np]
-    if (quad * 32 < 3 * Np) {
-      const int L = quad * 32 + lane;
-      const int d = L / Np, i = L - d * Np;
-      for (int e = grp; e < T; e += NGRP) {
-        float v[12];   // derivative d of the 6 components | LIFT of the 6 components
-        if (quad * 32 < Np)
-          tld_6x2(tmem + lane_base + PL::cV + e * 6, tmem + lane_base + PL::cL + e * 6, v);
-        else
-          tld6(tmem + lane_base + PL::cV + e * 6, v);
-        if (e >= ne) continue;
-        if (L < 3 * Np) {
+    if constexpr (PL::VT == 1) {
+      if (quad * 32 < 3 * Np) {
+        const int L = quad * 32 + lane;
+        const int d = L / Np, i = L - d * Np;
+        for (int e = grp; e < T; e += NGRP) {
+          float v[12];   // derivative d of the 6 components | LIFT of the 6 components
+          if (quad * 32 < Np)
+            tld_6x2(tmem + lane_base + PL::cV + e * 6, tmem + lane_base + PL::cL + e * 6, v);
+          else
+            tld6(tmem + lane_base + PL::cV + e * 6, v);
+          if (e >= ne) continue;
+          if (L < 3 * Np) {
 #pragma unroll
-          for (int c = 0; c < 6; ++c) DV[(e * 24 + d * 6 + c) * Np + i] = v[c];
+            for (int c = 0; c < 6; ++c) DV[(e * 24 + d * 6 + c) * Np + i] = v[c];
+          }
+          if (quad * 32 < Np && L < Np) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) DV[(e * 24 + 18 + c) * Np + i] = v[6 + c];
+          }
         }
-        if (quad * 32 < Np && L < Np) {
+      }
+    } else {
+      // two derivative products: lane d Np + i of the first holds derivative d
+      // (d < DPT), lane d' Np + i of the second derivative DPT + d'
+      constexpr int R0 = PL::DPT * Np, R1 = (3 - PL::DPT) * Np;
+      if (quad * 32 < R0) {
+        const int L = quad * 32 + lane;
+        const int d0 = L / Np, i0 = L - d0 * Np;
+        const int d1 = PL::DPT + d0;
+        for (int e = grp; e < T; e += NGRP) {
+          float v[6], w[6], l[6];
+          tld6(tmem + lane_base + PL::cV + e * 6, v);
+          if (quad * 32 < R1) tld6(tmem + lane_base + PL::cV + PL::NV + e * 6, w);
+          if (quad * 32 < Np) tld6(tmem + lane_base + PL::cL + e * 6, l);
+          if (e >= ne) continue;
+          if (L < R0) {
 #pragma unroll
-          for (int c = 0; c < 6; ++c) DV[(e * 24 + 18 + c) * Np + i] = v[6 + c];
+            for (int c = 0; c < 6; ++c) DV[(e * 24 + d0 * 6 + c) * Np + i0] = v[c];
+          }
+          if (quad * 32 < R1 && L < R1) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) DV[(e * 24 + d1 * 6 + c) * Np + i0] = w[c];
+          }
+          if (quad * 32 < Np && L < Np) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) DV[(e * 24 + 18 + c) * Np + L] = l[c];
+          }
         }
       }
     }
@@ -958,15 +1011,16 @@ cudaError_t launch_n(const StageParams<float>& P, int nb, cudaStream_t s) {
   StageParams<float> Q = P;
   Q.nb = nb;
   const long long tiles = (long long)((P.n_elem + PL::T - 1) / PL::T) * nb;
-  const int per_sm = 512 / (int)PL::TMEM_COLS;
+  const int per_sm = PL::ONE ? 1 : 512 / (int)PL::TMEM_COLS;
   const int grid = (int)std::min<long long>(tiles, (long long)per_sm * sms);
-  tc_stage_kernel<N, PML, BF><<<grid, TcWarps<PML, BF>::threads, PL::bytes, s>>>(Q);
+  tc_stage_kernel<N, PML, BF><<<grid, TcWarps<N, PML, BF>::threads, PL::bytes, s>>>(Q);
   return cudaGetLastError();
 }
 
 }  // namespace tc
 
-bool tc_supported(int N, bool kappa) { return N >= 1 && N <= 4 && !kappa; }
+// TF32: N <= 4; BF16 operands, whose tiles are half the size, also N = 5
+bool tc_supported(int N, bool kappa, bool bf16) { return N >= 1 && N <= (bf16 ? 5 : 4) && !kappa; }
 
 template <bool BF>
 cudaError_t configure_tc_bf(int N) {
@@ -976,6 +1030,12 @@ cudaError_t configure_tc_bf(int N) {
     case 2: e = tc::configure_n<2, false, BF>(); if (e == cudaSuccess) e = tc::configure_n<2, true, BF>(); break;
     case 3: e = tc::configure_n<3, false, BF>(); if (e == cudaSuccess) e = tc::configure_n<3, true, BF>(); break;
     case 4: e = tc::configure_n<4, false, BF>(); if (e == cudaSuccess) e = tc::configure_n<4, true, BF>(); break;
+    case 5:
+      if constexpr (BF) {
+        e = tc::configure_n<5, false, true>();
+        if (e == cudaSuccess) e = tc::configure_n<5, true, true>();
+      }
+      break;
     default: break;
   }
   return e;
@@ -992,6 +1052,10 @@ cudaError_t launch_tc_bf(int N, bool pml, const StageParams<float>& P, int nb, c
     case 2: return pml ? tc::launch_n<2, true, BF>(P, nb, s) : tc::launch_n<2, false, BF>(P, nb, s);
     case 3: return pml ? tc::launch_n<3, true, BF>(P, nb, s) : tc::launch_n<3, false, BF>(P, nb, s);
     case 4: return pml ? tc::launch_n<4, true, BF>(P, nb, s) : tc::launch_n<4, false, BF>(P, nb, s);
+    case 5:
+      if constexpr (BF)
+        return pml ? tc::launch_n<5, true, true>(P, nb, s) : tc::launch_n<5, false, true>(P, nb, s);
+      return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
 }

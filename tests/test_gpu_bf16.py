@@ -45,16 +45,18 @@ def increment_error(N, prof, n_hex=4, stage=0, sources=(), n_batch=1, seed=0):
     return err
 
 
-@pytest.mark.parametrize("N", [1, 2, 3, 4])
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5])
 def test_bf16_one_stage_with_pml(N):
-    err = increment_error(N, PML3)
+    # N = 5: two derivative products ([Dr; Ds], Dt) and two V_q products
+    err = increment_error(N, PML3, n_hex=4 if N < 5 else 3)
     print(f"BF16 N={N} increment error {err:.3e}")
     assert err < 3e-2, err
 
 
 def test_bf16_one_stage_without_pml_and_batched():
-    err = increment_error(4, None, n_hex=3, stage=2)
-    assert err < 3e-2, err
+    for N in (4, 5):
+        err = increment_error(N, None, n_hex=3, stage=2)
+        assert err < 3e-2, (N, err)
     srcs = tuple(Dipole(x=(0.1 * b, -0.05 * b, 0.02), t0=0.4, width=0.25, batch=b)
                  for b in range(3))
     err = increment_error(3, PML3, n_hex=3, sources=srcs, stage=1, n_batch=3)
