@@ -197,6 +197,22 @@ def run_reference(args, w):
     print(json.dumps(line))
 
 
+def job_time_max(t_local, dist, device):
+    """Replicas only: the job ends when its slowest rank does, so every rank
+    takes the maximum of the ranks' times (t_local unchanged without dist)."""
+    if dist is None:
+        return t_local
+    import torch
+    tt = torch.tensor([float(t_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_rate(units_per_rank, world, t_max):
+    """Units all ranks processed per unit of the slowest rank's time."""
+    return world * units_per_rank / t_max
+
+
 def mesh_dofs(s):
     i = s.info()
     return i["Np"] * 6 * (i["K"] + i["K_pml"]) * s.n_batch
@@ -443,12 +459,9 @@ def main():
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        tt = torch.tensor([ms], device=f"cuda:{local}")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * dofs * args.steps / (ms * 1e-3)
+    dev = f"cuda:{local}" if dist is not None and dist.get_backend() == "nccl" else "cpu"
+    ms = job_time_max(ev0.elapsed_time(ev1), dist, dev)
+    value = whole_job_rate(dofs * args.steps, world, ms * 1e-3)
 
     # per-kernel durations (CUDA events on the library stream, eager launches)
     kms = s.profile_stage(50, dt)
@@ -494,11 +507,13 @@ def main():
     rec_bytes = len(w.probes) * 6 * w.n_batch * 8
     q_host = np.zeros((w.n_batch, K, 12, Np))
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     t0 = time.perf_counter()
     s.set_state(q_host, 0.0)
     s.run_steps(args.steps, dt, record=True)
     t1 = time.perf_counter()
-    e2e_val = world * dofs * args.steps / (t1 - t0)
+    e2e_val = whole_job_rate(dofs * args.steps, world, job_time_max(t1 - t0, dist, dev))
     h2d = (w.n_batch * (K + K1) * 6 * Np * rs) / args.steps
     e2e = {"value": e2e_val, "unit": "DOF-updates/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": rec_bytes}
