@@ -43,11 +43,11 @@ FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (no measured figure available)
 # ncu --set full capture of the small case of the benchmark recipe (summary
 # and command in profiles/tc_stage_kernels_cube24_n4_full.md), valid for the
 # kernel source it was taken on (sha256 of csrc/tc_kernels.cu)
-TC_PML_TRAFFIC = {"sha256": "32e3ce971f6d2909e80441628067d6081273ab67d71296450c8b22540e95ff0b",
-                  "bytes_per_pml_element": 7585.0, "N": 4}
+TC_PML_TRAFFIC = {"sha256": "cd1d4393c3ef39e60c51d6f6b8ecbce5c21b49c72f9ec5107df6eb0860018ae2",
+                  "bytes_per_pml_element": {"tf32": 7579.0, "bf16": 7619.0}, "N": 4}
 
 
-def tc_pml_traffic(K1, N):
+def tc_pml_traffic(K1, N, precision):
     """Per-launch DRAM bytes of the PML kernel, or None once the kernel changed."""
     import hashlib
     src = os.path.join(ROOT, "paper_2006_02551_gb300", "csrc", "tc_kernels.cu")
@@ -56,9 +56,10 @@ def tc_pml_traffic(K1, N):
             h = hashlib.sha256(f.read()).hexdigest()
     except OSError:
         return None
-    if h != TC_PML_TRAFFIC["sha256"] or N != TC_PML_TRAFFIC["N"]:
+    per = TC_PML_TRAFFIC["bytes_per_pml_element"].get(precision)
+    if h != TC_PML_TRAFFIC["sha256"] or N != TC_PML_TRAFFIC["N"] or per is None:
         return None
-    return TC_PML_TRAFFIC["bytes_per_pml_element"] * K1
+    return per * K1
 
 
 def describe(w):
@@ -480,8 +481,7 @@ def main():
     achieved_gbs = d_bytes / (d_ms * 1e-3) / 1e9
     if args.precision in ("tf32", "bf16"):
         # tensor-core contractions: the stage is bound by HBM traffic
-        traffic = (tc_pml_traffic(K1 * w.n_batch, N)
-                   if dom == "pml" and args.precision == "tf32" else None)
+        traffic = tc_pml_traffic(K1 * w.n_batch, N, args.precision) if dom == "pml" else None
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
                     "frac": achieved_gbs / hbm, "traffic": traffic,
                     "traffic_source": "profiles/tc_stage_kernels_cube24_n4_full.md (scaled by elements)",
