@@ -102,7 +102,9 @@ typedef struct {
 /* Create a context for polynomial order N (1..5) with n_batch independent
  * excitations advanced together on CUDA device `device`, issuing work on
  * `cuda_stream` (a cudaStream_t, may be NULL).  EINVAL on bad N, precision
- * or n_batch; ECUDA if the device cannot be used. */
+ * or n_batch; EUNSUPPORTED for WADG_TF32 with N = 5 (the tensor-core stage
+ * takes N <= 4 with TF32 operands, N <= 5 with BF16); ECUDA if the device
+ * cannot be used. */
 wadg_status wadg_create(int N, wadg_precision prec, int32_t n_batch, int device,
                         void* cuda_stream, wadg_ctx** out);
 
@@ -271,11 +273,14 @@ const char* wadg_last_error(const wadg_ctx* ctx);
  * blocks start on the (member, class) items in proportion to their
  * algorithmic flops and then take tiles from per-item counters until none
  * are left, so the load balances itself; one step (the 5 stage launches and
- * each member's probe and clock kernels) is captured in a CUDA graph.  Members: FP32
- * contexts (WADG_FP32) with a mesh, the weight-adjusted or element-constant
- * PML scheme, on one device; the group runs on the first member's stream.
- * Each member keeps its own state, time, probes and records.  The group
- * refers to its members: destroy the group before any member. */
+ * each member's probe and clock kernels) is captured in a CUDA graph.  Each
+ * member advances exactly as wadg_run_steps advances it (the stage of
+ * eqs. 10, 11 and 26-29 with the time marching of Section II.B); the grouping
+ * itself has no counterpart in the paper.  Members: FP32 contexts (WADG_FP32)
+ * with a mesh, the weight-adjusted or element-constant PML scheme, on one
+ * device; the group runs on the first member's stream.  Each member keeps its
+ * own state, time, probes and records.  The group refers to its members:
+ * destroy the group before any member. */
 typedef struct wadg_group wadg_group;
 
 /* EINVAL for a null or repeated member or members on different devices,
