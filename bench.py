@@ -43,8 +43,8 @@ FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (no measured figure available)
 # ncu --set full capture of the small case of the benchmark recipe (summary
 # and command in profiles/tc_stage_kernels_cube24_n4_full.md), valid for the
 # kernel source it was taken on (sha256 of csrc/tc_kernels.cu)
-TC_PML_TRAFFIC = {"sha256": "cd1d4393c3ef39e60c51d6f6b8ecbce5c21b49c72f9ec5107df6eb0860018ae2",
-                  "bytes_per_pml_element": {"tf32": 7579.0, "bf16": 7619.0}, "N": 4}
+TC_PML_TRAFFIC = {"sha256": "441175909e75301bacc4fc388fa8c496c8341c44d8a79963edef4987c41fb6ad",
+                  "bytes_per_pml_element": {"tf32": 7585.0, "bf16": 7614.0}, "N": 4}
 
 
 def tc_pml_traffic(K1, N, precision):
@@ -408,7 +408,10 @@ def main():
     from synthetic import workload
     w = workload(args.workload)
     if args.hex:
+        from dataclasses import replace as _replace
         w = workload(args.workload, n_hex=args.hex)
+        if args.hex != workload(args.workload).n_hex:
+            w = _replace(w, name=f"{w.name} resized to {args.hex}^3 cells")
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

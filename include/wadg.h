@@ -253,6 +253,22 @@ wadg_status wadg_mesh_info(const wadg_ctx* ctx, int64_t* K, int64_t* K_pml, int3
 /* Block until all work issued by ctx has finished. */
 wadg_status wadg_synchronize(wadg_ctx* ctx);
 
+/* Failure-detection test aid for the TF32 and BF16 contexts, the ones whose
+ * kernels wait on device-side signals (the mbarriers between the tensor-core
+ * issuing thread and the compute warps).  Every such wait gives up after
+ * about one second, sets the context's error flag and lets the kernel drain
+ * the products it issued, release its tensor memory and end; the call that
+ * launched it (wadg_rk_stage, wadg_run_steps, wadg_run_steps_noalloc) then
+ * returns WADG_ETIMEOUT, with the state partly updated.  This call arms one
+ * request: the first block of a later tensor-core stage launch that takes it
+ * issues the flux product of its first tile without the completion signal,
+ * so that one wait runs out.  Nothing faults, traps or waits without limit,
+ * and the context stays usable (set the state again and step).  The request
+ * stays armed until a launch takes it.  EUNSUPPORTED for FP64 and FP32
+ * contexts.  (The paper has no counterpart; this tests the library's error
+ * path.) */
+wadg_status wadg_arm_wait_timeout(wadg_ctx* ctx);
+
 /* Reference-element operator of order N (host only, no device needed), for
  * checking the library's set-up against an independent construction.
  * which: 0 Dr, 1 Ds, 2 Dt ([Np][Np]), 3 LIFT ([Np][4 Nfp]), 4 V_q ([Nq][Np]),

@@ -572,6 +572,7 @@ StageParams<Real> stage_params(wadg_ctx* ctx, int stage, double dt, double t, bo
   P.alpha = 1.0;
   P.tcops = ctx->tcops.p;
   P.err = (int*)ctx->errflag.p;
+  P.inject = ctx->tc ? (int*)ctx->errflag.p + 1 : nullptr;
   return P;
 }
 
@@ -786,8 +787,9 @@ wadg_status wadg_create(int N, wadg_precision prec, int32_t n_batch, int device,
     if (ce == cudaSuccess) ce = dalloc(ctx->tdev, 8);
     if (ce == cudaSuccess) ce = dalloc(ctx->stepdev, 8);
     if (ce == cudaSuccess) ce = dalloc(ctx->flag, 4);
-    if (ce == cudaSuccess) ce = dalloc(ctx->errflag, 4);
-    if (ce == cudaSuccess) ce = cudaMemset(ctx->errflag.p, 0, 4);
+    // [0] error flag of the bounded waits, [1] armed failure-detection request
+    if (ce == cudaSuccess) ce = dalloc(ctx->errflag, 8);
+    if (ce == cudaSuccess) ce = cudaMemset(ctx->errflag.p, 0, 8);
     if (ce == cudaSuccess) ce = dalloc(ctx->obj, 8 * (size_t)n_batch);
     if (ce == cudaSuccess) ce = cudaMemset(ctx->obj.p, 0, 8 * (size_t)n_batch);
     if (ce != cudaSuccess) s = fail(nullptr, WADG_ECUDA, "%s", cudaGetErrorString(ce));
@@ -1085,6 +1087,9 @@ wadg_status wadg_run_steps(wadg_ctx* ctx, int64_t nsteps, double dt, double* pro
     done += n;
   }
   ctx->t += nsteps * dt;
+  // a wait that gave up explains whatever the state holds: report it first
+  s = check_err_flag(ctx);
+  if (s != WADG_OK) return s;
   // non-finite check of the E,H state
   CK(cudaMemsetAsync(ctx->flag.p, 0, 4, ctx->stream));
   const int64_t nq = ctx->nb * ctx->K * 6 * ctx->ref.Np;
@@ -1094,7 +1099,7 @@ wadg_status wadg_run_steps(wadg_ctx* ctx, int64_t nsteps, double dt, double* pro
   CK(cudaMemcpyAsync(&flag, ctx->flag.p, 4, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   if (flag) return fail(ctx, WADG_ENONFINITE, "state became non-finite");
-  return check_err_flag(ctx);
+  return WADG_OK;
 }
 
 wadg_status wadg_profile_stage(wadg_ctx* ctx, int reps, double dt, double* ms_out) {
@@ -1378,6 +1383,17 @@ wadg_status wadg_mesh_info(const wadg_ctx* ctx, int64_t* K, int64_t* K_pml, int3
 wadg_status wadg_synchronize(wadg_ctx* ctx) {
   if (!ctx) return fail(nullptr, WADG_EINVAL, "null context");
   cudaSetDevice(ctx->device);
+  CK(cudaStreamSynchronize(ctx->stream));
+  return WADG_OK;
+}
+
+wadg_status wadg_arm_wait_timeout(wadg_ctx* ctx) {
+  if (!ctx) return fail(nullptr, WADG_EINVAL, "null context");
+  if (!ctx->tc)
+    return fail(ctx, WADG_EUNSUPPORTED, "only the tensor-core kernels wait on device-side signals");
+  cudaSetDevice(ctx->device);
+  const int one = 1;
+  CK(cudaMemcpyAsync((int*)ctx->errflag.p + 1, &one, 4, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return WADG_OK;
 }

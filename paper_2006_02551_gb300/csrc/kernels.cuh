@@ -65,6 +65,8 @@ struct StageParams {
   double alpha;             // flux upwinding (1 upwind, 0 central)
   const void* tcops;        // tensor-core operator tables (TF32 path)
   int* err;                 // device error flag (bounded waits that gave up)
+  int* inject;              // tensor-core kernels: armed failure-detection request
+                            // (nonzero: one block withholds a product signal), or null
 };
 
 // reverse Runge-Kutta stage (adjoint.cu)

@@ -98,10 +98,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t a, uint32_t parity) {
   return ok != 0;
 }
 
-// bounded wait for the given phase parity
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// wait for the given phase parity; gives up (false) after about a second of
+// global time, or after 2^24 polls, whichever comes first.  A product or an
+// operand tile takes microseconds, so only a signal that never comes reaches
+// the limit.
+constexpr uint64_t kWaitLimitNs = 1000000000ull;
 __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
-  for (int i = 0; i < (1 << 22); ++i)
+  if (mbar_try_wait(a, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (int i = 0; i < (1 << 24); ++i) {
     if (mbar_try_wait(a, parity)) return true;
+    if (global_ns() - t0 > kWaitLimitNs) break;
+  }
   return false;
 }
 
@@ -598,6 +612,12 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
         if constexpr (BF) mma_bf16(d, a, b, id, acc);
         else mma_tf32(d, a, b, id, acc);
       };
+      // failure-detection hook: a block that takes the armed request withholds
+      // the completion signal of its first flux product, so that the compute
+      // warps' bounded wait runs out
+      bool withhold = false;
+      if (P.inject && (int)blockIdx.x < ntiles && *reinterpret_cast<volatile int*>(P.inject))
+        withhold = atomicExch(P.inject, 0) != 0;
       for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         if (!wait_ready(0)) { mfail = true; break; }
         if (PML) {   // V_q first: the quadrature epilogue waits for it alone
@@ -619,7 +639,8 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
         for (int k = 0; k < NFK / KS; ++k)
           mma(tmem + PL::cL, make_desc(sbase + PL::oL + 256 * k, 128, PL::SBO_L),
                    make_desc(sbase + PL::oBFL + 2 * PL::LB * k, PL::LB, PL::SBB_L), idV, k > 0);
-        mma_commit(saddr(mbar + 1));
+        if (!withhold) mma_commit(saddr(mbar + 1));
+        withhold = false;
         if (PML) {
           if (!wait_ready(2)) { mfail = true; break; }
           for (int k = 0; k < NqK / KS; ++k)

@@ -65,6 +65,7 @@ _SIG = {
                            C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)],
     "wadg_mesh_info": [_P, _I64, _I64, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
     "wadg_synchronize": [_P],
+    "wadg_arm_wait_timeout": [_P],
     "wadg_reference_operator": [C.c_int, C.c_int, _D, C.c_int64, _I64],
     "wadg_group_create": [C.c_int32, C.POINTER(_P), C.POINTER(_P)],
     "wadg_group_destroy": [_P],
@@ -272,6 +273,12 @@ class Solver:
 
     def synchronize(self):
         self._c(self.lib.wadg_synchronize(self.ctx))
+
+    def arm_wait_timeout(self):
+        """Failure-detection test aid (TF32/BF16 contexts): the next
+        tensor-core stage launch withholds one product signal, its bounded
+        wait runs out and the stepping call raises WadgError(ETIMEOUT)."""
+        self._c(self.lib.wadg_arm_wait_timeout(self.ctx))
 
 
 class Group:
