@@ -125,10 +125,15 @@ void dfree(DevPtr& d) {
   d.bytes = 0;
 }
 
+// Every device buffer ends with kSlack spare bytes: the tensor-core kernels
+// stage element blocks as bulk copies of their 16-byte-aligned cover, whose
+// end may pass a buffer's last value by up to 8 bytes.
+constexpr size_t kSlack = 64;
+
 cudaError_t dalloc(DevPtr& d, size_t bytes) {
   dfree(d);
   if (bytes == 0) return cudaSuccess;
-  cudaError_t e = cudaMalloc(&d.p, bytes);
+  cudaError_t e = cudaMalloc(&d.p, bytes + kSlack);
   if (e == cudaSuccess) d.bytes = bytes;
   else d.p = nullptr;
   return e;

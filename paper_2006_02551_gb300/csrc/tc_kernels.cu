@@ -211,12 +211,19 @@ __device__ __forceinline__ void mbar_arrive(uint32_t a) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
 }
 
-// 4-byte asynchronous global -> shared copies
-__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(saddr(dst)), "l"(src) : "memory");
+// bulk global -> shared copy (both addresses 16-byte aligned, size a
+// multiple of 16) whose bytes complete on mbarrier `bar`
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(dst), "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+// arrive on `bar` and add `bytes` to the transaction count its phase waits for
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
 }
 
 // operand element: TF32 held in 32 bits (4 per 16-byte core-matrix row, 8 K
@@ -306,11 +313,13 @@ struct Plan {
   static constexpr int NpP = (Np + 3) & ~3;
   static constexpr uint32_t oGeo = oRS + (PML ? T * 6 * NpP * 4 : 0);
   static constexpr int TS = T * 6 * Np;               // floats of one staged field block
-  static constexpr uint32_t TSB = (TS * 4 + 15) & ~15;
+  // a staged block is the 16-byte-aligned cover of the element block: up to
+  // 8 bytes more at each end
+  static constexpr uint32_t TSB = ((TS * 4 + 15) & ~15) + 16;
   static constexpr uint32_t SET = (PML ? 4 : 2) * TSB;  // q, res (+ P, res of P)
   static constexpr uint32_t oST = oGeo + 2 * T * 28 * 4;  // two staging sets
   static constexpr uint32_t oMisc = oST + 2 * SET;
-  // misc: 8 mbarriers | TMEM slot | flags | tile source list (64) | cached
+  // misc: 10 mbarriers | TMEM slot | flags | tile source list (64) | cached
   // (batch, element) of the first 64 sources
   static constexpr uint32_t MISC_BYTES = 1024;
   // epilogue scratch: the node rows of the products copied out of TMEM so that
@@ -386,12 +395,13 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
   float* RS = reinterpret_cast<float*>(smem + PL::oRS);     // [T][6][NpP]
   float* geo = reinterpret_cast<float*>(smem + PL::oGeo);   // [2][T][28]: n,Fscale x4 | metric
   // mbarriers: products done [0] V_q, [1] volume + LIFT, [2] P_q; operands
-  // ready [3] fields, [4] flux, [5] (t, z); [6] final drain of the MMA warp
+  // ready [3] fields, [4] flux, [5] (t, z); [6] final drain of the MMA warp;
+  // [7], [8] staging set 0 / 1 landed
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + PL::oMisc);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + PL::oMisc + 64);
-  int* flags = reinterpret_cast<int*>(smem + PL::oMisc + 68);   // [0] source count
-  int* srcl = reinterpret_cast<int*>(smem + PL::oMisc + 80);
-  int* srcc = reinterpret_cast<int*>(smem + PL::oMisc + 336);   // [64][2] batch, element
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + PL::oMisc + 80);
+  int* flags = reinterpret_cast<int*>(smem + PL::oMisc + 84);   // [0] source count
+  int* srcl = reinterpret_cast<int*>(smem + PL::oMisc + 112);
+  int* srcc = reinterpret_cast<int*>(smem + PL::oMisc + 368);   // [64][2] batch, element
   constexpr int kSrcCache = 64;
   const float* tops = reinterpret_cast<const float*>(P.tcops);
   const unsigned char* Fmask = P.tabs;
@@ -431,7 +441,7 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
     srcc[2 * s + 1] = P.src[s].elem;
   }
   if (tid == 0) {
-    for (int i = 0; i < 7; ++i) mbar_init(saddr(mbar + i), i >= 3 && i <= 5 ? NW : 1);
+    for (int i = 0; i < 9; ++i) mbar_init(saddr(mbar + i), i >= 3 && i <= 5 ? NW : 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tmem_alloc(saddr(tmem_slot), PL::TMEM_COLS);
@@ -469,35 +479,52 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
 
   constexpr int FT = (T * NF + kTcThreads - 1) / kTcThreads;   // flux tasks per thread
 
-  // copies of one tile's contiguous field blocks into staging set `set`
-  auto stage_tile = [&](int tile, int set) {
+  // A tile's contiguous field blocks (E,H and its register; P and its
+  // register in PML tiles) in global memory, and where each lands in staging
+  // set `set`: a block is copied as its 16-byte-aligned cover, so its first
+  // value sits (address mod 16) bytes into the buffer.  (The library's
+  // buffers end with spare bytes, so a cover never leaves its allocation.)
+  constexpr int NBLK = PML ? 4 : 2;
+  auto tile_blocks = [&](int tile, const float* (&g)[4]) {
     const int b = tile / tiles_per_batch;
     const int t0 = (tile - b * tiles_per_batch) * T;
-    const int ne = min(T, P.n_elem - t0);
-    const int eg0 = P.e_begin + t0;
-    const int nval = ne * 6 * Np;
-    unsigned char* st = smem + PL::oST + set * PL::SET;
-    float* sq = reinterpret_cast<float*>(st);
-    float* sr = reinterpret_cast<float*>(st + PL::TSB);
-    const float* gq = P.qin + (int64_t)b * P.strideQ + (int64_t)eg0 * 6 * Np;
-    const float* gr = P.resq + (int64_t)b * P.strideQ + (int64_t)eg0 * 6 * Np;
-    for (int idx = tid; idx < nval; idx += kTcThreads) {
-      cp_async4(sq + idx, gq + idx);
-      cp_async4(sr + idx, gr + idx);
-    }
-    if (PML) {
-      float* sp = reinterpret_cast<float*>(st + 2 * PL::TSB);
-      float* srp = reinterpret_cast<float*>(st + 3 * PL::TSB);
-      const float* gp = P.p + (int64_t)b * P.strideP + (int64_t)(eg0 - P.K0) * 6 * Np;
-      const float* grp = P.resp + (int64_t)b * P.strideP + (int64_t)(eg0 - P.K0) * 6 * Np;
-      for (int idx = tid; idx < nval; idx += kTcThreads) {
-        cp_async4(sp + idx, gp + idx);
-        cp_async4(srp + idx, grp + idx);
-      }
-    }
+    const int64_t oq = (int64_t)b * P.strideQ + (int64_t)(P.e_begin + t0) * 6 * Np;
+    const int64_t op = (int64_t)b * P.strideP + (int64_t)(P.e_begin + t0 - P.K0) * 6 * Np;
+    g[0] = P.qin + oq;
+    g[1] = P.resq + oq;
+    g[2] = PML ? P.p + op : nullptr;
+    g[3] = PML ? P.resp + op : nullptr;
   };
-  if (!mma_warp && (int)blockIdx.x < ntiles) stage_tile(blockIdx.x, 0);
-  asm volatile("cp.async.commit_group;" ::: "memory");
+  auto staged = [&](int set, int a, const float* g) {
+    return reinterpret_cast<float*>(smem + PL::oST + set * PL::SET + a * PL::TSB +
+                                    (reinterpret_cast<uintptr_t>(g) & 15));
+  };
+  // one thread issues the copies; they complete on staging barrier 7 + set
+  auto stage_tile = [&](int tile, int set) {
+    const float* g[4];
+    tile_blocks(tile, g);
+    const int b = tile / tiles_per_batch;
+    const int ne = min(T, P.n_elem - (tile - b * tiles_per_batch) * T);
+    const uint32_t nbytes = ne * 6 * Np * 4;
+    uint32_t lo[4], len[4], total = 0;
+#pragma unroll
+    for (int a = 0; a < NBLK; ++a) {
+      const uintptr_t s0 = reinterpret_cast<uintptr_t>(g[a]);
+      lo[a] = static_cast<uint32_t>(s0 & 15);
+      len[a] = (lo[a] + nbytes + 15) & ~15u;
+      total += len[a];
+    }
+    const uint32_t bar = saddr(mbar + 7 + set);
+    fence_async_smem();   // the buffers' earlier reads come before the copies' writes
+    mbar_expect_tx(bar, total);
+#pragma unroll
+    for (int a = 0; a < NBLK; ++a)
+      bulk_g2s(sbase + PL::oST + set * PL::SET + a * PL::TSB,
+               reinterpret_cast<const unsigned char*>(g[a]) - lo[a], len[a], bar);
+  };
+  int n_staged = 0, n_landed = 0;   // staging copies issued / waited for
+  if (tid == 0 && (int)blockIdx.x < ntiles) stage_tile(blockIdx.x, 0);
+  if ((int)blockIdx.x < ntiles) ++n_staged;
 
   // per-tile scattered loads (neighbour traces, sigma samples, geometry),
   // issued one tile ahead so their latency overlaps the previous tile's work
@@ -675,16 +702,19 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
   for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x, ++it) {
     const int set = it & 1;
     const int next = tile + gridDim.x;
-    unsigned char* stg = smem + PL::oST + set * PL::SET;
-    float* SQ = reinterpret_cast<float*>(stg);
-    float* SR = reinterpret_cast<float*>(stg + PL::TSB);
-    float* SP = reinterpret_cast<float*>(stg + 2 * PL::TSB);
-    float* SRP = reinterpret_cast<float*>(stg + 3 * PL::TSB);
+    const float* gblk[4];
+    tile_blocks(tile, gblk);
+    float* SQ = staged(set, 0, gblk[0]);
+    float* SR = staged(set, 1, gblk[1]);
+    float* SP = PML ? staged(set, 2, gblk[2]) : nullptr;
+    float* SRP = PML ? staged(set, 3, gblk[3]) : nullptr;
     float* geo = reinterpret_cast<float*>(smem + PL::oGeo) + set * T * 28;
     float* geo_next = reinterpret_cast<float*>(smem + PL::oGeo) + (set ^ 1) * T * 28;
     // the next tile's blocks stream in while this one is processed
-    if (next < ntiles) stage_tile(next, set ^ 1);
-    asm volatile("cp.async.commit_group;" ::: "memory");
+    if (next < ntiles) {
+      if (tid == 0) stage_tile(next, set ^ 1);
+      ++n_staged;
+    }
     const int b = tile / tiles_per_batch;
     const int t0 = (tile - b * tiles_per_batch) * T;
     const int ne = min(T, P.n_elem - t0);
@@ -700,8 +730,11 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
       load_nbr_idx(next, nbv, codev);   // consumed after this tile's flux
       load_geo_raw(next, nv, mv, matv);
     }
-    asm volatile("cp.async.wait_group 1;" ::: "memory");   // this tile's copies landed
-    cbar_sync(kTcThreads);
+    {   // this tile's copies landed (staging use it of set it & 1)
+      const bool ok = mbar_wait(saddr(mbar + 7 + set), (it >> 1) & 1);
+      if (!cbar_and(kTcThreads, ok)) { failed = true; break; }
+      ++n_landed;
+    }
     for (int s = tid; s < P.nsrc; s += kTcThreads) {
       const int sb = s < kSrcCache ? srcc[2 * s] : P.src[s].batch;
       const int se = s < kSrcCache ? srcc[2 * s + 1] : P.src[s].elem;
@@ -1002,7 +1035,10 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
     fence_after();
   }
 
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  // staging copies still in flight (the loop ended early) land before the
+  // block's shared memory is released
+  if (tid == 0)
+    for (int k = n_landed; k < n_staged; ++k) mbar_wait(saddr(mbar + 7 + (k & 1)), (k >> 1) & 1);
   if (failed && tid == 0) atomicExch(P.err, 1);
   }   // compute warps
   fence_before();
