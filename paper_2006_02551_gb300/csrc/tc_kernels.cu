@@ -320,8 +320,9 @@ struct Plan {
   static constexpr uint32_t oST = oGeo + 2 * T * 28 * 4;  // two staging sets
   static constexpr uint32_t oMisc = oST + 2 * SET;
   // misc: 10 mbarriers | TMEM slot | flags | tile source list (64) | cached
-  // (batch, element) of the first 64 sources
-  static constexpr uint32_t MISC_BYTES = 1024;
+  // (batch, element) of the first 64 sources | face tables (Fmask, fperm)
+  static constexpr uint32_t oTabs = 896;
+  static constexpr uint32_t MISC_BYTES = (oTabs + 100 * Nfp + 15) & ~15u;
   // epilogue scratch: the node rows of the products copied out of TMEM so that
   // every warp can share the per-node work.  PML: the volume/LIFT columns go
   // to the field-operand buffers (free once the first products are done), the
@@ -404,8 +405,11 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
   int* srcc = reinterpret_cast<int*>(smem + PL::oMisc + 368);   // [64][2] batch, element
   constexpr int kSrcCache = 64;
   const float* tops = reinterpret_cast<const float*>(P.tcops);
-  const unsigned char* Fmask = P.tabs;
-  const unsigned char* fperm = P.tabs + NF;
+  // face-node tables, copied to shared memory in the prologue: Fmask [NF],
+  // fperm [4][24][Nfp]
+  unsigned char* tabs_s = smem + PL::oMisc + PL::oTabs;
+  const unsigned char* Fmask = tabs_s;
+  const unsigned char* fperm = tabs_s + NF;
 
   // ---- prologue: zero the operand buffers, stage the operators
   for (uint32_t i = tid; i < PL::oGeo / 16; i += kAll)
@@ -440,6 +444,7 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
     srcc[2 * s] = P.src[s].batch;
     srcc[2 * s + 1] = P.src[s].elem;
   }
+  for (int i = tid; i < 100 * Nfp; i += kAll) tabs_s[i] = P.tabs[i];
   if (tid == 0) {
     for (int i = 0; i < 9; ++i) mbar_init(saddr(mbar + i), i >= 3 && i <= 5 ? NW : 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -499,7 +504,9 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
     return reinterpret_cast<float*>(smem + PL::oST + set * PL::SET + a * PL::TSB +
                                     (reinterpret_cast<uintptr_t>(g) & 15));
   };
-  // one thread issues the copies; they complete on staging barrier 7 + set
+  // the MMA thread issues the copies (tile k of this block into set k & 1,
+  // once the compute warps have signalled operands of tile k - 1, i.e. have
+  // finished with tile k - 2); they complete on staging barrier 7 + set
   auto stage_tile = [&](int tile, int set) {
     const float* g[4];
     tile_blocks(tile, g);
@@ -522,9 +529,6 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
       bulk_g2s(sbase + PL::oST + set * PL::SET + a * PL::TSB,
                reinterpret_cast<const unsigned char*>(g[a]) - lo[a], len[a], bar);
   };
-  int n_staged = 0, n_landed = 0;   // staging copies issued / waited for
-  if (tid == 0 && (int)blockIdx.x < ntiles) stage_tile(blockIdx.x, 0);
-  if ((int)blockIdx.x < ntiles) ++n_staged;
 
   // per-tile scattered loads (neighbour traces, sigma samples, geometry),
   // issued one tile ahead so their latency overlaps the previous tile's work
@@ -645,7 +649,13 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
       bool withhold = false;
       if (P.inject && (int)blockIdx.x < ntiles && *reinterpret_cast<volatile int*>(P.inject))
         withhold = atomicExch(P.inject, 0) != 0;
-      for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      int last_k[2] = {-1, -1};   // latest staging index issued into set 0 / 1
+      if ((int)blockIdx.x < ntiles) {
+        stage_tile(blockIdx.x, 0);
+        last_k[0] = 0;
+      }
+      int mit = 0;
+      for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++mit) {
         if (!wait_ready(0)) { mfail = true; break; }
         if (PML) {   // V_q first: the quadrature epilogue waits for it alone
           for (int t = 0; t < PL::VQT; ++t)   // rows 128 t .. 128 t + 127
@@ -662,6 +672,11 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
                           PL::SBO_V),
                 make_desc(sbase + PL::oBF + 2 * PL::LB * k, PL::LB, PL::SBB_V), idV, k > 0);
         issued = true;
+        // the compute warps are past tile mit - 1: its staging set takes tile mit + 1
+        if (tile + (int)gridDim.x < ntiles) {
+          stage_tile(tile + gridDim.x, (mit + 1) & 1);
+          last_k[(mit + 1) & 1] = mit + 1;
+        }
         if (!wait_ready(1)) { mfail = true; break; }
         for (int k = 0; k < NFK / KS; ++k)
           mma(tmem + PL::cL, make_desc(sbase + PL::oL + 256 * k, 128, PL::SBO_L),
@@ -677,6 +692,9 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
         }
       }
       if (mfail) atomicExch(P.err, 1);
+      // the staging copies this thread issued land before the memory is released
+      for (int s2 = 0; s2 < 2; ++s2)
+        if (last_k[s2] >= 0) mbar_wait(saddr(mbar + 7 + s2), (last_k[s2] >> 1) & 1);
       // every product this thread issued completes before the memory is released
       if (issued) {
         mma_commit(saddr(mbar + 6));
@@ -710,11 +728,6 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
     float* SRP = PML ? staged(set, 3, gblk[3]) : nullptr;
     float* geo = reinterpret_cast<float*>(smem + PL::oGeo) + set * T * 28;
     float* geo_next = reinterpret_cast<float*>(smem + PL::oGeo) + (set ^ 1) * T * 28;
-    // the next tile's blocks stream in while this one is processed
-    if (next < ntiles) {
-      if (tid == 0) stage_tile(next, set ^ 1);
-      ++n_staged;
-    }
     const int b = tile / tiles_per_batch;
     const int t0 = (tile - b * tiles_per_batch) * T;
     const int ne = min(T, P.n_elem - t0);
@@ -733,7 +746,6 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
     {   // this tile's copies landed (staging use it of set it & 1)
       const bool ok = mbar_wait(saddr(mbar + 7 + set), (it >> 1) & 1);
       if (!cbar_and(kTcThreads, ok)) { failed = true; break; }
-      ++n_landed;
     }
     for (int s = tid; s < P.nsrc; s += kTcThreads) {
       const int sb = s < kSrcCache ? srcc[2 * s] : P.src[s].batch;
@@ -809,8 +821,9 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
       const float cHx = ny * dHz - nz * dHy, cHy = nz * dHx - nx * dHz, cHz = nx * dHy - ny * dHx;
       const float cEx = ny * dEz - nz * dEy, cEy = nz * dEx - nx * dEz, cEz = nx * dEy - ny * dEx;
       const float al = (float)P.alpha;
-      const float YM = 1.f / ZM, YP = 1.f / ZP;
-      const float sH = fsc / (ZM + ZP), sE = fsc / (YM + YP);
+      // fast division (relative error ~1e-7, far below the operand rounding)
+      const float YM = __fdividef(1.f, ZM), YP = __fdividef(1.f, ZP);
+      const float sH = __fdividef(fsc, ZM + ZP), sE = __fdividef(fsc, YM + YP);
       float fo[6];
       fo[0] = sH * (ZP * cHx - al * (nx * ndE - dEx));
       fo[1] = sH * (ZP * cHy - al * (ny * ndE - dEy));
@@ -1035,10 +1048,6 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
     fence_after();
   }
 
-  // staging copies still in flight (the loop ended early) land before the
-  // block's shared memory is released
-  if (tid == 0)
-    for (int k = n_landed; k < n_staged; ++k) mbar_wait(saddr(mbar + 7 + (k & 1)), (k >> 1) & 1);
   if (failed && tid == 0) atomicExch(P.err, 1);
   }   // compute warps
   fence_before();
