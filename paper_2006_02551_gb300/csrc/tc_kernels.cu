@@ -1128,6 +1128,14 @@ cudaError_t launch_tc_bf(int N, bool pml, const StageParams<float>& P, int nb, c
 
 cudaError_t launch_stage_tc(int N, bool pml, const StageParams<float>& P, int nb, cudaStream_t s,
                             bool bf16) {
+  // the kernels stage element blocks as bulk copies of their 16-byte-aligned
+  // cover, sized for blocks that start 0 or 8 bytes past a boundary: every
+  // field buffer must start on a 16-byte boundary
+  const uintptr_t a = reinterpret_cast<uintptr_t>(P.qin) | reinterpret_cast<uintptr_t>(P.qout) |
+                      reinterpret_cast<uintptr_t>(P.resq) |
+                      (pml ? reinterpret_cast<uintptr_t>(P.p) | reinterpret_cast<uintptr_t>(P.resp)
+                           : 0);
+  if (a & 15) return cudaErrorMisalignedAddress;
   return bf16 ? launch_tc_bf<true>(N, pml, P, nb, s) : launch_tc_bf<false>(N, pml, P, nb, s);
 }
 
