@@ -43,8 +43,8 @@ FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (no measured figure available)
 # ncu --set full capture of the small case of the benchmark recipe (summary
 # and command in profiles/tc_stage_kernels_cube24_n4_full.md), valid for the
 # kernel source it was taken on (sha256 of csrc/tc_kernels.cu)
-TC_PML_TRAFFIC = {"sha256": "441175909e75301bacc4fc388fa8c496c8341c44d8a79963edef4987c41fb6ad",
-                  "bytes_per_pml_element": {"tf32": 7585.0, "bf16": 7614.0}, "N": 4}
+TC_PML_TRAFFIC = {"sha256": "5c10c6dbb7f780aeacaa8a09c746996ff9fccf51005c4844ac3bb53c19b138ad",
+                  "bytes_per_pml_element": {"tf32": 7631.0, "bf16": 7552.0}, "N": 4}
 
 
 def tc_pml_traffic(K1, N, precision):
