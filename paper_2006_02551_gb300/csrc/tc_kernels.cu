@@ -316,8 +316,18 @@ struct Plan {
   // a staged block is the 16-byte-aligned cover of the element block: up to
   // 8 bytes more at each end
   static constexpr uint32_t TSB = ((TS * 4 + 15) & ~15) + 16;
-  static constexpr uint32_t SET = (PML ? 4 : 2) * TSB;  // q, res (+ P, res of P)
-  static constexpr uint32_t oST = oGeo + 2 * T * 28 * 4;  // two staging sets
+  // a staging set: q, res (+ P, res of P), then the tile's geometry blocks as
+  // stored in global memory (covers again): unit normal and Fscale [T][4][4]
+  // floats, metric [T][9] doubles, 1/eps, 1/mu, Z [T][3] floats
+  static constexpr uint32_t GFN = ((T * 64 + 15) & ~15) + 16;
+  static constexpr uint32_t GMET = ((T * 72 + 15) & ~15) + 16;
+  static constexpr uint32_t GMAT = ((T * 12 + 15) & ~15) + 16;
+  static constexpr uint32_t oSFN = (PML ? 4 : 2) * TSB;   // offsets within a set
+  static constexpr uint32_t oSMET = oSFN + GFN;
+  static constexpr uint32_t oSMAT = oSMET + GMET;
+  static constexpr uint32_t SET = oSMAT + GMAT;
+  // the current tile's metric (9) and 1/eps, 1/mu in float [T][12]
+  static constexpr uint32_t oST = oGeo + ((T * 12 * 4 + 15) & ~15u);  // two staging sets
   static constexpr uint32_t oMisc = oST + 2 * SET;
   // misc: 10 mbarriers | TMEM slot | flags | tile source list (64) | cached
   // (batch, element) of the first 64 sources | face tables (Fmask, fperm)
@@ -412,7 +422,7 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
   const int quad = warp & 3, grp = warp >> 2;   // TMEM lane quadrant, element group
   const uint32_t sbase = saddr(smem);
   float* RS = reinterpret_cast<float*>(smem + PL::oRS);     // [T][6][NpP]
-  float* geo = reinterpret_cast<float*>(smem + PL::oGeo);   // [2][T][28]: n,Fscale x4 | metric
+  float* geoM = reinterpret_cast<float*>(smem + PL::oGeo);  // [T][12]: metric | 1/eps, 1/mu
   // mbarriers: products done [0] V_q, [1] volume + LIFT, [2] P_q; operands
   // ready [3] fields, [4] flux, [5] (t, z); [6] final drain of the MMA warp;
   // [7], [8] staging set 0 / 1 landed
@@ -529,23 +539,45 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
     const float* g[4];
     tile_blocks(tile, g);
     const int b = tile / tiles_per_batch;
-    const int ne = min(T, P.n_elem - (tile - b * tiles_per_batch) * T);
-    const uint32_t nbytes = ne * 6 * Np * 4;
-    uint32_t lo[4], len[4], total = 0;
+    const int t0 = tile - b * tiles_per_batch;
+    const int ne = min(T, P.n_elem - t0 * T);
+    const int eg0 = P.e_begin + t0 * T;
+    constexpr int NB = NBLK + 3;
+    const unsigned char* src[NB];
+    uint32_t bytes[NB], dst[NB];
 #pragma unroll
     for (int a = 0; a < NBLK; ++a) {
-      const uintptr_t s0 = reinterpret_cast<uintptr_t>(g[a]);
-      lo[a] = static_cast<uint32_t>(s0 & 15);
-      len[a] = (lo[a] + nbytes + 15) & ~15u;
+      src[a] = reinterpret_cast<const unsigned char*>(g[a]);
+      bytes[a] = ne * 6 * Np * 4;
+      dst[a] = a * PL::TSB;
+    }
+    src[NBLK] = reinterpret_cast<const unsigned char*>(P.fnrm + (int64_t)eg0 * 16);
+    bytes[NBLK] = ne * 64;
+    dst[NBLK] = PL::oSFN;
+    src[NBLK + 1] = reinterpret_cast<const unsigned char*>(P.geo + (int64_t)eg0 * 9);
+    bytes[NBLK + 1] = ne * 72;
+    dst[NBLK + 1] = PL::oSMET;
+    src[NBLK + 2] = reinterpret_cast<const unsigned char*>(P.mat + (int64_t)eg0 * 3);
+    bytes[NBLK + 2] = ne * 12;
+    dst[NBLK + 2] = PL::oSMAT;
+    uint32_t lo[NB], len[NB], total = 0;
+#pragma unroll
+    for (int a = 0; a < NB; ++a) {
+      lo[a] = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(src[a]) & 15);
+      len[a] = (lo[a] + bytes[a] + 15) & ~15u;
       total += len[a];
     }
     const uint32_t bar = saddr(mbar + 7 + set);
     fence_async_smem();   // the buffers' earlier reads come before the copies' writes
     mbar_expect_tx(bar, total);
 #pragma unroll
-    for (int a = 0; a < NBLK; ++a)
-      bulk_g2s(sbase + PL::oST + set * PL::SET + a * PL::TSB,
-               reinterpret_cast<const unsigned char*>(g[a]) - lo[a], len[a], bar);
+    for (int a = 0; a < NB; ++a)
+      bulk_g2s(sbase + PL::oST + set * PL::SET + dst[a], src[a] - lo[a], len[a], bar);
+  };
+  // a staged geometry block of set `set` (offset `o` within the set) whose
+  // global copy starts at g
+  auto staged_at = [&](int set, uint32_t o, const void* g) {
+    return smem + PL::oST + set * PL::SET + o + (reinterpret_cast<uintptr_t>(g) & 15);
   };
 
   // per-tile scattered loads (neighbour traces, sigma samples, geometry),
@@ -617,32 +649,7 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
       }
     }
   };
-  // geometry and material of a tile: raw loads first, arithmetic later.
-  // Thread tid < 4 ne handles face tid&3 of element tid>>2, tid < 9 ne one
-  // metric entry, tid < 3 ne one material entry.
-  static_assert(16 * T <= kTcThreads, "one geometry item per thread");
-  // geometry and material of a tile, loaded a tile ahead and stored after
-  // this tile's flux: normal and Fscale (16 per element), metric (9), 1/eps,
-  // 1/mu, Z (3); thread tid carries at most one item of each
-  auto load_geo_raw = [&](int tile, float& nv, double& mv, float& matv) {
-    const int b = tile / tiles_per_batch;
-    const int t0 = (tile - b * tiles_per_batch) * T;
-    const int ne = min(T, P.n_elem - t0);
-    const int eg0 = P.e_begin + t0;
-    if (tid < ne * 16) nv = P.fnrm[(int64_t)eg0 * 16 + tid];
-    if (tid < ne * 9) mv = P.geo[(int64_t)eg0 * 9 + tid];
-    if (tid < ne * 3) matv = P.mat[eg0 * 3 + tid];
-  };
-  // layout per element (28 floats): n, Fscale of the 4 faces | metric (9) |
-  // 1/eps, 1/mu, Z
-  auto store_geo = [&](int tile, float nv, double mv, float matv, float* gb) {
-    const int b = tile / tiles_per_batch;
-    const int t0 = (tile - b * tiles_per_batch) * T;
-    const int ne = min(T, P.n_elem - t0);
-    if (tid < ne * 16) gb[(tid >> 4) * 28 + (tid & 15)] = nv;
-    if (tid < ne * 9) gb[(tid / 9) * 28 + 16 + tid % 9] = (float)mv;
-    if (tid < ne * 3) gb[(tid / 3) * 28 + 25 + tid % 3] = matv;
-  };
+  static_assert(9 * T <= kTcThreads, "one metric entry per thread");
   if (mma_warp) {
     // ---- issuing warpgroup: lane 0 of its first warp issues every product
     // of every tile of this block.  With SPLIT it first hands registers to
@@ -730,14 +737,10 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
   float Ep[FT][3], Hp[FT][3], ZPv[FT];
   int nbv[FT], codev[FT];
   float sgv[PML ? EH : 1][VQT][3];
-  float nv = 0.f, matv = 0.f;
-  double mv = 0.0;
   if ((int)blockIdx.x < ntiles) {
     load_nbr_idx(blockIdx.x, nbv, codev);
     load_nbr_val(blockIdx.x, nbv, codev, Ep, Hp, ZPv);
     load_sig(blockIdx.x, sgv);
-    load_geo_raw(blockIdx.x, nv, mv, matv);
-    store_geo(blockIdx.x, nv, mv, matv, geo);
   }
 
   int it = 0;
@@ -750,8 +753,6 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
     float* SR = staged(set, 1, gblk[1]);
     float* SP = PML ? staged(set, 2, gblk[2]) : nullptr;
     float* SRP = PML ? staged(set, 3, gblk[3]) : nullptr;
-    float* geo = reinterpret_cast<float*>(smem + PL::oGeo) + set * T * 28;
-    float* geo_next = reinterpret_cast<float*>(smem + PL::oGeo) + (set ^ 1) * T * 28;
     const int b = tile / tiles_per_batch;
     const int t0 = (tile - b * tiles_per_batch) * T;
     const int ne = min(T, P.n_elem - t0);
@@ -765,12 +766,19 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
     if (tid == 0) flags[0] = 0;
     if (next < ntiles) {
       load_nbr_idx(next, nbv, codev);   // consumed after this tile's flux
-      load_geo_raw(next, nv, mv, matv);
     }
     {   // this tile's copies landed (staging use it of set it & 1)
       const bool ok = mbar_wait(saddr(mbar + 7 + set), (it >> 1) & 1);
       if (!cbar_and(kTcThreads, ok)) { failed = true; break; }
     }
+    // this tile's staged geometry: normal and Fscale [T][4][4], metric
+    // [T][9] (double), 1/eps, 1/mu, Z [T][3]
+    const float* fn_s =
+        reinterpret_cast<const float*>(staged_at(set, PL::oSFN, P.fnrm + (int64_t)eg0 * 16));
+    const double* met_s =
+        reinterpret_cast<const double*>(staged_at(set, PL::oSMET, P.geo + (int64_t)eg0 * 9));
+    const float* mat_s =
+        reinterpret_cast<const float*>(staged_at(set, PL::oSMAT, P.mat + (int64_t)eg0 * 3));
     for (int s = tid; s < P.nsrc; s += kTcThreads) {
       const int sb = s < kSrcCache ? srcc[2 * s] : P.src[s].batch;
       const int se = s < kSrcCache ? srcc[2 * s + 1] : P.src[s].elem;
@@ -822,13 +830,13 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
       const int e = task / NF, fm = task - e * NF;
       const int f = fm / Nfp;
       const int ni = Fmask[fm];
-      const float* nn = geo + e * 28 + f * 4;
+      const float* nn = fn_s + e * 16 + f * 4;
       const float nx = nn[0], ny = nn[1], nz = nn[2], fsc = nn[3];
       const float* sq = SQ + e * 6 * Np + ni;
       float Em[3], Hm[3], Eo[3], Ho[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) { Em[c] = sq[c * Np]; Hm[c] = sq[(3 + c) * Np]; }
-      const float ZM = geo[e * 28 + 27];
+      const float ZM = mat_s[e * 3 + 2];
       float ZP = ZPv[u];
       if (ZP < 0.f) {   // perfect electric conductor: mirror state
         ZP = ZM;
@@ -860,10 +868,11 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
         put_op<BF>(smem + PL::oBFL + PL::ofs(e * 6 + c, fm, PL::SBB_L, PL::LB), fo[c]);
     }
     signal_ready(4);   // LIFT operand
-    if (next < ntiles) {
-      load_nbr_val(next, nbv, codev, Ep, Hp, ZPv);
-      store_geo(next, nv, mv, matv, geo_next);
-    }
+    if (next < ntiles) load_nbr_val(next, nbv, codev, Ep, Hp, ZPv);
+    // this tile's metric and 1/eps, 1/mu in float for the curl epilogue (read
+    // after the next barrier; the previous tile's readers are past the last)
+    if (tid < ne * 9) geoM[(tid / 9) * 12 + tid % 9] = (float)met_s[tid];
+    if (tid < ne * 2) geoM[(tid >> 1) * 12 + 9 + (tid & 1)] = mat_s[(tid >> 1) * 3 + (tid & 1)];
 
     if (PML) {
       if (!wait_bar(0)) { failed = true; break; }   // V_q product
@@ -970,7 +979,7 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
       const int e = task / Np, i = task - e * Np;
       const int eg = eg0 + e;
       const float* dv = DV + e * 24 * Np + i;
-      const float* g = geo + e * 28 + 16;
+      const float* g = geoM + e * 12;
       float dx[6], dy[6], dz[6];
 #pragma unroll
       for (int c = 0; c < 6; ++c) {
@@ -1000,7 +1009,7 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
 #pragma unroll
         for (int c = 0; c < 3; ++c) CH[c] -= jt * (float)sd.dir[c] * w;
       }
-      const float ie = geo[e * 28 + 25], im = geo[e * 28 + 26];
+      const float ie = geoM[e * 12 + 9], im = geoM[e * 12 + 10];
       const float rhs[6] = {ie * CH[0], ie * CH[1], ie * CH[2], -im * CE[0], -im * CE[1], -im * CE[2]};
       if (!PML) {
 #pragma unroll
