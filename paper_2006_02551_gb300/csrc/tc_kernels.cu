@@ -171,6 +171,29 @@ __device__ __forceinline__ void tld6(uint32_t taddr, float* v) {
 }
 
 // 6 consecutive columns at each of two / four column addresses, one wait
+// the same at two pairs of column addresses (two elements), one wait
+__device__ __forceinline__ void tld_6x2x2(uint32_t a0, uint32_t a1, uint32_t b0, uint32_t b1,
+                                          float* v) {
+  uint32_t r[24];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%24];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%4, %5}, [%25];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%6, %7, %8, %9}, [%26];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%10, %11}, [%27];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%12, %13, %14, %15}, [%28];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%16, %17}, [%29];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%18, %19, %20, %21}, [%30];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%22, %23}, [%31];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23])
+      : "r"(a0), "r"(a0 + 4), "r"(a1), "r"(a1 + 4), "r"(b0), "r"(b0 + 4), "r"(b1), "r"(b1 + 4)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 24; ++i) v[i] = __uint_as_float(r[i]);
+}
 __device__ __forceinline__ void tld_6x2(uint32_t a0, uint32_t a1, float* v) {
   uint32_t r[12];
   asm volatile(
@@ -880,15 +903,32 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
       {
         const float ie0 = 1.f / (float)P.eps0;
 #pragma unroll
-        for (int t = 0; t < VQT; ++t)         // V_q product t: points 128 t + lane row
+        for (int t = 0; t < VQT; ++t) {       // V_q product t: points 128 t + lane row
+        const uint32_t cq = PL::cVq + t * PL::NQ;
+        // this lane's columns of the group's elements grp + NGRP k (warp-uniform);
+        // with two per group both loads are in flight before one wait
+        float vv[EH][12];
+        if constexpr (EH == 2 && 2 * NGRP == T) {
+          float w[24];
+          tld_6x2x2(tmem + lane_base + cq + grp * 6, tmem + lane_base + cq + 6 * T + grp * 6,
+                    tmem + lane_base + cq + (grp + NGRP) * 6,
+                    tmem + lane_base + cq + 6 * T + (grp + NGRP) * 6, w);
 #pragma unroll
-        for (int k = 0; k < EH; ++k) {       // warp-uniform loop over this group's elements
+          for (int i = 0; i < 12; ++i) { vv[0][i] = w[i]; vv[1][i] = w[12 + i]; }
+        } else {
+#pragma unroll
+          for (int k = 0; k < EH; ++k) {
+            const int e = grp + NGRP * k;
+            if (e < T)
+              tld_6x2(tmem + lane_base + cq + e * 6, tmem + lane_base + cq + 6 * T + e * 6, vv[k]);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < EH; ++k) {
           const int q = 128 * t + quad * 32 + lane;   // quadrature point of this lane
           const int e = grp + NGRP * k;
           if (e >= T) break;
-          float v[12];
-          const uint32_t cq = PL::cVq + t * PL::NQ;
-          tld_6x2(tmem + lane_base + cq + e * 6, tmem + lane_base + cq + 6 * T + e * 6, v);
+          const float* v = vv[k];
           if (e >= ne || q >= NqK) continue;
           const float* sg = sgv[k][t];
           float o[12];
@@ -910,6 +950,7 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
             put_op<BF>(smem + PL::oBTZ + PL::ofs(6 * T + e * 6 + c, q, PL::SBB_Q, PL::LB), o[6 + c]);
           }
         }
+        }   // t
       }
       if (next < ntiles) load_sig(next, sgv);
       signal_ready(5);   // P_q operand; the product overlaps the epilogue below
