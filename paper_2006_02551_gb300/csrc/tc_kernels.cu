@@ -965,8 +965,12 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
       if (quad * 32 < 3 * Np) {
         const int L = quad * 32 + lane;
         const int d = L / Np, i = L - d * Np;
-        for (int e = grp; e < T; e += NGRP) {
-          float v[12];   // derivative d of the 6 components | LIFT of the 6 components
+        // derivative d of the 6 components | LIFT of the 6 components
+#pragma unroll
+        for (int k = 0; k < EH; ++k) {
+          const int e = grp + NGRP * k;
+          if (e >= T) break;
+          float v[12];
           if (quad * 32 < Np)
             tld_6x2(tmem + lane_base + PL::cV + e * 6, tmem + lane_base + PL::cL + e * 6, v);
           else
@@ -1075,7 +1079,10 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
       float* DP = reinterpret_cast<float*>(smem + PL::oDP);   // [T][12][Np]
       if (quad * 32 < Np) {
         const int i = quad * 32 + lane;
-        for (int e = grp; e < T; e += NGRP) {
+#pragma unroll
+        for (int k = 0; k < EH; ++k) {
+          const int e = grp + NGRP * k;
+          if (e >= T) break;
           float v[12];   // s | rhs of P
           tld_6x2(tmem + lane_base + PL::cPq + e * 6, tmem + lane_base + PL::cPq + 6 * T + e * 6, v);
           if (e >= ne || i >= Np) continue;
