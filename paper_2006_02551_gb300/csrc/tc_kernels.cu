@@ -930,15 +930,17 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
           if (e >= T) break;
           const float* v = vv[k];
           if (e >= ne || q >= NqK) continue;
-          const float* sg = sgv[k][t];
+          // sigma_u / eps0 at this point
+          const float sg[3] = {sgv[k][t][0] * ie0, sgv[k][t][1] * ie0, sgv[k][t][2] * ie0};
           float o[12];
 #pragma unroll
           for (int u = 0; u < 3; ++u) {
             const float su = sg[u], sv = sg[(u + 1) % 3], sw = sg[(u + 2) % 3];
-            // eq. 9 with kappa = 1: a = 1, b = (sv + sw - su)/eps0, c = sv sw/eps0^2 - b su/eps0
-            const float bc = (sv + sw - su) * ie0;
-            const float cc = sv * sw * ie0 * ie0 - bc * su * ie0;
-            const float dd = su * ie0;
+            // eq. 9 with kappa = 1 in terms of s = sigma / eps0: a = 1,
+            // b = sv + sw - su, c = sv sw - b su
+            const float bc = sv + sw - su;
+            const float cc = sv * sw - bc * su;
+            const float dd = su;
             o[u] = bc * v[u] + cc * v[6 + u];
             o[3 + u] = bc * v[3 + u] + cc * v[9 + u];
             o[6 + u] = v[u] - dd * v[6 + u];
