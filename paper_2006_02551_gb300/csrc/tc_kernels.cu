@@ -403,14 +403,15 @@ struct Plan {
 // "operand ready" mbarriers the compute warps arrive on and commits each
 // product to a "product done" mbarrier, so that issuing the products (about a
 // hundred cycles per instruction for the issuing thread) stays off the compute
-// warps' path.  Usually one issuing warp, and the launch holds every thread to
-// 96 registers (5 warps per scheduler).  Two-per-SM BF16 PML blocks (SPLIT)
-// use a whole issuing warpgroup that hands most of its registers to the
-// compute warps (setmaxnreg): measured faster there, slower elsewhere.
+// warps' path.  Blocks that share an SM two at a time (BF16 PML, and the
+// non-PML class) use a whole issuing warpgroup that hands most of its
+// registers to the compute warps (setmaxnreg, SPLIT), which removes their
+// spills.  One-per-SM blocks keep one issuing warp and 96 registers per
+// thread (5 warps per scheduler): the split measured slower there.
 template <int N, bool PML, bool BF>
 struct TcWarps {
   static constexpr bool ONE = Plan<N, PML, BF>::ONE;   // one block per SM
-  static constexpr bool SPLIT = Plan<N, PML, BF>::PAIR;
+  static constexpr bool SPLIT = Plan<N, PML, BF>::PAIR || (!PML && !ONE);
   static constexpr int compute = ONE ? 16 : 8;
   static constexpr int issue = SPLIT ? 4 : 1;
   static constexpr int threads = 32 * (compute + issue);
