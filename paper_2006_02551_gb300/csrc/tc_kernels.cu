@@ -396,37 +396,34 @@ struct Plan {
   static_assert(bytes <= 227 * 1024, "shared memory");
 };
 
-// Warp roles.  The compute warps (16 in a TF32 PML block, one block per SM; 8
-// in a BF16 PML or a non-PML block, two per SM) stage the tile, build the operands, compute the
-// flux and run the epilogues; they synchronise among themselves on a named
-// barrier.  Extra issuing warps follow them: lane 0 of the first waits for
-// "operand ready" mbarriers the compute warps arrive on and commits each
-// product to a "product done" mbarrier, so that issuing the products (about a
-// hundred cycles per instruction for the issuing thread) stays off the compute
-// warps' path.  Blocks that share an SM two at a time (BF16 PML, and the
-// non-PML class) use a whole issuing warpgroup that hands most of its
-// registers to the compute warps (setmaxnreg, SPLIT), which removes their
-// spills.  One-per-SM blocks keep one issuing warp and 96 registers per
-// thread (5 warps per scheduler): the split measured slower there.
+// Warp roles.  The compute warps (16 in a one-per-SM block: TF32 PML and the
+// N = 5 BF16 blocks; 8 in a block that shares its SM with another) stage the
+// tile, build the operands, compute the flux and run the epilogues; they
+// synchronise among themselves on a named barrier.  An issuing warpgroup
+// follows them: lane 0 of its first warp waits for "operand ready" mbarriers
+// the compute warps arrive on and commits each product to a "product done"
+// mbarrier, so that issuing the products (about a hundred cycles per
+// instruction for the issuing thread) stays off the compute warps' path.  The
+// issuing warpgroup keeps 24 registers per thread and hands the rest of its
+// launch allocation to the compute warps (setmaxnreg), which removes their
+// spills (the launch holds every thread to the share of 5 or 6 warps per
+// scheduler).
 template <int N, bool PML, bool BF>
 struct TcWarps {
   static constexpr bool ONE = Plan<N, PML, BF>::ONE;   // one block per SM
-  static constexpr bool SPLIT = Plan<N, PML, BF>::PAIR || (!PML && !ONE);
   static constexpr int compute = ONE ? 16 : 8;
-  static constexpr int issue = SPLIT ? 4 : 1;
+  static constexpr int issue = 4;
   static constexpr int threads = 32 * (compute + issue);
-  // registers per thread at launch and, with SPLIT, of the issuing warpgroup
-  // after it gives its share away and of the compute warps after they take it
-  // (the block's launch allocation covers both: checked against the compiled
-  // kernel before the first launch)
-  static constexpr int launch_regs = SPLIT ? 80 : 96;
+  // registers per thread at launch, of the issuing warpgroup after it gives
+  // its share away, and of the compute warps after they take it (the block's
+  // launch allocation covers both: checked against the compiled kernel before
+  // the first launch)
+  static constexpr int launch_regs = ONE ? 96 : 80;
   static constexpr int issue_regs = 24;
   static constexpr int compute_regs =
-      SPLIT ? ((threads * launch_regs - 32 * issue * issue_regs) / (32 * compute)) & ~7
-            : launch_regs;
+      ((threads * launch_regs - 32 * issue * issue_regs) / (32 * compute)) & ~7;
   static_assert(compute_regs >= launch_regs && compute_regs <= 256, "register split");
-  static_assert(!SPLIT || 32 * compute * compute_regs + 32 * issue * issue_regs <=
-                              threads * launch_regs,
+  static_assert(32 * compute * compute_regs + 32 * issue * issue_regs <= threads * launch_regs,
                 "register split within the launch allocation");
 };
 
@@ -442,7 +439,7 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
   constexpr int NpK = PL::NpK, NFK = PL::NFK, NqK = PL::NqK;
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const bool mma_warp = warp >= NW;   // the issuing warp(s)
+  const bool mma_warp = warp >= NW;   // the issuing warpgroup
   const int quad = warp & 3, grp = warp >> 2;   // TMEM lane quadrant, element group
   const uint32_t sbase = saddr(smem);
   float* RS = reinterpret_cast<float*>(smem + PL::oRS);     // [T][6][NpP]
@@ -676,10 +673,9 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
   static_assert(9 * T <= kTcThreads, "one metric entry per thread");
   if (mma_warp) {
     // ---- issuing warpgroup: lane 0 of its first warp issues every product
-    // of every tile of this block.  With SPLIT it first hands registers to
-    // the compute warps (warpgroup-uniform).
-    if constexpr (TcWarps<N, PML, BF>::SPLIT)
-      asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(TcWarps<N, PML, BF>::issue_regs));
+    // of every tile of this block.  It first hands registers to the compute
+    // warps (warpgroup-uniform).
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(TcWarps<N, PML, BF>::issue_regs));
     if (warp == NW && lane == 0) {
       uint32_t rph[3] = {0, 0, 0};   // parity of the operand-ready barriers 3, 4, 5
       bool issued = false, mfail = false;
@@ -756,8 +752,7 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
     }
     __syncwarp();
   } else {
-  if constexpr (TcWarps<N, PML, BF>::SPLIT)
-    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(TcWarps<N, PML, BF>::compute_regs));
+  asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(TcWarps<N, PML, BF>::compute_regs));
   float Ep[FT][3], Hp[FT][3], ZPv[FT];
   int nbv[FT], codev[FT];
   float sgv[PML ? EH : 1][VQT][3];
@@ -1143,17 +1138,15 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
 template <int N, bool PML, bool BF>
 cudaError_t configure_n() {
   using TW = TcWarps<N, PML, BF>;
-  // with SPLIT the compute warps' setmaxnreg.inc waits until the block's
-  // launch allocation can cover the split: refuse a build whose compiled
-  // register count would leave it short
-  if constexpr (TW::SPLIT) {
-    cudaFuncAttributes fa{};
-    cudaError_t e = cudaFuncGetAttributes(&fa, tc_stage_kernel<N, PML, BF>);
-    if (e != cudaSuccess) return e;
-    if ((long)fa.numRegs * TW::threads <
-        32L * TW::compute * TW::compute_regs + 32L * TW::issue * TW::issue_regs)
-      return cudaErrorInvalidConfiguration;
-  }
+  // the compute warps' setmaxnreg.inc waits until the block's launch
+  // allocation can cover the split: refuse a build whose compiled register
+  // count would leave it short
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaFuncGetAttributes(&fa, tc_stage_kernel<N, PML, BF>);
+  if (e != cudaSuccess) return e;
+  if ((long)fa.numRegs * TW::threads <
+      32L * TW::compute * TW::compute_regs + 32L * TW::issue * TW::issue_regs)
+    return cudaErrorInvalidConfiguration;
   return cudaFuncSetAttribute(tc_stage_kernel<N, PML, BF>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)Plan<N, PML, BF>::bytes);
