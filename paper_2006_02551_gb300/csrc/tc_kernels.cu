@@ -813,29 +813,38 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
       constexpr int CW = PL::O::CW;
       constexpr int G4 = (Np + CW - 1) / CW;
       constexpr int NTASK = PL::ROWS_F * G4;
-      for (int task = tid; task < NTASK; task += kTcThreads) {
+      constexpr int NIT = (NTASK + kTcThreads - 1) / kTcThreads;
+      // every task's values are loaded before any is converted and stored,
+      // so the loads of a thread's tasks overlap
+      float x[NIT][8];
+#pragma unroll
+      for (int it2 = 0; it2 < NIT; ++it2) {
+        const int task = tid + it2 * kTcThreads;
         const int row = task / G4, g = task - row * G4;
         const int rr = PML && row >= 6 * T ? row - 6 * T : row;
-        if (rr >= ne * 6) continue;
+        const bool live = task < NTASK && rr < ne * 6;
         const float* src = (PML && row >= 6 * T ? SP : SQ) + rr * Np + CW * g;
+#pragma unroll
+        for (int h = 0; h < CW; ++h) x[it2][h] = live && CW * g + h < Np ? src[h] : 0.f;
+      }
+#pragma unroll
+      for (int it2 = 0; it2 < NIT; ++it2) {
+        const int task = tid + it2 * kTcThreads;
+        const int row = task / G4, g = task - row * G4;
+        const int rr = PML && row >= 6 * T ? row - 6 * T : row;
+        if (task >= NTASK || rr >= ne * 6) continue;
         unsigned char* dst = smem + PL::oBF + PL::ofs(row, CW * g, PL::SBB_V, PL::LB);
         if constexpr (BF) {
           uint32_t w[4];
 #pragma unroll
           for (int h = 0; h < 4; ++h) {
-            const float a = CW * g + 2 * h < Np ? src[2 * h] : 0.f;
-            const float b = CW * g + 2 * h + 1 < Np ? src[2 * h + 1] : 0.f;
-            const __nv_bfloat162 v2 = __floats2bfloat162_rn(a, b);
+            const __nv_bfloat162 v2 = __floats2bfloat162_rn(x[it2][2 * h], x[it2][2 * h + 1]);
             w[h] = *reinterpret_cast<const uint32_t*>(&v2);
           }
           *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
         } else {
-          float4 v;
-          v.x = to_tf32(src[0]);
-          v.y = CW * g + 1 < Np ? to_tf32(src[1]) : 0.f;
-          v.z = CW * g + 2 < Np ? to_tf32(src[2]) : 0.f;
-          v.w = CW * g + 3 < Np ? to_tf32(src[3]) : 0.f;
-          *reinterpret_cast<float4*>(dst) = v;
+          *reinterpret_cast<float4*>(dst) = make_float4(to_tf32(x[it2][0]), to_tf32(x[it2][1]),
+                                                        to_tf32(x[it2][2]), to_tf32(x[it2][3]));
         }
       }
     }
