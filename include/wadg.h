@@ -253,6 +253,17 @@ wadg_status wadg_mesh_info(const wadg_ctx* ctx, int64_t* K, int64_t* K_pml, int3
 /* Block until all work issued by ctx has finished. */
 wadg_status wadg_synchronize(wadg_ctx* ctx);
 
+/* Cap on the device bytes this context may hold (0, the default: no cap).
+ * Every device buffer the library allocates for the context counts: state,
+ * geometry, coefficients, operators, probe records, adjoint buffers.  A
+ * request that would take the context past the cap fails before any device
+ * call, as an exhausted device would: the call returns WADG_ENOMEM and the
+ * context stays usable (raise the cap and repeat the call).  A cap below
+ * what is already held blocks further allocations only.  held_out (may be
+ * NULL) receives the bytes the context holds now.  Allocations of a group
+ * (wadg_group_*) do not count.  (The paper has no counterpart.) */
+wadg_status wadg_set_memory_limit(wadg_ctx* ctx, size_t bytes, size_t* held_out);
+
 /* Failure-detection test aid for the TF32 and BF16 contexts, the ones whose
  * kernels wait on device-side signals (the mbarriers between the tensor-core
  * issuing thread and the compute warps).  Every such wait gives up after

@@ -44,9 +44,23 @@ struct RkC {
 };
 const RkC kRkC;
 
+// Device bytes a context may hold (limit 0: no cap) and holds.  The
+// allocations made while one of the context's entry points runs count
+// against it (see BudgetScope).
+struct Budget {
+  size_t limit = 0, held = 0;
+};
+thread_local Budget* t_budget = nullptr;
+struct BudgetScope {
+  Budget* prev;
+  explicit BudgetScope(Budget* b) : prev(t_budget) { t_budget = b; }
+  ~BudgetScope() { t_budget = prev; }
+};
+
 struct DevPtr {
   void* p = nullptr;
   size_t bytes = 0;
+  Budget* owner = nullptr;   // budget the bytes count against, if any
 };
 
 }  // namespace
@@ -86,6 +100,7 @@ struct wadg_ctx {
   DevPtr q[2], rq, p, rp, geo, fnrm, mat, nbr, code, sig, kap, ops, tabs, verts;
   DevPtr src, srcw, pr_elem, pr_ell, pr_out, obj, tdev, stepdev, flag, tcops, errflag;
   DevPtr stored;     // stored-matrix scheme: per PML element operators
+  Budget budget;     // device-memory cap (wadg_set_memory_limit)
   bool tc = false;   // tensor-core stage kernels (TF32 or BF16 operands)
   bool bf16 = false; // BF16 operands
   int cur = 0;
@@ -121,8 +136,10 @@ wadg_status fail(wadg_ctx* c, wadg_status s, const char* fmt, ...) {
 
 void dfree(DevPtr& d) {
   if (d.p) cudaFree(d.p);
+  if (d.p && d.owner) d.owner->held -= d.bytes;
   d.p = nullptr;
   d.bytes = 0;
+  d.owner = nullptr;
 }
 
 // Every device buffer ends with kSlack spare bytes: the tensor-core kernels
@@ -130,12 +147,21 @@ void dfree(DevPtr& d) {
 // end may pass a buffer's last value by up to 8 bytes.
 constexpr size_t kSlack = 64;
 
+// A request beyond the active budget's cap fails as the device would when out
+// of memory, before any device call.
 cudaError_t dalloc(DevPtr& d, size_t bytes) {
   dfree(d);
   if (bytes == 0) return cudaSuccess;
+  Budget* b = t_budget;
+  if (b && b->limit && b->held + bytes > b->limit) return cudaErrorMemoryAllocation;
   cudaError_t e = cudaMalloc(&d.p, bytes + kSlack);
-  if (e == cudaSuccess) d.bytes = bytes;
-  else d.p = nullptr;
+  if (e == cudaSuccess) {
+    d.bytes = bytes;
+    d.owner = b;
+    if (b) b->held += bytes;
+  } else {
+    d.p = nullptr;
+  }
   return e;
 }
 
@@ -755,6 +781,7 @@ wadg_status wadg_create(int N, wadg_precision prec, int32_t n_batch, int device,
   if (cudaSetDevice(device) != cudaSuccess)
     return fail(nullptr, WADG_ECUDA, "cudaSetDevice(%d) failed", device);
   ctx = new wadg_ctx();
+  BudgetScope budget_scope(&ctx->budget);
   ctx->N = N;
   ctx->prec = prec;
   ctx->nb = n_batch;
@@ -836,6 +863,7 @@ wadg_status wadg_set_mesh_periodic(wadg_ctx* ctx, int64_t nv, const double* vxyz
   if (nv < 4 || K < 1 || !vxyz || !etov) return fail(ctx, WADG_EINVAL, "empty mesh");
   if (K > (int64_t)1 << 30) return fail(ctx, WADG_EINVAL, "too many elements");
   cudaSetDevice(ctx->device);
+  BudgetScope budget_scope(&ctx->budget);
   for (int64_t i = 0; i < 4 * K; ++i)
     if (etov[i] < 0 || etov[i] >= nv)
       return fail(ctx, WADG_EINVAL, "etov[%lld] = %lld out of range", (long long)i,
@@ -957,6 +985,7 @@ wadg_status wadg_set_materials(wadg_ctx* ctx, const double* eps_r, const double*
   wadg_status s = need_mesh(ctx);
   if (s != WADG_OK) return s;
   cudaSetDevice(ctx->device);
+  BudgetScope budget_scope(&ctx->budget);
   for (int64_t k = 0; k < ctx->K; ++k)
     if ((eps_r && !(eps_r[k] > 0)) || (mu_r && !(mu_r[k] > 0)))
       return fail(ctx, WADG_EINVAL, "material of element %lld not positive", (long long)k);
@@ -972,6 +1001,7 @@ wadg_status wadg_set_pml_profile(wadg_ctx* ctx, const wadg_pml_profile* prof,
   wadg_status s = need_mesh(ctx);
   if (s != WADG_OK) return s;
   cudaSetDevice(ctx->device);
+  BudgetScope budget_scope(&ctx->budget);
   if (scheme != WADG_PML_WAA && scheme != WADG_PML_STORED && scheme != WADG_PML_EC)
     return fail(ctx, WADG_EINVAL, "unknown PML scheme %d", (int)scheme);
   if (prof) {
@@ -1006,6 +1036,7 @@ wadg_status wadg_set_sources(wadg_ctx* ctx, int32_t n, const wadg_dipole* src) {
   wadg_status s = need_mesh(ctx);
   if (s != WADG_OK) return s;
   cudaSetDevice(ctx->device);
+  BudgetScope budget_scope(&ctx->budget);
   if (n < 0 || (n > 0 && !src)) return fail(ctx, WADG_EINVAL, "bad source list");
   for (int i = 0; i < n; ++i) {
     if (src[i].batch < 0 || src[i].batch >= ctx->nb)
@@ -1020,6 +1051,7 @@ wadg_status wadg_set_probes(wadg_ctx* ctx, int32_t n, const double* xyz) {
   wadg_status s = need_mesh(ctx);
   if (s != WADG_OK) return s;
   cudaSetDevice(ctx->device);
+  BudgetScope budget_scope(&ctx->budget);
   if (n < 0 || (n > 0 && !xyz)) return fail(ctx, WADG_EINVAL, "bad probe list");
   ctx->probe_user.assign(xyz, xyz + 3 * (size_t)n);
   return upload_probes(ctx);
@@ -1029,6 +1061,7 @@ wadg_status wadg_set_state(wadg_ctx* ctx, const double* q, double t) {
   wadg_status s = need_mesh(ctx);
   if (s != WADG_OK) return s;
   cudaSetDevice(ctx->device);
+  BudgetScope budget_scope(&ctx->budget);
   s = ctx->rs == 8 ? set_state_t<double>(ctx, q) : set_state_t<float>(ctx, q);
   if (s == WADG_OK) ctx->t = t;
   return s;
@@ -1063,6 +1096,7 @@ wadg_status wadg_run_steps(wadg_ctx* ctx, int64_t nsteps, double dt, double* pro
   if (nsteps < 0 || !(dt > 0)) return fail(ctx, WADG_EINVAL, "bad nsteps or dt");
   if (nsteps == 0) return WADG_OK;
   cudaSetDevice(ctx->device);
+  BudgetScope budget_scope(&ctx->budget);
   const int64_t chunk = std::min<int64_t>(nsteps, 4096);
   const size_t need = (size_t)chunk * ctx->nprobe * 6 * ctx->nb * 8;
   if (ctx->nprobe > 0 && ctx->pr_out.bytes < need) {
@@ -1332,6 +1366,7 @@ wadg_status wadg_adjoint(wadg_ctx* ctx, int64_t nsteps, double dt, int32_t ckpt_
     return fail(ctx, WADG_EUNSUPPORTED, "the adjoint is built for the weight-adjusted scheme");
   if (ctx->nprobe < 1) return fail(ctx, WADG_ESTATE, "the objective needs probes");
   cudaSetDevice(ctx->device);
+  BudgetScope budget_scope(&ctx->budget);
   const size_t need = (size_t)std::min<int64_t>(ckpt_every, 4096) * ctx->nprobe * 6 * ctx->nb * 8;
   if (ctx->pr_out.bytes < need) {
     invalidate_graphs(ctx);
@@ -1389,6 +1424,13 @@ wadg_status wadg_synchronize(wadg_ctx* ctx) {
   if (!ctx) return fail(nullptr, WADG_EINVAL, "null context");
   cudaSetDevice(ctx->device);
   CK(cudaStreamSynchronize(ctx->stream));
+  return WADG_OK;
+}
+
+wadg_status wadg_set_memory_limit(wadg_ctx* ctx, size_t bytes, size_t* held_out) {
+  if (!ctx) return fail(nullptr, WADG_EINVAL, "null context");
+  ctx->budget.limit = bytes;
+  if (held_out) *held_out = ctx->budget.held;
   return WADG_OK;
 }
 

@@ -66,6 +66,7 @@ _SIG = {
     "wadg_mesh_info": [_P, _I64, _I64, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
     "wadg_synchronize": [_P],
     "wadg_arm_wait_timeout": [_P],
+    "wadg_set_memory_limit": [_P, C.c_size_t, _P],
     "wadg_reference_operator": [C.c_int, C.c_int, _D, C.c_int64, _I64],
     "wadg_group_create": [C.c_int32, C.POINTER(_P), C.POINTER(_P)],
     "wadg_group_destroy": [_P],
@@ -273,6 +274,14 @@ class Solver:
 
     def synchronize(self):
         self._c(self.lib.wadg_synchronize(self.ctx))
+
+    def set_memory_limit(self, nbytes):
+        """Cap the device bytes this context may hold (0: no cap); returns
+        the bytes it holds now.  Allocations past the cap raise
+        WadgError(ENOMEM) and leave the context usable."""
+        held = C.c_size_t()
+        self._c(self.lib.wadg_set_memory_limit(self.ctx, nbytes, C.byref(held)))
+        return held.value
 
     def arm_wait_timeout(self):
         """Failure-detection test aid (TF32/BF16 contexts): the next

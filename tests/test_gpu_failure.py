@@ -80,3 +80,76 @@ def test_cuda_core_contexts_have_no_waits_to_arm():
         s, _, _ = make_pair(2, 2, 0.1, 1, PML3, precision)
         assert _status_of(s.arm_wait_timeout) == WADG_EUNSUPPORTED
         s.close()
+
+
+def test_memory_limit_reports_enomem_and_context_recovers():
+    """An allocation past the context's cap fails as an exhausted device
+    would (ENOMEM, no device call made), and the context then completes the
+    same work once the cap is raised, bit for bit as a context never capped."""
+    from paper_2006_02551_gb300 import Solver
+    from paper_2006_02551_gb300.wadg import WADG_ENOMEM
+    from synthetic import cube_tet_mesh
+
+    v, e = cube_tet_mesh(3, 0.1, 2)
+
+    def setup(s):
+        s.set_mesh(v, e)
+        s.set_pml(PML3)
+        s.set_state(None, 0.0)
+
+    ref = Solver(2, "fp32")
+    setup(ref)
+    ref.set_probes([(0.1, 0.2, 0.3)])
+    dt = ref.stable_dt(0.5)
+    rec_ref = ref.run_steps(4, dt)
+    q_ref, _ = ref.get_state()
+    ref.close()
+
+    s = Solver(2, "fp32")
+    held0 = s.set_memory_limit(0)
+    assert held0 > 0                                   # operators, counters
+    s.set_memory_limit(held0 + 1024)
+    assert _status_of(lambda: s.set_mesh(v, e)) == WADG_ENOMEM
+    s.set_memory_limit(0)
+    setup(s)
+    held1 = s.set_memory_limit(0)
+    assert held1 > held0
+    s.set_memory_limit(held1)                          # cap at what is held
+    # probe records are allocated by the first run: refuse them, then allow
+    assert _status_of(lambda: s.set_probes([(0.1, 0.2, 0.3)])) == WADG_ENOMEM
+    s.set_memory_limit(0)
+    s.set_probes([(0.1, 0.2, 0.3)])
+    s.set_memory_limit(s.set_memory_limit(0))          # cap at what is held
+    assert _status_of(lambda: s.run_steps(4, dt)) == WADG_ENOMEM
+    s.set_memory_limit(0)
+    s.set_state(None, 0.0)
+    rec = s.run_steps(4, dt)
+    q, _ = s.get_state()
+    assert np.array_equal(q, q_ref)
+    assert np.array_equal(rec, rec_ref)
+    # the adjoint's buffers count too
+    s.set_memory_limit(s.set_memory_limit(0))
+    assert _status_of(lambda: s.adjoint(4, dt)) == WADG_ENOMEM
+    s.set_memory_limit(0)
+    s.set_state(None, 0.0)
+    J, *_ = s.adjoint(4, dt)
+    assert np.all(np.isfinite(J))
+    s.close()
+
+
+def test_malformed_input_is_rejected():
+    from paper_2006_02551_gb300 import Solver
+    from paper_2006_02551_gb300.wadg import WADG_EINVAL
+    from synthetic import Dipole
+
+    s = Solver(1, "fp64")
+    v = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [0, 0, -1], [0, 0, 2.0]])
+    # three positively oriented tetrahedra on one face: not a manifold mesh
+    bad = np.array([[0, 1, 2, 3], [0, 2, 1, 4], [0, 1, 2, 5]])
+    assert _status_of(lambda: s.set_mesh(v, bad)) == WADG_EINVAL
+    assert _status_of(lambda: s.set_mesh(v, np.array([[0, 1, 2, 6]]))) == WADG_EINVAL
+    s.set_mesh(v, bad[:2])                      # two elements, one shared face
+    assert _status_of(lambda: s.set_materials(np.array([1.0, -1.0]), None)) == WADG_EINVAL
+    src = Dipole(x=(0.1, 0.1, 0.1), dir=(0.0, 0.0, 1.0), t0=1.0, width=0.0)
+    assert _status_of(lambda: s.set_sources([src])) == WADG_EINVAL
+    s.close()
