@@ -61,11 +61,12 @@ def rel_err(q_lib, states_ref, mask):
 
 
 def make_pair(N, n_hex, jitter, seed, prof, precision="fp64", sources=(), probes=(),
-              eps=None, mu=None, n_batch=1, scheme="waa"):
+              eps=None, mu=None, n_batch=1, scheme="waa", mesh=None):
     """scheme: "waa", "stored" (eqs. 10-13) or "ec" (the weight-adjusted
-    scheme with the profile evaluated at each element's centroid)."""
+    scheme with the profile evaluated at each element's centroid).  mesh:
+    (vertices, elements) to use instead of the jittered cube."""
     from paper_2006_02551_gb300 import Solver
-    v, e = cube_tet_mesh(n_hex, jitter, seed)
+    v, e = cube_tet_mesh(n_hex, jitter, seed) if mesh is None else mesh
     sim = Simulation(N, v, e, profile=prof, eps=eps, mu=mu, sources=sources,
                      probes=probes, n_batch=n_batch,
                      scheme="stored" if scheme == "stored" else "waa")

@@ -24,9 +24,10 @@ def built():
     build.build()
 
 
-def increment_error(N, prof, n_hex=4, stage=0, sources=(), n_batch=1, seed=0):
-    s, sim, mask = make_pair(N, n_hex, 0.15, seed, prof, "tf32", sources=sources,
-                             n_batch=n_batch)
+def increment_error(N, prof, n_hex=4, stage=0, sources=(), n_batch=1, seed=0,
+                    precision="tf32", mesh=None):
+    s, sim, mask = make_pair(N, n_hex, 0.15, seed, prof, precision, sources=sources,
+                             n_batch=n_batch, mesh=mesh)
     st = random_states(sim.K, sim.Np, n_batch, 300 + seed, mask)
     q0 = to_lib(st)
     s.set_state(q0, 0.0)
@@ -99,3 +100,28 @@ def test_tc_rejects_kappa_and_high_order():
         s.set_pml(PmlProfile(kappa_max=2.0))
     assert e.value.status == wadg.WADG_EUNSUPPORTED
     s.close()
+
+
+@pytest.mark.parametrize("precision,bound", [("tf32", 1e-2), ("bf16", 3e-2)])
+@pytest.mark.parametrize("drop", ["interior", "pml"])
+def test_tc_blocks_off_16_byte_boundaries(precision, bound, drop):
+    """Cube meshes have an even element count in each class, so every staged
+    E,H and P block starts on a 16-byte boundary.  Removing one element (its
+    faces become PEC walls, for the library and the oracle alike) makes the
+    PML class start at an odd element ("interior") or holds an odd number of
+    PML elements ("pml"); with two excitations the second one's blocks then
+    start 8 bytes past a boundary as well, which the staging copies cover.
+    (An element block is 24 N_p bytes: only an odd N_p, N = 4 here, leaves
+    blocks off the boundary; the geometry blocks are off it at any N.)"""
+    from synthetic import cube_tet_mesh
+    from tests.parity_util import pml_mask
+    v, e = cube_tet_mesh(4, 0.15, 0)
+    mask = pml_mask(v, e, PML3)
+    k = int(np.flatnonzero(mask if drop == "pml" else ~mask)[0])
+    e = np.delete(e, k, axis=0)
+    mask = pml_mask(v, e, PML3)
+    K1 = int(mask.sum())
+    K0 = len(e) - K1
+    assert (K0 % 2 == 1) if drop == "interior" else (K1 % 2 == 1)
+    err = increment_error(4, PML3, n_batch=2, precision=precision, mesh=(v, e))
+    assert err < bound, err
