@@ -43,8 +43,8 @@ FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (no measured figure available)
 # ncu --set full capture of the small case of the benchmark recipe (summary
 # and command in profiles/tc_stage_kernels_cube24_n4_full.md), valid for the
 # kernel source it was taken on (sha256 of csrc/tc_kernels.cu)
-TC_PML_TRAFFIC = {"sha256": "817acfa165c1487258cd88cbd4d145af8f10e73a6accb5d79ad14ebcd561340a",
-                  "bytes_per_pml_element": {"tf32": 7496.0, "bf16": 7526.0}, "N": 4}
+TC_PML_TRAFFIC = {"sha256": "5cfe46d2f115bc85c1d72ea3ba5e8be2e75c8fe060566677b5bc905d0eea0bae",
+                  "bytes_per_pml_element": {"tf32": 7487.0, "bf16": 7516.0}, "N": 4}
 
 
 def tc_pml_traffic(K1, N, precision):

@@ -17,6 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libwadg.so")
+# diagnostic build with device-side index checks (-DWADG_CHECKED)
+LIB_CHECKED = os.path.join(OUT_DIR, "libwadg_checked.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -47,23 +49,28 @@ def _stale(lib):
     return False
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not _stale(LIB):
-        return LIB
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Compile and link the library; checked=True builds the diagnostic
+    variant with device-side index checks (a separate file and object dir)."""
+    lib = LIB_CHECKED if checked else LIB
+    build_dir = BUILD_DIR + ("_checked" if checked else "")
+    extra = ["-DWADG_CHECKED"] if checked else []
+    if not force and not _stale(lib):
+        return lib
     cuda = _cuda_home()
     nvcc = os.path.join(cuda, "bin", "nvcc")
     os.makedirs(OUT_DIR, exist_ok=True)
-    os.makedirs(BUILD_DIR, exist_ok=True)
+    os.makedirs(build_dir, exist_ok=True)
     cu, cpp = _sources()
     inc = ["-I", CSRC, "-I", os.path.join(os.path.dirname(HERE), "include")]
     jobs = []
     for f in cu:
-        o = os.path.join(BUILD_DIR, f + ".o")
-        jobs.append([nvcc, ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
+        o = os.path.join(build_dir, f + ".o")
+        jobs.append([nvcc, ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", *extra,
                      "-Xptxas", "-v" if verbose else "-O3", *inc, "-c",
                      os.path.join(CSRC, f), "-o", o])
     for f in cpp:
-        o = os.path.join(BUILD_DIR, f + ".o")
+        o = os.path.join(build_dir, f + ".o")
         jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", *inc, "-c",
                      os.path.join(CSRC, f), "-o", o])
 
@@ -79,13 +86,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if r.returncode != 0:
             raise RuntimeError("compile failed: " + " ".join(cmd) + "\n" + r.stdout + r.stderr)
     objs = [cmd[cmd.index("-o") + 1] for cmd, _ in results]
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     link = [nvcc, ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(link, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed: " + r.stdout + r.stderr)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -692,7 +692,9 @@ wadg_status check_err_flag(wadg_ctx* ctx) {
   CK(cudaStreamSynchronize(ctx->stream));
   if (e) {
     CK(cudaMemset(ctx->errflag.p, 0, 4));
-    return fail(ctx, WADG_ETIMEOUT, "a tensor-core stage kernel gave up waiting for its products");
+    if (e & 1)
+      return fail(ctx, WADG_ETIMEOUT, "a tensor-core stage kernel gave up waiting for its products");
+    return fail(ctx, WADG_ECUDA, "a device index check failed (checked build): mesh tables corrupt");
   }
   return WADG_OK;
 }
@@ -1086,7 +1088,7 @@ wadg_status wadg_rk_stage(wadg_ctx* ctx, int stage, double t, double dt) {
   cudaSetDevice(ctx->device);
   s = ctx->rs == 8 ? issue_stage<double>(ctx, stage, dt, t, false)
                    : issue_stage<float>(ctx, stage, dt, t, false);
-  if (s != WADG_OK || !ctx->tc) return s;
+  if (s != WADG_OK) return s;
   return check_err_flag(ctx);
 }
 

@@ -24,6 +24,20 @@
 
 namespace wadg {
 
+// Checked builds (-DWADG_CHECKED, a diagnostic build of the library): index
+// checks before the scattered reads of the stage kernels record a violation
+// in the context's status word (value 2) and skip the read; in other builds
+// WADG_INDEX_OK is the constant true and costs nothing.
+#ifdef WADG_CHECKED
+__device__ __forceinline__ bool wadg_index_ok(bool ok, int* status) {
+  if (!ok) atomicOr(status, 2);
+  return ok;
+}
+#define WADG_INDEX_OK(cond, status) ::wadg::wadg_index_ok((cond), (status))
+#else
+#define WADG_INDEX_OK(cond, status) true
+#endif
+
 struct SrcDev {
   int elem;     // internal element id
   int batch;

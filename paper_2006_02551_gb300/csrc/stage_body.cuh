@@ -225,9 +225,11 @@ __device__ __forceinline__ void stage_body(const StageParams<Real>& P, unsigned 
     const Real ZM = P.mat[eg * 3 + 2];
     Real ZP = ZM;
     const int nb = P.nbr[eg * 4 + f];
-    if (nb >= 0) {
-      const int code = P.code[eg * 4 + f];
-      const int np2 = fperm[(f * 24 + code) * Nfp + m];
+    const int code = nb >= 0 ? P.code[eg * 4 + f] : 0;
+    const bool face_ok =
+        nb >= 0 && WADG_INDEX_OK(nb < P.strideQ / (6 * Np) && code < 24, P.err);
+    const int np2 = face_ok ? fperm[(f * 24 + code) * Nfp + m] : 0;
+    if (face_ok && WADG_INDEX_OK(np2 < Np, P.err)) {
       const Real* qn = qin + (int64_t)nb * 6 * Np + np2;
 #pragma unroll
       for (int c = 0; c < 3; ++c) { Ep[c] = qn[c * Np]; Hp[c] = qn[(3 + c) * Np]; }

@@ -639,7 +639,10 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
       if (task < ne * NF && nbv[u] >= 0) {
         const int fm = task % NF;
         const int f = fm / Nfp, m = fm - f * Nfp;
+        // checked builds: an index out of range leaves the PEC mirror in place
+        if (!WADG_INDEX_OK(nbv[u] < P.strideQ / (6 * Np) && codev[u] < 24, P.err)) continue;
         const int np2 = fperm[(f * 24 + codev[u]) * Nfp + m];
+        if (!WADG_INDEX_OK(np2 < Np, P.err)) continue;
         const float* qn = qin + (int64_t)nbv[u] * 6 * Np + np2;
 #pragma unroll
         for (int c = 0; c < 3; ++c) { Ep[u][c] = qn[c * Np]; Hp[u][c] = qn[(3 + c) * Np]; }

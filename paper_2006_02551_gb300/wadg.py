@@ -13,7 +13,9 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_lib", "libwadg.so")
+# WADG_LIB selects another build of the library (the checked diagnostic
+# build, _lib/libwadg_checked.so) for the whole process
+LIB_PATH = os.environ.get("WADG_LIB") or os.path.join(HERE, "_lib", "libwadg.so")
 
 WADG_OK, WADG_EINVAL, WADG_ENOMEM, WADG_ECUDA, WADG_ESTATE = 0, 1, 2, 3, 4
 WADG_ENOTFOUND, WADG_ETIMEOUT, WADG_ENONFINITE, WADG_EUNSUPPORTED = 5, 6, 7, 8
