@@ -5,7 +5,6 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
-#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -103,6 +102,15 @@ struct wadg_ctx {
   Budget budget;     // device-memory cap (wadg_set_memory_limit)
   bool tc = false;   // tensor-core stage kernels (TF32 or BF16 operands)
   bool bf16 = false; // BF16 operands
+  // Readiness of the device side.  ready: the per-element tables and the
+  // state buffers match the host mesh (the last rebuild completed).  src_ok,
+  // probes_ok: the source and probe tables match the current element order
+  // (the last upload of each completed).  A set-up call that fails part-way
+  // clears its flag, and every call that launches kernels or touches the
+  // state refuses (ESTATE) until the failed call has been repeated
+  // successfully, so no kernel ever sees a freed or half-built table.
+  bool ready = false;
+  bool src_ok = true, probes_ok = true;
   int cur = 0;
   int nsrc = 0, nprobe = 0;
   std::vector<wadg_dipole> src_user;
@@ -493,13 +501,19 @@ wadg_status rebuild_typed(wadg_ctx* ctx) {
 }
 
 wadg_status rebuild(wadg_ctx* ctx) {
-  return ctx->rs == 8 ? rebuild_typed<double>(ctx) : rebuild_typed<float>(ctx);
+  ctx->ready = false;
+  const wadg_status s = ctx->rs == 8 ? rebuild_typed<double>(ctx) : rebuild_typed<float>(ctx);
+  ctx->ready = s == WADG_OK;
+  return s;
 }
 
 template <typename Real>
 wadg_status upload_sources(wadg_ctx* ctx) {
   const int Np = ctx->ref.Np;
   invalidate_graphs(ctx);
+  // no source counts until the new tables are complete
+  ctx->nsrc = 0;
+  ctx->src_ok = false;
   std::vector<SrcDev> sd;
   std::vector<Real> w;
   for (const wadg_dipole& d : ctx->src_user) {
@@ -523,19 +537,22 @@ wadg_status upload_sources(wadg_ctx* ctx) {
       w.push_back((Real)(a / ctx->J_u[k]));
     }
   }
-  ctx->nsrc = (int)sd.size();
   CK(dalloc(ctx->src, sd.size() * sizeof(SrcDev)));
   CK(dalloc(ctx->srcw, w.size() * sizeof(Real)));
   if (!sd.empty()) {
     CK(cudaMemcpy(ctx->src.p, sd.data(), sd.size() * sizeof(SrcDev), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->srcw.p, w.data(), w.size() * sizeof(Real), cudaMemcpyHostToDevice));
   }
+  ctx->nsrc = (int)sd.size();
+  ctx->src_ok = true;
   return WADG_OK;
 }
 
 wadg_status upload_probes(wadg_ctx* ctx) {
-  const int Np = ctx->ref.Np;
   invalidate_graphs(ctx);
+  // no probe counts until the new tables are complete
+  ctx->nprobe = 0;
+  ctx->probes_ok = false;
   const int n = (int)(ctx->probe_user.size() / 3);
   std::vector<int> el;
   std::vector<double> ell;
@@ -548,14 +565,14 @@ wadg_status upload_probes(wadg_ctx* ctx) {
     std::vector<double> l = ctx->ref.lagrange_at(rst[0], rst[1], rst[2]);
     ell.insert(ell.end(), l.begin(), l.end());
   }
-  ctx->nprobe = n;
   CK(dalloc(ctx->pr_elem, el.size() * 4));
   CK(dalloc(ctx->pr_ell, ell.size() * 8));
   if (n) {
     CK(cudaMemcpy(ctx->pr_elem.p, el.data(), el.size() * 4, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->pr_ell.p, ell.data(), ell.size() * 8, cudaMemcpyHostToDevice));
   }
-  (void)Np;
+  ctx->nprobe = n;
+  ctx->probes_ok = true;
   return WADG_OK;
 }
 
@@ -702,6 +719,21 @@ wadg_status check_err_flag(wadg_ctx* ctx) {
 wadg_status need_mesh(wadg_ctx* ctx) {
   if (!ctx) return fail(nullptr, WADG_EINVAL, "null context");
   if (!ctx->has_mesh) return fail(ctx, WADG_ESTATE, "no mesh set");
+  return WADG_OK;
+}
+
+// every device table the stage, probe and state calls read is complete
+wadg_status need_ready(wadg_ctx* ctx) {
+  wadg_status s = need_mesh(ctx);
+  if (s != WADG_OK) return s;
+  if (!ctx->ready)
+    return fail(ctx, WADG_ESTATE,
+                "the device tables are incomplete after a failed set-up call: repeat "
+                "wadg_set_mesh, wadg_set_materials or wadg_set_pml_profile");
+  if (!ctx->src_ok)
+    return fail(ctx, WADG_ESTATE, "the sources are not mapped after a failed call: repeat wadg_set_sources");
+  if (!ctx->probes_ok)
+    return fail(ctx, WADG_ESTATE, "the probes are not mapped after a failed call: repeat wadg_set_probes");
   return WADG_OK;
 }
 
@@ -878,6 +910,12 @@ wadg_status wadg_set_mesh_periodic(wadg_ctx* ctx, int64_t nv, const double* vxyz
   // face keys use the periodic representatives of the vertices
   auto cv = [vcanon](int64_t v) { return vcanon ? vcanon[v] : v; };
   ctx->has_mesh = false;
+  ctx->ready = false;
+  // the point tables refer to the old element order: drop them
+  invalidate_graphs(ctx);
+  for (DevPtr* d : {&ctx->src, &ctx->srcw, &ctx->pr_elem, &ctx->pr_ell}) dfree(*d);
+  ctx->nsrc = ctx->nprobe = 0;
+  ctx->src_ok = ctx->probes_ok = true;
   ctx->K = K;
   ctx->nv = nv;
   ctx->vxyz.assign(vxyz, vxyz + 3 * nv);
@@ -1060,7 +1098,7 @@ wadg_status wadg_set_probes(wadg_ctx* ctx, int32_t n, const double* xyz) {
 }
 
 wadg_status wadg_set_state(wadg_ctx* ctx, const double* q, double t) {
-  wadg_status s = need_mesh(ctx);
+  wadg_status s = need_ready(ctx);
   if (s != WADG_OK) return s;
   cudaSetDevice(ctx->device);
   BudgetScope budget_scope(&ctx->budget);
@@ -1070,7 +1108,7 @@ wadg_status wadg_set_state(wadg_ctx* ctx, const double* q, double t) {
 }
 
 wadg_status wadg_get_state(wadg_ctx* ctx, double* q, double* t) {
-  wadg_status s = need_mesh(ctx);
+  wadg_status s = need_ready(ctx);
   if (s != WADG_OK) return s;
   cudaSetDevice(ctx->device);
   if (q) {
@@ -1085,6 +1123,7 @@ wadg_status wadg_rk_stage(wadg_ctx* ctx, int stage, double t, double dt) {
   wadg_status s = need_mesh(ctx);
   if (s != WADG_OK) return s;
   if (stage < 0 || stage > 4) return fail(ctx, WADG_EINVAL, "stage must be 0..4");
+  if ((s = need_ready(ctx)) != WADG_OK) return s;
   cudaSetDevice(ctx->device);
   s = ctx->rs == 8 ? issue_stage<double>(ctx, stage, dt, t, false)
                    : issue_stage<float>(ctx, stage, dt, t, false);
@@ -1093,7 +1132,7 @@ wadg_status wadg_rk_stage(wadg_ctx* ctx, int stage, double t, double dt) {
 }
 
 wadg_status wadg_run_steps(wadg_ctx* ctx, int64_t nsteps, double dt, double* probe_out) {
-  wadg_status s = need_mesh(ctx);
+  wadg_status s = need_ready(ctx);
   if (s != WADG_OK) return s;
   if (nsteps < 0 || !(dt > 0)) return fail(ctx, WADG_EINVAL, "bad nsteps or dt");
   if (nsteps == 0) return WADG_OK;
@@ -1144,7 +1183,7 @@ wadg_status wadg_run_steps(wadg_ctx* ctx, int64_t nsteps, double dt, double* pro
 }
 
 wadg_status wadg_profile_stage(wadg_ctx* ctx, int reps, double dt, double* ms_out) {
-  wadg_status s = need_mesh(ctx);
+  wadg_status s = need_ready(ctx);
   if (s != WADG_OK) return s;
   if (reps < 1 || !ms_out) return fail(ctx, WADG_EINVAL, "bad arguments");
   cudaSetDevice(ctx->device);
@@ -1359,7 +1398,7 @@ extern "C" {
 wadg_status wadg_adjoint(wadg_ctx* ctx, int64_t nsteps, double dt, int32_t ckpt_every,
                          double* J_out, double* dJ_deps, double* dJ_dsigma_max,
                          double* dJ_dp_sigma) {
-  wadg_status s = need_mesh(ctx);
+  wadg_status s = need_ready(ctx);
   if (s != WADG_OK) return s;
   if (nsteps < 1 || !(dt > 0) || ckpt_every < 1) return fail(ctx, WADG_EINVAL, "bad arguments");
   if (ctx->tc) return fail(ctx, WADG_EUNSUPPORTED, "the adjoint runs on the FP64/FP32 kernels");
@@ -1489,31 +1528,28 @@ const char* wadg_last_error(const wadg_ctx* ctx) {
 // of a chunk of steps before they are copied to the host -- in the file-scope
 // array below.  The array is part of the library image: every GPU that loads
 // the library holds its kNoAllocBytes until the process exits.  In host code
-// the array's name is only a stand-in for the device object; its device
-// address is looked up once per device with cudaGetSymbolAddress.
+// the array's name is only a stand-in for the device object; each call looks
+// up its device address on the current device with cudaGetSymbolAddress.
+// With lazy module loading the array's memory is committed when the module is
+// first used on a device, so the first call should come before any stream
+// capture.
 namespace {
 
 constexpr size_t kNoAllocBytes = size_t(16) << 20;   // 16 MiB per device
 constexpr size_t kNoAllocRecords = 256;               // offset of the probe records
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-std::mutex g_noalloc_mu;
-void* g_noalloc_addr[256] = {};   // device address of the array, per device ordinal
-
-// device address of the scratch array on ctx's device (which is current)
+// device address of the scratch array on ctx's device (which is current).
+// Looked up on every call rather than cached: the lookup is cheap once the
+// module is loaded, and an address kept from before a device reset or a
+// recreated primary context would be stale.
 wadg_status noalloc_scratch(wadg_ctx* ctx, unsigned char** out) {
-  if (ctx->device < 0 || ctx->device >= 256)
-    return fail(ctx, WADG_EINVAL, "device ordinal %d out of range", ctx->device);
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[ctx->device]) {
-    void* a = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&a, g_noalloc_scratch);
-    if (e != cudaSuccess || !a)
-      return fail(ctx, WADG_ECUDA, "cudaGetSymbolAddress of the step scratch: %s",
-                  cudaGetErrorString(e));
-    g_noalloc_addr[ctx->device] = a;
-  }
-  *out = static_cast<unsigned char*>(g_noalloc_addr[ctx->device]);
+  void* a = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&a, g_noalloc_scratch);
+  if (e != cudaSuccess || !a)
+    return fail(ctx, WADG_ECUDA, "cudaGetSymbolAddress of the step scratch: %s",
+                cudaGetErrorString(e));
+  *out = static_cast<unsigned char*>(a);
   return WADG_OK;
 }
 
@@ -1546,7 +1582,7 @@ wadg_status noalloc_stage(wadg_ctx* ctx, int stage, double dt, const double* tde
 
 extern "C" wadg_status wadg_run_steps_noalloc(wadg_ctx* ctx, int64_t nsteps, double dt,
                                               double* probe_out) {
-  wadg_status s = need_mesh(ctx);
+  wadg_status s = need_ready(ctx);
   if (s != WADG_OK) return s;
   if (nsteps < 0 || !(dt > 0)) return fail(ctx, WADG_EINVAL, "bad nsteps or dt");
   if (nsteps == 0) return WADG_OK;
@@ -1600,6 +1636,8 @@ extern "C" wadg_status wadg_run_steps_noalloc(wadg_ctx* ctx, int64_t nsteps, dou
     done += n;
   }
   ctx->t += nsteps * dt;
+  // a wait that gave up explains whatever the state holds: report it first
+  if ((s = check_err_flag(ctx)) != WADG_OK) return s;
   CK(cudaMemsetAsync(flag, 0, 4, ctx->stream));
   const int64_t nq = ctx->nb * ctx->K * 6 * ctx->ref.Np;
   if (ctx->rs == 8) CK(launch_check_finite<double>((const double*)ctx->q[ctx->cur].p, nq, flag, ctx->stream));
@@ -1608,7 +1646,7 @@ extern "C" wadg_status wadg_run_steps_noalloc(wadg_ctx* ctx, int64_t nsteps, dou
   CK(cudaMemcpyAsync(&hflag, flag, 4, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   if (hflag) return fail(ctx, WADG_ENONFINITE, "state became non-finite");
-  return check_err_flag(ctx);
+  return WADG_OK;
 }
 
 // ====================================================================== groups
@@ -1656,6 +1694,18 @@ wadg_status gfail(wadg_group* g, wadg_status s, const char* fmt, ...) {
       return gfail(g, e_ == cudaErrorMemoryAllocation ? WADG_ENOMEM : WADG_ECUDA,       \
                    "%s: %s", #call, cudaGetErrorString(e_));                            \
   } while (0)
+
+// every member's device tables are complete (no set-up call of a member
+// failed part-way since its last success)
+wadg_status group_members_ready(wadg_group* g) {
+  for (size_t c = 0; c < g->ctx.size(); ++c) {
+    const wadg_ctx* x = g->ctx[c];
+    if (!x->has_mesh || !x->ready || !x->src_ok || !x->probes_ok)
+      return gfail(g, WADG_ESTATE, "member %d has an incomplete set-up (a set-up call failed)",
+                   (int)c);
+  }
+  return WADG_OK;
+}
 
 void group_drop_graphs(wadg_group* g) {
   for (auto& x : g->graph)
@@ -1813,7 +1863,8 @@ wadg_status wadg_group_create(int32_t n, wadg_ctx* const* ctxs, wadg_group** out
   for (int i = 0; i < n; ++i) {
     wadg_ctx* x = ctxs[i];
     if (!x) return fail(nullptr, WADG_EINVAL, "null context %d", i);
-    if (!x->has_mesh) return fail(nullptr, WADG_ESTATE, "context %d has no mesh", i);
+    if (!x->has_mesh || !x->ready || !x->src_ok || !x->probes_ok)
+      return fail(nullptr, WADG_ESTATE, "context %d has no mesh or an incomplete set-up", i);
     if (x->prec != WADG_FP32 || x->tc)
       return fail(nullptr, WADG_EUNSUPPORTED, "groups run the FP32 CUDA-core kernels (context %d)", i);
     if (x->scheme == WADG_PML_STORED)
@@ -1858,6 +1909,7 @@ wadg_status wadg_group_destroy(wadg_group* g) {
 wadg_status wadg_group_autotune(wadg_group* g, const double* dt, int32_t reps, double* ms_out) {
   if (!g) return WADG_EINVAL;
   if (!dt || reps < 1) return gfail(g, WADG_EINVAL, "bad arguments");
+  if (wadg_status s0 = group_members_ready(g); s0 != WADG_OK) return s0;
   cudaSetDevice(g->device);
   group_drop_graphs(g);
   cudaEvent_t e0, e1;
@@ -1911,10 +1963,12 @@ wadg_status wadg_group_info(const wadg_group* g, int32_t* nblocks, int32_t* thre
 wadg_status wadg_group_run_steps(wadg_group* g, int64_t nsteps, const double* dt,
                                  double* const* probe_out) {
   if (!g) return WADG_EINVAL;
+  wadg_status s0;
   if (!dt || nsteps < 0) return gfail(g, WADG_EINVAL, "bad arguments");
   for (size_t c = 0; c < g->ctx.size(); ++c)
     if (!(dt[c] > 0)) return gfail(g, WADG_EINVAL, "dt of member %d must be > 0", (int)c);
   if (nsteps == 0) return WADG_OK;
+  if ((s0 = group_members_ready(g)) != WADG_OK) return s0;
   cudaSetDevice(g->device);
   const int64_t chunk = std::min<int64_t>(nsteps, 4096);
   for (wadg_ctx* x : g->ctx) {

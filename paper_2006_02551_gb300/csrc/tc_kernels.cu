@@ -743,15 +743,17 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
           mma_commit(saddr(mbar + 2));
         }
       }
-      if (mfail) atomicExch(P.err, 1);
       // the staging copies this thread issued land before the memory is released
       for (int s2 = 0; s2 < 2; ++s2)
-        if (last_k[s2] >= 0) mbar_wait(saddr(mbar + 7 + s2), (last_k[s2] >> 1) & 1);
+        if (last_k[s2] >= 0 && !mbar_wait(saddr(mbar + 7 + s2), (last_k[s2] >> 1) & 1))
+          mfail = true;
       // every product this thread issued completes before the memory is released
       if (issued) {
         mma_commit(saddr(mbar + 6));
-        mbar_wait(saddr(mbar + 6), 0);
+        if (!mbar_wait(saddr(mbar + 6), 0)) mfail = true;
       }
+      // a wait that gave up, here or above, is reported as a timeout
+      if (mfail) atomicExch(P.err, 1);
     }
     __syncwarp();
   } else {

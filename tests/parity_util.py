@@ -60,6 +60,27 @@ def rel_err(q_lib, states_ref, mask):
     return float(np.linalg.norm(d) / max(np.linalg.norm(ref[sel]), 1e-300))
 
 
+def increment_err(q_lib, states_ref, q0, mask):
+    """Relative L2 error of the stage increment: |q_lib - q_ref| / |q_ref - q0|
+    over E, H of all elements and P of PML elements.  One stage changes the
+    state by a fraction of its size (dt |f(q)| against |q|), so dividing by the
+    increment, not by the state, keeps the bound on the part the kernel
+    computes."""
+    ref = to_lib(states_ref)
+    sel = np.ones(ref.shape[:3], bool)
+    sel[:, ~mask, 6:] = False
+    inc = (ref - q0)[sel]
+    return float(np.linalg.norm((q_lib - ref)[sel]) / max(np.linalg.norm(inc), 1e-300))
+
+
+def round_states(states, precision):
+    """Inputs of a non-FP64 comparison rounded to FP32 on both sides, so that
+    the error measured is that of the stage and not of storing its input."""
+    if precision == "fp64":
+        return states
+    return [{f: st[f].astype(np.float32).astype(np.float64) for f in st} for st in states]
+
+
 def make_pair(N, n_hex, jitter, seed, prof, precision="fp64", sources=(), probes=(),
               eps=None, mu=None, n_batch=1, scheme="waa", mesh=None):
     """scheme: "waa", "stored" (eqs. 10-13) or "ec" (the weight-adjusted

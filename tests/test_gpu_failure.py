@@ -71,6 +71,16 @@ def test_withheld_signal_reports_timeout_and_context_recovers(precision, prof):
     assert _status_of(lambda: s.rk_stage(0, 0.0, dt)) == WADG_ETIMEOUT
     s.set_state(q0, 0.0)
     s.rk_stage(0, 0.0, dt)
+
+    # and so does the allocation-free stepping entry point, whose next call
+    # then steps as before (the flag was read and cleared)
+    s.set_state(q0, 0.0)
+    s.arm_wait_timeout()
+    assert _status_of(lambda: s.run_steps_noalloc(3, dt)) == WADG_ETIMEOUT
+    s.set_state(q0, 0.0)
+    s.run_steps_noalloc(3, dt)
+    again, _ = s.get_state()
+    assert np.array_equal(again, clean)
     s.close()
 
 
@@ -80,6 +90,17 @@ def test_cuda_core_contexts_have_no_waits_to_arm():
         s, _, _ = make_pair(2, 2, 0.1, 1, PML3, precision)
         assert _status_of(s.arm_wait_timeout) == WADG_EUNSUPPORTED
         s.close()
+
+
+def assert_refused(s, dt):
+    """Every call that launches kernels or touches the device state returns
+    ESTATE (before any launch) after a set-up call failed part-way."""
+    from paper_2006_02551_gb300.wadg import WADG_ESTATE
+    for call in (lambda: s.run_steps(1, dt), lambda: s.run_steps_noalloc(1, dt),
+                 lambda: s.rk_stage(0, 0.0, dt), lambda: s.set_state(None, 0.0),
+                 lambda: s.get_state(), lambda: s.profile_stage(1, dt),
+                 lambda: s.adjoint(2, dt, 1)):
+        assert _status_of(call) == WADG_ESTATE
 
 
 def test_memory_limit_reports_enomem_and_context_recovers():
@@ -110,13 +131,25 @@ def test_memory_limit_reports_enomem_and_context_recovers():
     assert held0 > 0                                   # operators, counters
     s.set_memory_limit(held0 + 1024)
     assert _status_of(lambda: s.set_mesh(v, e)) == WADG_ENOMEM
+    # nothing steps or touches the state on a half-built context
+    assert_refused(s, dt)
     s.set_memory_limit(0)
     setup(s)
     held1 = s.set_memory_limit(0)
     assert held1 > held0
+    # a profile whose fields and samples do not fit leaves the tables
+    # incomplete (capped at what the context holds without a PML)
+    s.set_pml(None)
+    s.set_memory_limit(s.set_memory_limit(0))
+    assert _status_of(lambda: s.set_pml(PML3)) == WADG_ENOMEM
+    assert_refused(s, dt)
+    s.set_memory_limit(0)
+    s.set_pml(PML3)
+    s.set_state(None, 0.0)
     s.set_memory_limit(held1)                          # cap at what is held
     # probe records are allocated by the first run: refuse them, then allow
     assert _status_of(lambda: s.set_probes([(0.1, 0.2, 0.3)])) == WADG_ENOMEM
+    assert_refused(s, dt)
     s.set_memory_limit(0)
     s.set_probes([(0.1, 0.2, 0.3)])
     s.set_memory_limit(s.set_memory_limit(0))          # cap at what is held
