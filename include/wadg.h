@@ -26,6 +26,14 @@
  *    four vertices of the element in etov order.
  *  - Units are normalised: the background has eps = mu = 1 (so c0 = 1) and
  *    eps0 of the PML profile is a parameter (1 in normalised units).
+ *  - A set-up call (wadg_set_mesh, wadg_set_materials, wadg_set_pml_profile,
+ *    wadg_set_quadrature, wadg_set_sources, wadg_set_probes) that fails
+ *    part-way, for instance because an allocation was refused, leaves the
+ *    tables it was rebuilding incomplete: until the failed call (or
+ *    wadg_set_mesh) has been repeated successfully, every call that launches
+ *    kernels or reads or writes the state returns WADG_ESTATE without
+ *    touching the device.  A failed wadg_set_sources / wadg_set_probes
+ *    removes the previous sources / probes.
  */
 #ifndef WADG_H
 #define WADG_H
@@ -55,7 +63,7 @@ typedef enum {
  * in double.  FP32: fields, operators, coefficient samples in float; the
  * geometric factors stay double on the device and the source waveform, the
  * coefficient sampling and the objective sums are evaluated in double.
- * TF32 / BF16 (N <= 4, kappa = 1): as FP32, with the reference-operator
+ * TF32 / BF16 (kappa = 1): as FP32, with the reference-operator
  * contractions (D_r, D_s, D_t, LIFT, V_q, P_q) on the tensor cores, operands
  * rounded to TF32 or BF16 (nearest) and accumulated in FP32. */
 typedef enum { WADG_FP64 = 0, WADG_FP32 = 1, WADG_TF32 = 2, WADG_BF16 = 3 } wadg_precision;
@@ -99,12 +107,14 @@ typedef struct {
   int32_t batch;
 } wadg_dipole;
 
-/* Create a context for polynomial order N (1..5) with n_batch independent
- * excitations advanced together on CUDA device `device`, issuing work on
+/* Create a context for polynomial order N (1..5; the nodal basis of degree
+ * N on each tetrahedron of Section II.A, N_p = (N+1)(N+2)(N+3)/6 nodes, the
+ * orders p = 1..5 of Table I) with n_batch independent excitations advanced
+ * together on CUDA device `device`, issuing work on
  * `cuda_stream` (a cudaStream_t, may be NULL).  EINVAL on bad N, precision
- * or n_batch; EUNSUPPORTED for WADG_TF32 with N = 5 (the tensor-core stage
- * takes N <= 4 with TF32 operands, N <= 5 with BF16); ECUDA if the device
- * cannot be used. */
+ * or n_batch (a TF32 context at N = 5 needs a compact volume rule before
+ * it takes a PML, see wadg_set_quadrature); ECUDA if the device cannot be
+ * used. */
 wadg_status wadg_create(int N, wadg_precision prec, int32_t n_batch, int device,
                         void* cuda_stream, wadg_ctx** out);
 
@@ -150,24 +160,80 @@ wadg_status wadg_set_materials(wadg_ctx* ctx, const double* eps_r, const double*
 wadg_status wadg_set_pml_profile(wadg_ctx* ctx, const wadg_pml_profile* prof,
                                  wadg_pml_scheme scheme);
 
+/* Volume quadrature of the weight-adjusted PML terms (eqs. 20, 21 and
+ * 26-29: the coefficients are sampled at these points, V_q interpolates to
+ * them and P_q = M^-1 V_q^T W projects back).  rstw[nq][4] holds the points
+ * (r, s, t) on the reference tetrahedron and their weights w (summing to its
+ * volume 4/3).  Section III uses rules of degree 2p with far fewer points
+ * than the default, the conical-product (Stroud) rule of (N+1)^3 points
+ * (degree 2N+1), which rstw = NULL restores.  The rule must have positive
+ * weights, points inside the tetrahedron and integrate degree 2N exactly
+ * (checked: P_q V_q must be the identity to 1e-10), else EINVAL.  The PML
+ * kernels are compiled for two capacities: compact rules of at most
+ * C_N = 4, 14, 24, 48, 84 points (N = 1..5) and rules of at most (N+1)^3
+ * points; a rule is padded with zero-weight points to the capacity it falls
+ * in (EUNSUPPORTED above (N+1)^3).  TF32 contexts at N = 5 need a compact
+ * rule before a weight-adjusted or element-constant PML can be set; groups
+ * take members with the default rule only.  The stored-matrix scheme keeps
+ * its own rule.  Rebuilds the per-element tables when a mesh is set (as
+ * wadg_set_pml_profile does: the state is reset, sources and probes are
+ * re-mapped). */
+wadg_status wadg_set_quadrature(wadg_ctx* ctx, int32_t nq, const double* rstw);
+
 /* n point dipoles (copied).  ENOTFOUND if a point lies outside the mesh,
  * EINVAL for a batch index out of range or a non-positive width.  A point on
  * a shared face or vertex belongs to the lowest caller element id whose
  * barycentric coordinates are all >= -1e-12. */
 wadg_status wadg_set_sources(wadg_ctx* ctx, int32_t n, const wadg_dipole* src);
 
-/* n probe points xyz[n][3]; E and H there are recorded after every full
- * time step by wadg_run_steps.  ENOTFOUND if a point is outside the mesh. */
+/* n probe points xyz[n][3]; E and H there (the nodal expansion of
+ * Section II.A evaluated at the point) are recorded after every full time
+ * step by wadg_run_steps, as the field samples from which Section III
+ * measures the PML reflection.  ENOTFOUND if a point is outside the mesh. */
 wadg_status wadg_set_probes(wadg_ctx* ctx, int32_t n, const double* xyz);
 
-/* State exchange (host memory, double): q[n_batch][K][12][Np] with the 12
- * components (Ex,Ey,Ez,Hx,Hy,Hz,PEx,PEy,PEz,PHx,PHy,PHz), caller element
- * order.  set_state ignores the P components of non-PML elements (they are
- * not stored) and sets the solution time to t; get_state writes zeros there.
- * q == NULL in set_state zeros the state.  set_state also clears the probe
- * objective. */
-wadg_status wadg_set_state(wadg_ctx* ctx, const double* q, double t);
-wadg_status wadg_get_state(wadg_ctx* ctx, double* q, double* t);
+/* State exchange.  The semi-discrete unknowns of Section II.A (the nodal
+ * values of E, H and, in PML elements, the auxiliary fields P^E, P^H of
+ * eqs. 5-8 that eqs. 10, 11 and 26-29 advance) as
+ * q[n_batch][K][12][Np] (double) with the 12 components (Ex,Ey,Ez,Hx,Hy,Hz,
+ * PEx,PEy,PEz,PHx,PHy,PHz), caller element order.  set_state ignores the P
+ * components of non-PML elements (they are not stored) and sets the solution
+ * time to t; get_state writes zeros there.  q == NULL in set_state zeros the
+ * state.  set_state also clears the Runge-Kutta register and the probe
+ * objective.
+ * on_device = 0: q is host memory; the call converts on the host and copies
+ * (synchronising the context's stream).
+ * on_device = 1: q is device memory on the context's device; a kernel on
+ * the context's stream converts between q and the internal blocks, with no
+ * host copy, and the call returns without waiting (q must stay valid until
+ * the stream has passed the exchange, as for any stream-ordered work). */
+wadg_status wadg_set_state(wadg_ctx* ctx, const void* q, double t, int on_device);
+wadg_status wadg_get_state(wadg_ctx* ctx, void* q, double* t, int on_device);
+
+/* Device bytes the state buffers of the current mesh and PML need
+ * (the two E,H copies, their register, P and its register; each block
+ * padded and 256-byte aligned): the size wadg_bind_state wants.  ESTATE
+ * without a mesh. */
+wadg_status wadg_state_bytes(const wadg_ctx* ctx, size_t* bytes);
+
+/* Place the state buffers in caller-owned device memory dev (on the
+ * context's device, 256-byte aligned, at least wadg_state_bytes bytes), for
+ * callers such as PyTorch whose allocator owns the device memory.  The
+ * current state moves into dev (device to device) and the library releases
+ * its own buffers.  dev must stay allocated until the context is destroyed
+ * or the state is unbound with dev = NULL (the library then allocates its
+ * own buffers again and moves the state back).  Later set-up calls that
+ * rebuild the state (wadg_set_mesh, wadg_set_pml_profile, ...) keep using
+ * dev, and fail with EINVAL when it is too small for the new state.  Bound
+ * bytes do not count against wadg_set_memory_limit.  The internal layout of
+ * dev is the library's; exchange values through wadg_set_state /
+ * wadg_get_state. */
+wadg_status wadg_bind_state(wadg_ctx* ctx, void* dev, size_t bytes);
+
+/* Bytes the context has copied from host to device and back since it was
+ * created: state exchanges through host memory, probe records, objective
+ * reads and the few bytes of step clocks and status flags. */
+wadg_status wadg_transfer_bytes(const wadg_ctx* ctx, size_t* h2d, size_t* d2h);
 
 /* One stage i (0..4) of the five-stage fourth-order low-storage Runge-Kutta
  * scheme: res <- A_i res + dt * f(q, t + c_i dt); q <- q + B_i res, where f
@@ -177,7 +243,9 @@ wadg_status wadg_get_state(wadg_ctx* ctx, double* q, double* t);
 wadg_status wadg_rk_stage(wadg_ctx* ctx, int stage, double t, double dt);
 
 /* Advance every excitation by nsteps full steps of size dt from the current
- * solution time.  If probe_out is not NULL it receives
+ * solution time: the explicit time marching of the semi-discrete system
+ * (Section II.B), each step the five stages of wadg_rk_stage.  If probe_out
+ * is not NULL it receives
  * probe_out[nsteps][nprobe][6][n_batch] (double; Ex..Hz after each step).
  * The FP64 objective sum over probes and steps of |E|^2 accumulates per
  * excitation (wadg_objective).  ENONFINITE if the state became non-finite. */
@@ -222,14 +290,17 @@ wadg_status wadg_adjoint(wadg_ctx* ctx, int64_t nsteps, double dt, int32_t ckpt_
  * library (held on every GPU that loads the library until the process
  * exits).  Steps are processed in chunks whose probe records fit the array;
  * EINVAL if the records of a single step (nprobe * 6 * n_batch doubles) do
- * not fit.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and should come before any stream capture.  Every
- * call shares the one array per device, so calls whose work overlaps on the
- * GPU (other threads, other streams) race on it. */
+ * not fit.  Each call looks up the array's device address on the context's
+ * device (cudaGetSymbolAddress); with lazy module loading the first call on
+ * a device also loads the module, so it should come before any stream
+ * capture.  Every call shares the one array per device and sets the counters
+ * it needs before use, so calls whose work overlaps on the GPU (other
+ * threads, other streams) race on it. */
 wadg_status wadg_run_steps_noalloc(wadg_ctx* ctx, int64_t nsteps, double dt, double* probe_out);
 
-/* Largest step for the given CFL number:
- * dt = cfl * 2 / ((N+1)^2 * max_{k,f} Fscale_{k,f}), Fscale = sJ/J. */
+/* Largest step for the given CFL number of the explicit time marching
+ * (Section II.B; the paper states no step rule, this is the usual nodal DG
+ * bound): dt = cfl * 2 / ((N+1)^2 * max_{k,f} Fscale_{k,f}), Fscale = sJ/J. */
 wadg_status wadg_stable_dt(const wadg_ctx* ctx, double cfl, double* dt_out);
 
 /* Objective J_b = sum over probes and recorded steps of |E|^2 for each
@@ -240,13 +311,16 @@ wadg_status wadg_objective(wadg_ctx* ctx, double* J_out);
  * per-element PML coefficients (the samples of the weight-adjusted and
  * element-constant schemes, the operators of the stored-matrix scheme), for
  * the reference operators, and for the per-element geometry and
- * connectivity.  Any pointer may be NULL. */
+ * connectivity: the memory comparison of Section II.B (15 N_p^2 values per
+ * PML element for stored matrices against samples at N_q points for the
+ * weight-adjusted scheme) and Table I.  Any pointer may be NULL. */
 wadg_status wadg_memory_report(const wadg_ctx* ctx, size_t* bytes_state,
                                size_t* bytes_pml_coeff, size_t* bytes_operators,
                                size_t* bytes_geometry);
 
 /* Mesh sizes after set_mesh / set_pml_profile: elements, PML elements,
- * nodes per element, volume quadrature nodes per element. */
+ * nodes per element, volume quadrature nodes per element (of the rule, not
+ * counting the padding to the kernels' capacity). */
 wadg_status wadg_mesh_info(const wadg_ctx* ctx, int64_t* K, int64_t* K_pml, int32_t* Np,
                            int32_t* Nq);
 

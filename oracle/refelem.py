@@ -198,7 +198,12 @@ FACE_VERTS = ((0, 1, 2), (0, 1, 3), (1, 2, 3), (0, 2, 3))
 
 
 class RefElement:
-    def __init__(self, N, quad_points_per_dir=None):
+    """volume_rule: optional (nq, 4) array of points (r, s, t) and weights on
+    the reference tetrahedron to use for the weight-adjusted terms instead
+    of the conical-product rule (Section III uses rules of degree 2p with
+    fewer points); it must integrate degree 2N exactly for P_q V_q = I."""
+
+    def __init__(self, N, quad_points_per_dir=None, volume_rule=None):
         if N < 1:
             raise ValueError("N >= 1")
         self.N = N
@@ -231,9 +236,14 @@ class RefElement:
             E[np.ix_(fm, np.arange(f * self.Nfp, (f + 1) * self.Nfp))] = Mf
         self.Emat = E
         self.LIFT = self.Minv @ E
-        # quadrature of degree 2N+1 (eq. 19), V_q, P_q (eqs. 20, 21)
-        nq = quad_points_per_dir or (N + 1)
-        rq, sq, tq, wq = stroud_rule(nq)
+        # quadrature of degree 2N+1 (eq. 19), or the caller's rule; V_q, P_q
+        # (eqs. 20, 21)
+        if volume_rule is not None:
+            rule = np.asarray(volume_rule, dtype=np.float64).reshape(-1, 4)
+            rq, sq, tq, wq = (rule[:, i].copy() for i in range(4))
+        else:
+            nq = quad_points_per_dir or (N + 1)
+            rq, sq, tq, wq = stroud_rule(nq)
         self.rq, self.sq, self.tq, self.wq = rq, sq, tq, wq
         self.Nq = rq.size
         VI = tet_basis(N, rq, sq, tq)

@@ -21,7 +21,7 @@ import numpy as np
 from . import lserk
 from .geometry import Geometry
 from .maxwell import Discretization
-from .refelem import ref_element
+from .refelem import RefElement, ref_element
 
 FIELDS = ("E", "H", "PE", "PH")
 
@@ -35,8 +35,9 @@ def dipole_current(src, t):
 class Simulation:
     def __init__(self, N, vxyz, etov, profile=None, eps=None, mu=None,
                  sources=(), probes=(), n_batch=1, scheme="waa", alpha=1.0,
-                 stored_quad_points=None, vcanon=None):
-        self.ref = ref_element(N)
+                 stored_quad_points=None, vcanon=None, volume_rule=None):
+        self.ref = ref_element(N) if volume_rule is None else RefElement(
+            N, volume_rule=volume_rule)
         self.geom = Geometry(self.ref, vxyz, etov, vcanon)
         self.disc = Discretization(self.ref, self.geom, eps, mu, profile,
                                    alpha, stored_quad_points)

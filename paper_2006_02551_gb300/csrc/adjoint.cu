@@ -22,12 +22,12 @@ namespace wadg {
 
 namespace {
 
-template <int N>
+template <int N, int QC = 0>
 struct AD {
   static constexpr int Np = (N + 1) * (N + 2) * (N + 3) / 6;
   static constexpr int Nfp = (N + 1) * (N + 2) / 2;
   static constexpr int NF = 4 * Nfp;
-  static constexpr int Nq = (N + 1) * (N + 1) * (N + 1);
+  static constexpr int Nq = quad_capacity(N, QC);   // volume quadrature points
   static constexpr int NpP = (Np + 3) & ~3;
   static constexpr int NqP = (Nq + 3) & ~3;
 };
@@ -97,9 +97,9 @@ __global__ void __launch_bounds__(kAdjThreads) adj_lift_kernel(const AdjParams<R
 }
 
 // ---------------------------------------------------------------- adj_main
-template <typename Real, int N, bool PML>
+template <typename Real, int N, bool PML, int QC = 0>
 struct AdjTile {
-  using D = AD<N>;
+  using D = AD<N, QC>;
   static constexpr int C = PML ? 12 : 6;
   // MU, QF, ADJ [C][Np]; FLH [NF][3]; CH [3][Np]; (PML) ZZ [NqP][12]
   static constexpr int per = 3 * C * D::Np + 3 * D::NF + (PML ? 12 * D::NqP : 0) + 16;
@@ -114,11 +114,11 @@ __device__ __forceinline__ void atomic_add_real(Real* p, Real v) {
   atomicAdd(p, v);
 }
 
-template <typename Real, int N, bool PML>
+template <typename Real, int N, bool PML, int QC = 0>
 __global__ void __launch_bounds__(kAdjThreads) adj_main_kernel(const AdjParams<Real> A) {
-  using D = AD<N>;
+  using D = AD<N, QC>;
   constexpr int Np = D::Np, Nfp = D::Nfp, NF = D::NF, Nq = D::Nq, NpP = D::NpP, NqP = D::NqP;
-  using TL = AdjTile<Real, N, PML>;
+  using TL = AdjTile<Real, N, PML, QC>;
   constexpr int T = TL::T, C = TL::C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* MU = reinterpret_cast<Real*>(smem_raw);   // [T][C][Np]
@@ -512,7 +512,7 @@ __global__ void adj_probe_kernel(const Real* q, int64_t strideQ, int nprobe, int
 }
 
 template <typename Real, int N>
-cudaError_t adj_stage_n(const AdjParams<Real>& P, int nb, cudaStream_t s) {
+cudaError_t adj_stage_n(const AdjParams<Real>& P, int nb, cudaStream_t s, int qc) {
   {
     dim3 g((P.K + 7) / 8, nb);
     adj_lift_kernel<Real, N><<<g, kAdjThreads, 0, s>>>(P);
@@ -529,6 +529,10 @@ cudaError_t adj_stage_n(const AdjParams<Real>& P, int nb, cudaStream_t s) {
       using TL = AdjTile<Real, N, false>;
       dim3 g((Q.n_elem + TL::T - 1) / TL::T, nb);
       adj_main_kernel<Real, N, false><<<g, kAdjThreads, TL::smem, s>>>(Q);
+    } else if (qc) {
+      using TL = AdjTile<Real, N, true, 1>;
+      dim3 g((Q.n_elem + TL::T - 1) / TL::T, nb);
+      adj_main_kernel<Real, N, true, 1><<<g, kAdjThreads, TL::smem, s>>>(Q);
     } else {
       using TL = AdjTile<Real, N, true>;
       dim3 g((Q.n_elem + TL::T - 1) / TL::T, nb);
@@ -549,6 +553,10 @@ cudaError_t adj_configure_n() {
     e = cudaFuncSetAttribute(adj_main_kernel<Real, N, true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)AdjTile<Real, N, true>::smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(adj_main_kernel<Real, N, true, 1>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)AdjTile<Real, N, true, 1>::smem);
   return e;
 }
 
@@ -569,18 +577,21 @@ template cudaError_t configure_adjoint_kernels<double>(int);
 template cudaError_t configure_adjoint_kernels<float>(int);
 
 template <typename Real>
-cudaError_t launch_adjoint_stage(int N, const AdjParams<Real>& P, int nb, cudaStream_t s) {
+cudaError_t launch_adjoint_stage(int N, const AdjParams<Real>& P, int nb, cudaStream_t s,
+                                 int qc) {
   switch (N) {
-    case 1: return adj_stage_n<Real, 1>(P, nb, s);
-    case 2: return adj_stage_n<Real, 2>(P, nb, s);
-    case 3: return adj_stage_n<Real, 3>(P, nb, s);
-    case 4: return adj_stage_n<Real, 4>(P, nb, s);
-    case 5: return adj_stage_n<Real, 5>(P, nb, s);
+    case 1: return adj_stage_n<Real, 1>(P, nb, s, qc);
+    case 2: return adj_stage_n<Real, 2>(P, nb, s, qc);
+    case 3: return adj_stage_n<Real, 3>(P, nb, s, qc);
+    case 4: return adj_stage_n<Real, 4>(P, nb, s, qc);
+    case 5: return adj_stage_n<Real, 5>(P, nb, s, qc);
     default: return cudaErrorInvalidValue;
   }
 }
-template cudaError_t launch_adjoint_stage<double>(int, const AdjParams<double>&, int, cudaStream_t);
-template cudaError_t launch_adjoint_stage<float>(int, const AdjParams<float>&, int, cudaStream_t);
+template cudaError_t launch_adjoint_stage<double>(int, const AdjParams<double>&, int, cudaStream_t,
+                                                  int);
+template cudaError_t launch_adjoint_stage<float>(int, const AdjParams<float>&, int, cudaStream_t,
+                                                 int);
 
 template <typename Real>
 cudaError_t launch_adjoint_probes(const Real* q, int64_t strideQ, int nprobe, int nb, int Np,

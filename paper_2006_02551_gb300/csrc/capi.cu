@@ -60,6 +60,7 @@ struct DevPtr {
   void* p = nullptr;
   size_t bytes = 0;
   Budget* owner = nullptr;   // budget the bytes count against, if any
+  bool borrowed = false;     // points into caller memory (wadg_bind_state)
 };
 
 }  // namespace
@@ -99,6 +100,12 @@ struct wadg_ctx {
   DevPtr q[2], rq, p, rp, geo, fnrm, mat, nbr, code, sig, kap, ops, tabs, verts;
   DevPtr src, srcw, pr_elem, pr_ell, pr_out, obj, tdev, stepdev, flag, tcops, errflag;
   DevPtr stored;     // stored-matrix scheme: per PML element operators
+  DevPtr dperm;      // internal -> caller element id (int32), device state exchange
+  // caller-owned device memory holding the state buffers (wadg_bind_state)
+  void* bound = nullptr;
+  size_t bound_bytes = 0;
+  // bytes this context copied between host and device memory
+  size_t h2d = 0, d2h = 0;
   Budget budget;     // device-memory cap (wadg_set_memory_limit)
   bool tc = false;   // tensor-core stage kernels (TF32 or BF16 operands)
   bool bf16 = false; // BF16 operands
@@ -111,6 +118,10 @@ struct wadg_ctx {
   // successfully, so no kernel ever sees a freed or half-built table.
   bool ready = false;
   bool src_ok = true, probes_ok = true;
+  bool ops_ok = true;   // the reference-operator tables match ref
+  // quadrature class of the PML kernels (quad_capacity): 0 for the default
+  // conical-product rule, 1 for a compact caller rule (wadg_set_quadrature)
+  int qc = 0;
   int cur = 0;
   int nsrc = 0, nprobe = 0;
   std::vector<wadg_dipole> src_user;
@@ -143,11 +154,12 @@ wadg_status fail(wadg_ctx* c, wadg_status s, const char* fmt, ...) {
   } while (0)
 
 void dfree(DevPtr& d) {
-  if (d.p) cudaFree(d.p);
+  if (d.p && !d.borrowed) cudaFree(d.p);
   if (d.p && d.owner) d.owner->held -= d.bytes;
   d.p = nullptr;
   d.bytes = 0;
   d.owner = nullptr;
+  d.borrowed = false;
 }
 
 // Every device buffer ends with kSlack spare bytes: the tensor-core kernels
@@ -334,6 +346,47 @@ wadg_status build_stored_ops(wadg_ctx* ctx, const double* dprof) {
   return WADG_OK;
 }
 
+// The five state buffers (q[0], q[1], rq, p, rp), each followed by kSlack
+// spare bytes and starting on a 256-byte boundary.
+size_t state_layout(size_t qbytes, size_t pbytes, size_t off[5]) {
+  const size_t sz[5] = {qbytes, qbytes, qbytes, pbytes, pbytes};
+  size_t o = 0;
+  for (int i = 0; i < 5; ++i) {
+    off[i] = o;
+    o += (sz[i] + kSlack + 255) & ~size_t(255);
+  }
+  return o;
+}
+
+DevPtr* state_buf(wadg_ctx* ctx, int i) {
+  DevPtr* b[5] = {&ctx->q[0], &ctx->q[1], &ctx->rq, &ctx->p, &ctx->rp};
+  return b[i];
+}
+
+// (re)allocate the state buffers: in the caller's bound memory when bound
+// (EINVAL if it is too small), else in the library's own
+wadg_status alloc_state_buffers(wadg_ctx* ctx, size_t qbytes, size_t pbytes) {
+  size_t off[5];
+  const size_t need = state_layout(qbytes, pbytes, off);
+  const size_t sz[5] = {qbytes, qbytes, qbytes, pbytes, pbytes};
+  for (int i = 0; i < 5; ++i) dfree(*state_buf(ctx, i));
+  if (ctx->bound) {
+    if (ctx->bound_bytes < need)
+      return fail(ctx, WADG_EINVAL, "the bound state memory holds %zu bytes, the state needs %zu",
+                  ctx->bound_bytes, need);
+    for (int i = 0; i < 5; ++i) {
+      DevPtr* d = state_buf(ctx, i);
+      if (sz[i] == 0) continue;
+      d->p = static_cast<unsigned char*>(ctx->bound) + off[i];
+      d->bytes = sz[i];
+      d->borrowed = true;
+    }
+    return WADG_OK;
+  }
+  for (int i = 0; i < 5; ++i) CK(dalloc(*state_buf(ctx, i), sz[i]));
+  return WADG_OK;
+}
+
 template <typename Real>
 wadg_status rebuild_typed(wadg_ctx* ctx) {
   const int64_t K = ctx->K;
@@ -431,20 +484,22 @@ wadg_status rebuild_typed(wadg_ctx* ctx) {
   CK(cudaMemcpy(ctx->nbr.p, nbr.data(), nbr.size() * 4, cudaMemcpyHostToDevice));
   CK(dalloc(ctx->code, code.size()));
   CK(cudaMemcpy(ctx->code.p, code.data(), code.size(), cudaMemcpyHostToDevice));
+  {  // internal -> caller element id, for the device state exchange
+    std::vector<int> pm(K);
+    for (int64_t e = 0; e < K; ++e) pm[e] = (int)ctx->perm[e];
+    CK(dalloc(ctx->dperm, pm.size() * 4));
+    CK(cudaMemcpy(ctx->dperm.p, pm.data(), pm.size() * 4, cudaMemcpyHostToDevice));
+  }
   // ---- state
   const size_t qbytes = (size_t)ctx->nb * K * 6 * Np * sizeof(Real);
   const size_t pbytes = (size_t)ctx->nb * ctx->K1 * 6 * Np * sizeof(Real);
-  for (int i = 0; i < 2; ++i) {
-    CK(dalloc(ctx->q[i], qbytes));
-    if (qbytes) CK(cudaMemsetAsync(ctx->q[i].p, 0, qbytes, ctx->stream));
+  {
+    wadg_status st = alloc_state_buffers(ctx, qbytes, pbytes);
+    if (st != WADG_OK) return st;
   }
-  CK(dalloc(ctx->rq, qbytes));
-  if (qbytes) CK(cudaMemsetAsync(ctx->rq.p, 0, qbytes, ctx->stream));
-  CK(dalloc(ctx->p, pbytes));
-  CK(dalloc(ctx->rp, pbytes));
-  if (pbytes) {
-    CK(cudaMemsetAsync(ctx->p.p, 0, pbytes, ctx->stream));
-    CK(cudaMemsetAsync(ctx->rp.p, 0, pbytes, ctx->stream));
+  for (int i = 0; i < 5; ++i) {
+    DevPtr* d = state_buf(ctx, i);
+    if (d->bytes) CK(cudaMemsetAsync(d->p, 0, d->bytes, ctx->stream));
   }
   ctx->cur = 0;
   ctx->t = 0.0;
@@ -630,16 +685,20 @@ template <typename Real>
 cudaError_t launch_pml_class(wadg_ctx* ctx, const StageParams<Real>& P) {
   if (ctx->scheme == WADG_PML_STORED) return launch_stage_stored<Real>(ctx->N, P, ctx->nb, ctx->stream);
   if constexpr (std::is_same<Real, float>::value) {
-    if (ctx->tc) return launch_stage_tc(ctx->N, true, P, ctx->nb, ctx->stream, ctx->bf16);
+    if (ctx->tc) {
+      // compact volume rules: the row-owned kernel; (N+1)^3 rules: the other
+      if (ctx->qc == 1) return launch_pml_tc_rows(ctx->N, P, ctx->nb, ctx->stream, ctx->bf16);
+      return launch_stage_tc(ctx->N, true, P, ctx->nb, ctx->stream, ctx->bf16, ctx->qc);
+    }
   }
-  return launch_stage<Real>(ctx->N, true, ctx->kappa, P, ctx->nb, ctx->stream);
+  return launch_stage<Real>(ctx->N, true, ctx->kappa, P, ctx->nb, ctx->stream, ctx->qc);
 }
 
 template <typename Real>
 wadg_status issue_stage(wadg_ctx* ctx, int stage, double dt, double t, bool use_tdev) {
   if (ctx->tc) {
     StageParams<float> A = stage_params<float>(ctx, stage, dt, t, use_tdev, false);
-    CK(launch_stage_tc(ctx->N, false, A, ctx->nb, ctx->stream, ctx->bf16));
+    CK(launch_stage_tc(ctx->N, false, A, ctx->nb, ctx->stream, ctx->bf16, ctx->qc));
     if (ctx->K1 > 0) {
       StageParams<float> B = stage_params<float>(ctx, stage, dt, t, use_tdev, true);
       CK(launch_pml_class<float>(ctx, B));
@@ -706,6 +765,7 @@ wadg_status capture_graphs(wadg_ctx* ctx, double dt) {
 wadg_status check_err_flag(wadg_ctx* ctx) {
   int e = 0;
   CK(cudaMemcpyAsync(&e, ctx->errflag.p, 4, cudaMemcpyDeviceToHost, ctx->stream));
+  ctx->d2h += 4;
   CK(cudaStreamSynchronize(ctx->stream));
   if (e) {
     CK(cudaMemset(ctx->errflag.p, 0, 4));
@@ -726,6 +786,9 @@ wadg_status need_mesh(wadg_ctx* ctx) {
 wadg_status need_ready(wadg_ctx* ctx) {
   wadg_status s = need_mesh(ctx);
   if (s != WADG_OK) return s;
+  if (!ctx->ops_ok)
+    return fail(ctx, WADG_ESTATE, "the operator tables are incomplete after a failed call: "
+                "repeat wadg_set_quadrature");
   if (!ctx->ready)
     return fail(ctx, WADG_ESTATE,
                 "the device tables are incomplete after a failed set-up call: repeat "
@@ -762,6 +825,7 @@ static wadg_status set_state_t(wadg_ctx* ctx, const double* q) {
     CK(cudaMemcpy(ctx->q[0].p, hq.data(), hq.size() * sizeof(Real), cudaMemcpyHostToDevice));
   if (!hp.empty())
     CK(cudaMemcpy(ctx->p.p, hp.data(), hp.size() * sizeof(Real), cudaMemcpyHostToDevice));
+  ctx->h2d += (hq.size() + hp.size()) * sizeof(Real);
   CK(cudaMemset(ctx->rq.p, 0, ctx->rq.bytes));
   if (ctx->rp.bytes) CK(cudaMemset(ctx->rp.p, 0, ctx->rp.bytes));
   CK(cudaMemset(ctx->obj.p, 0, ctx->obj.bytes));
@@ -778,6 +842,7 @@ static wadg_status get_state_t(wadg_ctx* ctx, double* q) {
   CK(cudaMemcpy(hq.data(), ctx->q[ctx->cur].p, hq.size() * sizeof(Real), cudaMemcpyDeviceToHost));
   if (!hp.empty())
     CK(cudaMemcpy(hp.data(), ctx->p.p, hp.size() * sizeof(Real), cudaMemcpyDeviceToHost));
+  ctx->d2h += (hq.size() + hp.size()) * sizeof(Real);
   for (int b = 0; b < ctx->nb; ++b)
     for (int64_t e = 0; e < K; ++e) {
       const int64_t k = ctx->perm[e];
@@ -794,6 +859,33 @@ static wadg_status get_state_t(wadg_ctx* ctx, double* q) {
   return WADG_OK;
 }
 
+// device-resident exchange: a kernel on the context's stream converts
+// between the caller's array (ABI layout, double) and the internal blocks
+template <typename Real>
+static wadg_status set_state_dev(wadg_ctx* ctx, const double* q) {
+  ctx->cur = 0;
+  if (q) {
+    CK(launch_state_exchange<Real>(true, (const int*)ctx->dperm.p, ctx->K, ctx->K0, ctx->ref.Np,
+                                   ctx->nb, const_cast<double*>(q), (Real*)ctx->q[0].p,
+                                   (Real*)ctx->p.p, ctx->stream));
+  } else {
+    if (ctx->q[0].bytes) CK(cudaMemsetAsync(ctx->q[0].p, 0, ctx->q[0].bytes, ctx->stream));
+    if (ctx->p.bytes) CK(cudaMemsetAsync(ctx->p.p, 0, ctx->p.bytes, ctx->stream));
+  }
+  CK(cudaMemsetAsync(ctx->rq.p, 0, ctx->rq.bytes, ctx->stream));
+  if (ctx->rp.bytes) CK(cudaMemsetAsync(ctx->rp.p, 0, ctx->rp.bytes, ctx->stream));
+  CK(cudaMemsetAsync(ctx->obj.p, 0, ctx->obj.bytes, ctx->stream));
+  return WADG_OK;
+}
+
+template <typename Real>
+static wadg_status get_state_dev(wadg_ctx* ctx, double* q) {
+  CK(launch_state_exchange<Real>(false, (const int*)ctx->dperm.p, ctx->K, ctx->K0, ctx->ref.Np,
+                                 ctx->nb, q, (Real*)ctx->q[ctx->cur].p, (Real*)ctx->p.p,
+                                 ctx->stream));
+  return WADG_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -806,8 +898,8 @@ wadg_status wadg_create(int N, wadg_precision prec, int32_t n_batch, int device,
   if (N < 1 || N > 5) return fail(nullptr, WADG_EINVAL, "N must be in 1..5 (got %d)", N);
   if (prec != WADG_FP64 && prec != WADG_FP32 && prec != WADG_TF32 && prec != WADG_BF16)
     return fail(nullptr, WADG_EINVAL, "unknown precision %d", prec);
-  if ((prec == WADG_TF32 || prec == WADG_BF16) && !tc_supported(N, false, prec == WADG_BF16))
-    return fail(nullptr, WADG_EUNSUPPORTED, "the tensor-core stage is built for N <= 4 (TF32), N <= 5 (BF16)");
+  if ((prec == WADG_TF32 || prec == WADG_BF16) && !tc_supported(N, false, prec == WADG_BF16, 1))
+    return fail(nullptr, WADG_EUNSUPPORTED, "the tensor-core stage is built for N <= 5");
   if (n_batch < 1) return fail(nullptr, WADG_EINVAL, "n_batch must be >= 1");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
@@ -842,6 +934,7 @@ wadg_status wadg_create(int N, wadg_precision prec, int32_t n_batch, int device,
     cudaError_t ce = ctx->rs == 8 ? configure_stage_kernels<double>(N)
                                   : configure_stage_kernels<float>(N);
     if (ce == cudaSuccess && ctx->tc) ce = configure_tc_kernels(N, ctx->bf16);
+    if (ce == cudaSuccess && ctx->tc) ce = configure_tc_rows(N, ctx->bf16);
     if (ce == cudaSuccess)
       ce = ctx->rs == 8 ? configure_stored_kernels<double>(N) : configure_stored_kernels<float>(N);
     if (ce == cudaSuccess && !ctx->tc)
@@ -879,7 +972,7 @@ wadg_status wadg_destroy(wadg_ctx* ctx) {
                     &ctx->nbr, &ctx->code, &ctx->sig, &ctx->kap, &ctx->ops, &ctx->tabs,
                     &ctx->verts, &ctx->src, &ctx->srcw, &ctx->pr_elem, &ctx->pr_ell,
                     &ctx->pr_out, &ctx->obj, &ctx->tdev, &ctx->stepdev, &ctx->flag,
-                    &ctx->tcops, &ctx->errflag, &ctx->stored})
+                    &ctx->tcops, &ctx->errflag, &ctx->stored, &ctx->dperm})
     dfree(*d);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
@@ -1056,6 +1149,9 @@ wadg_status wadg_set_pml_profile(wadg_ctx* ctx, const wadg_pml_profile* prof,
       if (prof->kappa_max[u] != 1.0) kap = true;
     if (kap && ctx->tc && scheme != WADG_PML_STORED)
       return fail(ctx, WADG_EUNSUPPORTED, "kappa_max != 1 is not built for the tensor-core stage");
+    if (ctx->tc && scheme != WADG_PML_STORED && !tc_supported(ctx->N, false, ctx->bf16, ctx->qc))
+      return fail(ctx, WADG_EUNSUPPORTED,
+                  "TF32 operands at N = 5 need a compact volume rule (wadg_set_quadrature)");
     if (kap && scheme == WADG_PML_STORED)
       return fail(ctx, WADG_EUNSUPPORTED, "the stored-matrix scheme is built for kappa = 1");
     ctx->has_prof = true;
@@ -1069,6 +1165,53 @@ wadg_status wadg_set_pml_profile(wadg_ctx* ctx, const wadg_pml_profile* prof,
   }
   s = rebuild(ctx);
   if (s != WADG_OK) return s;
+  return remap_points(ctx);
+}
+
+wadg_status wadg_set_quadrature(wadg_ctx* ctx, int32_t nq, const double* rstw) {
+  if (!ctx) return fail(nullptr, WADG_EINVAL, "null context");
+  cudaSetDevice(ctx->device);
+  BudgetScope budget_scope(&ctx->budget);
+  const int N = ctx->N;
+  std::vector<double> r, s_, t, w;
+  int qc = 0, cap = 0;
+  if (rstw) {
+    if (nq < 1) return fail(ctx, WADG_EINVAL, "empty quadrature rule");
+    if (nq <= compact_nq(N)) qc = 1;
+    else if (nq <= quad_capacity(N, 0)) qc = 0;
+    else
+      return fail(ctx, WADG_EUNSUPPORTED, "the PML kernels hold at most %d volume quadrature "
+                  "points at N = %d (got %d)", quad_capacity(N, 0), N, (int)nq);
+    cap = quad_capacity(N, qc);
+    for (int q = 0; q < nq; ++q) {
+      r.push_back(rstw[4 * q]);
+      s_.push_back(rstw[4 * q + 1]);
+      t.push_back(rstw[4 * q + 2]);
+      w.push_back(rstw[4 * q + 3]);
+    }
+  } else {
+    stroud_rule(N + 1, r, s_, t, w);
+    cap = quad_capacity(N, 0);
+  }
+  if (ctx->tc && ctx->has_prof && ctx->scheme != WADG_PML_STORED &&
+      !tc_supported(N, false, ctx->bf16, qc))
+    return fail(ctx, WADG_EUNSUPPORTED,
+                "TF32 operands at N = 5 need a compact volume rule with the PML set");
+  RefOps R = ctx->ref;
+  const char* e = nullptr;
+  if (!set_volume_rule(R, r, s_, t, w, cap, &e)) return fail(ctx, WADG_EINVAL, "%s", e);
+  // the operator tables and (with a mesh) every per-element table follow
+  ctx->ready = false;
+  invalidate_graphs(ctx);
+  ctx->ref = R;
+  ctx->qc = qc;
+  ctx->ops_ok = false;
+  wadg_status st = ctx->rs == 8 ? upload_ops<double>(ctx) : upload_ops<float>(ctx);
+  if (st != WADG_OK) return st;
+  ctx->ops_ok = true;
+  if (!ctx->has_mesh) return WADG_OK;
+  st = rebuild(ctx);
+  if (st != WADG_OK) return st;
   return remap_points(ctx);
 }
 
@@ -1097,25 +1240,100 @@ wadg_status wadg_set_probes(wadg_ctx* ctx, int32_t n, const double* xyz) {
   return upload_probes(ctx);
 }
 
-wadg_status wadg_set_state(wadg_ctx* ctx, const double* q, double t) {
+wadg_status wadg_set_state(wadg_ctx* ctx, const void* q, double t, int on_device) {
   wadg_status s = need_ready(ctx);
   if (s != WADG_OK) return s;
   cudaSetDevice(ctx->device);
   BudgetScope budget_scope(&ctx->budget);
-  s = ctx->rs == 8 ? set_state_t<double>(ctx, q) : set_state_t<float>(ctx, q);
+  const double* qd = static_cast<const double*>(q);
+  if (on_device)
+    s = ctx->rs == 8 ? set_state_dev<double>(ctx, qd) : set_state_dev<float>(ctx, qd);
+  else
+    s = ctx->rs == 8 ? set_state_t<double>(ctx, qd) : set_state_t<float>(ctx, qd);
   if (s == WADG_OK) ctx->t = t;
   return s;
 }
 
-wadg_status wadg_get_state(wadg_ctx* ctx, double* q, double* t) {
+wadg_status wadg_get_state(wadg_ctx* ctx, void* q, double* t, int on_device) {
   wadg_status s = need_ready(ctx);
   if (s != WADG_OK) return s;
   cudaSetDevice(ctx->device);
   if (q) {
-    s = ctx->rs == 8 ? get_state_t<double>(ctx, q) : get_state_t<float>(ctx, q);
+    double* qd = static_cast<double*>(q);
+    if (on_device)
+      s = ctx->rs == 8 ? get_state_dev<double>(ctx, qd) : get_state_dev<float>(ctx, qd);
+    else
+      s = ctx->rs == 8 ? get_state_t<double>(ctx, qd) : get_state_t<float>(ctx, qd);
     if (s != WADG_OK) return s;
   }
   if (t) *t = ctx->t;
+  return WADG_OK;
+}
+
+wadg_status wadg_state_bytes(const wadg_ctx* ctx, size_t* bytes) {
+  if (!ctx || !bytes) return fail(nullptr, WADG_EINVAL, "null argument");
+  if (!ctx->has_mesh) return fail(const_cast<wadg_ctx*>(ctx), WADG_ESTATE, "no mesh set");
+  size_t off[5];
+  const size_t r = ctx->rs;
+  *bytes = state_layout((size_t)ctx->nb * ctx->K * 6 * ctx->ref.Np * r,
+                        (size_t)ctx->nb * ctx->K1 * 6 * ctx->ref.Np * r, off);
+  return WADG_OK;
+}
+
+wadg_status wadg_bind_state(wadg_ctx* ctx, void* dev, size_t bytes) {
+  wadg_status s = need_ready(ctx);
+  if (s != WADG_OK) return s;
+  if (dev && (reinterpret_cast<uintptr_t>(dev) & 255))
+    return fail(ctx, WADG_EINVAL, "bound state memory must start on a 256-byte boundary");
+  cudaSetDevice(ctx->device);
+  BudgetScope budget_scope(&ctx->budget);
+  const size_t qb = ctx->q[0].bytes, pb = ctx->p.bytes;
+  size_t off[5];
+  if (dev && bytes < state_layout(qb, pb, off))
+    return fail(ctx, WADG_EINVAL, "the state needs %zu bytes (wadg_state_bytes), got %zu",
+                state_layout(qb, pb, off), bytes);
+  // the current state moves into the new buffers: copy it device to device
+  DevPtr old[5];
+  for (int i = 0; i < 5; ++i) {
+    old[i] = *state_buf(ctx, i);
+    *state_buf(ctx, i) = DevPtr{};
+  }
+  void* prev = ctx->bound;
+  size_t prev_bytes = ctx->bound_bytes;
+  ctx->bound = dev;
+  ctx->bound_bytes = dev ? bytes : 0;
+  s = alloc_state_buffers(ctx, qb, pb);
+  if (s == WADG_OK) {
+    for (int i = 0; i < 5 && s == WADG_OK; ++i) {
+      DevPtr* d = state_buf(ctx, i);
+      if (old[i].bytes) {
+        const cudaError_t e = cudaMemcpyAsync(d->p, old[i].p, old[i].bytes,
+                                              cudaMemcpyDeviceToDevice, ctx->stream);
+        if (e != cudaSuccess) s = fail(ctx, WADG_ECUDA, "state copy: %s", cudaGetErrorString(e));
+      }
+    }
+    const cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (s == WADG_OK && e != cudaSuccess)
+      s = fail(ctx, WADG_ECUDA, "state copy: %s", cudaGetErrorString(e));
+  }
+  if (s != WADG_OK) {   // keep the old buffers
+    for (int i = 0; i < 5; ++i) {
+      dfree(*state_buf(ctx, i));
+      *state_buf(ctx, i) = old[i];
+    }
+    ctx->bound = prev;
+    ctx->bound_bytes = prev_bytes;
+    return s;
+  }
+  for (int i = 0; i < 5; ++i) dfree(old[i]);
+  invalidate_graphs(ctx);   // the graphs captured the old buffer addresses
+  return WADG_OK;
+}
+
+wadg_status wadg_transfer_bytes(const wadg_ctx* ctx, size_t* h2d, size_t* d2h) {
+  if (!ctx) return fail(nullptr, WADG_EINVAL, "null context");
+  if (h2d) *h2d = ctx->h2d;
+  if (d2h) *d2h = ctx->d2h;
   return WADG_OK;
 }
 
@@ -1154,6 +1372,7 @@ wadg_status wadg_run_steps(wadg_ctx* ctx, int64_t nsteps, double dt, double* pro
     const int64_t n = std::min(chunk, nsteps - done);
     double tt = ctx->t + done * dt;
     CK(cudaMemcpyAsync(ctx->tdev.p, &tt, 8, cudaMemcpyHostToDevice, ctx->stream));
+    ctx->h2d += 8;
     CK(cudaMemsetAsync(ctx->stepdev.p, 0, 8, ctx->stream));
     for (int64_t i = 0; i < n; ++i) {
       CK(cudaGraphLaunch(ctx->graph[ctx->cur], ctx->stream));
@@ -1162,6 +1381,7 @@ wadg_status wadg_run_steps(wadg_ctx* ctx, int64_t nsteps, double dt, double* pro
     if (probe_out && rec) {
       CK(cudaMemcpyAsync(probe_out + (size_t)done * rec, ctx->pr_out.p, (size_t)n * rec * 8,
                          cudaMemcpyDeviceToHost, ctx->stream));
+      ctx->d2h += (size_t)n * rec * 8;
     }
     CK(cudaStreamSynchronize(ctx->stream));
     done += n;
@@ -1177,6 +1397,7 @@ wadg_status wadg_run_steps(wadg_ctx* ctx, int64_t nsteps, double dt, double* pro
   else CK(launch_check_finite<float>((const float*)ctx->q[ctx->cur].p, nq, (int*)ctx->flag.p, ctx->stream));
   int flag = 0;
   CK(cudaMemcpyAsync(&flag, ctx->flag.p, 4, cudaMemcpyDeviceToHost, ctx->stream));
+  ctx->d2h += 4;
   CK(cudaStreamSynchronize(ctx->stream));
   if (flag) return fail(ctx, WADG_ENONFINITE, "state became non-finite");
   return WADG_OK;
@@ -1202,7 +1423,7 @@ wadg_status wadg_profile_stage(wadg_ctx* ctx, int reps, double dt, double* ms_ou
       } else {
         StageParams<float> P = stage_params<float>(ctx, stage, dt, ctx->t, false, cls == 1);
         if (cls == 1) CK(launch_pml_class<float>(ctx, P));
-        else if (ctx->tc) CK(launch_stage_tc(ctx->N, false, P, ctx->nb, ctx->stream, ctx->bf16));
+        else if (ctx->tc) CK(launch_stage_tc(ctx->N, false, P, ctx->nb, ctx->stream, ctx->bf16, ctx->qc));
         else CK(launch_stage<float>(ctx->N, false, false, P, ctx->nb, ctx->stream));
       }
       CK(cudaEventRecord(ev[2 * cls + 1], ctx->stream));
@@ -1365,7 +1586,7 @@ wadg_status adjoint_typed(wadg_ctx* ctx, int64_t nsteps, double dt, int C, doubl
         A.rk_a = kRkA[i];
         A.rk_b = kRkB[i];
         A.t = tn + kRkC.c[i] * dt;
-        CK(launch_adjoint_stage<Real>(ctx->N, A, nb, ctx->stream));
+        CK(launch_adjoint_stage<Real>(ctx->N, A, nb, ctx->stream, ctx->qc));
       }
     }
   }
@@ -1435,6 +1656,7 @@ wadg_status wadg_objective(wadg_ctx* ctx, double* J_out) {
   cudaSetDevice(ctx->device);
   CK(cudaStreamSynchronize(ctx->stream));
   CK(cudaMemcpy(J_out, ctx->obj.p, 8 * (size_t)ctx->nb, cudaMemcpyDeviceToHost));
+  ctx->d2h += 8 * (size_t)ctx->nb;
   return WADG_OK;
 }
 
@@ -1457,7 +1679,7 @@ wadg_status wadg_mesh_info(const wadg_ctx* ctx, int64_t* K, int64_t* K_pml, int3
   if (K) *K = ctx->K;
   if (K_pml) *K_pml = ctx->K1;
   if (Np) *Np = ctx->ref.Np;
-  if (Nq) *Nq = ctx->ref.Nq;
+  if (Nq) *Nq = ctx->ref.Nq_rule;
   return WADG_OK;
 }
 
@@ -1558,7 +1780,7 @@ wadg_status noalloc_stage(wadg_ctx* ctx, int stage, double dt, const double* tde
   if (ctx->tc) {
     StageParams<float> A = stage_params<float>(ctx, stage, dt, 0.0, false, false);
     A.t_dev = tdev;
-    CK(launch_stage_tc(ctx->N, false, A, ctx->nb, ctx->stream, ctx->bf16));
+    CK(launch_stage_tc(ctx->N, false, A, ctx->nb, ctx->stream, ctx->bf16, ctx->qc));
     if (ctx->K1 > 0) {
       StageParams<float> B = stage_params<float>(ctx, stage, dt, 0.0, false, true);
       B.t_dev = tdev;
@@ -1606,6 +1828,7 @@ extern "C" wadg_status wadg_run_steps_noalloc(wadg_ctx* ctx, int64_t nsteps, dou
     // the array keeps the previous call's contents: set the counters
     const double tt = ctx->t + done * dt;
     CK(cudaMemcpyAsync(tdev, &tt, 8, cudaMemcpyHostToDevice, ctx->stream));
+    ctx->h2d += 8;
     CK(cudaMemsetAsync(stepdev, 0, 8, ctx->stream));
     for (int64_t i = 0; i < n; ++i) {
       for (int st = 0; st < 5; ++st) {
@@ -1629,9 +1852,11 @@ extern "C" wadg_status wadg_run_steps_noalloc(wadg_ctx* ctx, int64_t nsteps, dou
       }
       CK(launch_advance(tdev, stepdev, dt, ctx->stream));
     }
-    if (probe_out && rec)
+    if (probe_out && rec) {
       CK(cudaMemcpyAsync(probe_out + (size_t)done * rec, rec_dev, (size_t)n * rec * 8,
                          cudaMemcpyDeviceToHost, ctx->stream));
+      ctx->d2h += (size_t)n * rec * 8;
+    }
     CK(cudaStreamSynchronize(ctx->stream));
     done += n;
   }
@@ -1644,6 +1869,7 @@ extern "C" wadg_status wadg_run_steps_noalloc(wadg_ctx* ctx, int64_t nsteps, dou
   else CK(launch_check_finite<float>((const float*)ctx->q[ctx->cur].p, nq, flag, ctx->stream));
   int hflag = 0;
   CK(cudaMemcpyAsync(&hflag, flag, 4, cudaMemcpyDeviceToHost, ctx->stream));
+  ctx->d2h += 4;
   CK(cudaStreamSynchronize(ctx->stream));
   if (hflag) return fail(ctx, WADG_ENONFINITE, "state became non-finite");
   return WADG_OK;
@@ -1700,7 +1926,7 @@ wadg_status gfail(wadg_group* g, wadg_status s, const char* fmt, ...) {
 wadg_status group_members_ready(wadg_group* g) {
   for (size_t c = 0; c < g->ctx.size(); ++c) {
     const wadg_ctx* x = g->ctx[c];
-    if (!x->has_mesh || !x->ready || !x->src_ok || !x->probes_ok)
+    if (!x->has_mesh || !x->ready || !x->src_ok || !x->probes_ok || !x->ops_ok)
       return gfail(g, WADG_ESTATE, "member %d has an incomplete set-up (a set-up call failed)",
                    (int)c);
   }
@@ -1863,10 +2089,13 @@ wadg_status wadg_group_create(int32_t n, wadg_ctx* const* ctxs, wadg_group** out
   for (int i = 0; i < n; ++i) {
     wadg_ctx* x = ctxs[i];
     if (!x) return fail(nullptr, WADG_EINVAL, "null context %d", i);
-    if (!x->has_mesh || !x->ready || !x->src_ok || !x->probes_ok)
+    if (!x->has_mesh || !x->ready || !x->src_ok || !x->probes_ok || !x->ops_ok)
       return fail(nullptr, WADG_ESTATE, "context %d has no mesh or an incomplete set-up", i);
     if (x->prec != WADG_FP32 || x->tc)
       return fail(nullptr, WADG_EUNSUPPORTED, "groups run the FP32 CUDA-core kernels (context %d)", i);
+    if (x->qc != 0)
+      return fail(nullptr, WADG_EUNSUPPORTED,
+                  "groups run the default (N+1)^3-point volume rule (context %d)", i);
     if (x->scheme == WADG_PML_STORED)
       return fail(nullptr, WADG_EUNSUPPORTED, "groups run the weight-adjusted kernels (context %d)", i);
     if (x->device != ctxs[0]->device)

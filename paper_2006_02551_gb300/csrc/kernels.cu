@@ -6,31 +6,32 @@
 
 namespace wadg {
 
-template <typename Real, int N, bool PML, bool KAPPA, bool STORED = false>
-__global__ void __launch_bounds__(Tile<Real, N, PML>::THREADS)
+template <typename Real, int N, bool PML, bool KAPPA, bool STORED = false, int QC = 0>
+__global__ void __launch_bounds__(Tile<Real, N, PML, 0, QC>::THREADS)
 stage_kernel(const StageParams<Real> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  stage_body<Real, N, PML, KAPPA, STORED, 0>(P, smem_raw, blockIdx.x, gridDim.x);
+  stage_body<Real, N, PML, KAPPA, STORED, 0, QC>(P, smem_raw, blockIdx.x, gridDim.x);
 }
 
-template <typename Real, int N, bool PML, bool KAPPA, bool STORED = false>
+template <typename Real, int N, bool PML, bool KAPPA, bool STORED = false, int QC = 0>
 static cudaError_t configure_one() {
-  using TL = Tile<Real, N, PML>;
-  return cudaFuncSetAttribute(stage_kernel<Real, N, PML, KAPPA, STORED>,
+  using TL = Tile<Real, N, PML, 0, QC>;
+  return cudaFuncSetAttribute(stage_kernel<Real, N, PML, KAPPA, STORED, QC>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL::smem);
 }
 
 // resident blocks per SM of one stage-kernel instance (cached per instance)
-template <typename Real, int N, bool PML, bool KAPPA, bool STORED = false>
+template <typename Real, int N, bool PML, bool KAPPA, bool STORED = false, int QC = 0>
 static int resident_blocks() {
   static int cached = 0;
   if (cached == 0) {
-    using TL = Tile<Real, N, PML>;
+    using TL = Tile<Real, N, PML, 0, QC>;
     int nb = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stage_kernel<Real, N, PML, KAPPA, STORED>,
-                                                      TL::THREADS, TL::smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &nb, stage_kernel<Real, N, PML, KAPPA, STORED, QC>, TL::THREADS, TL::smem) !=
+            cudaSuccess ||
         nb < 1)
       nb = 1;
     cached = nb * (sms > 0 ? sms : 1);
@@ -38,16 +39,16 @@ static int resident_blocks() {
   return cached;
 }
 
-template <typename Real, int N, bool PML, bool KAPPA, bool STORED = false>
+template <typename Real, int N, bool PML, bool KAPPA, bool STORED = false, int QC = 0>
 static cudaError_t launch_one(const StageParams<Real>& P, int nb, cudaStream_t s) {
-  using TL = Tile<Real, N, PML>;
+  using TL = Tile<Real, N, PML, 0, QC>;
   if (P.n_elem <= 0) return cudaSuccess;
   StageParams<Real> Q = P;
   Q.nb = nb;
   const long long tiles = (long long)((P.n_elem + TL::T - 1) / TL::T) * nb;
   const int grid =
-      (int)std::min<long long>(tiles, resident_blocks<Real, N, PML, KAPPA, STORED>());
-  stage_kernel<Real, N, PML, KAPPA, STORED><<<grid, TL::THREADS, TL::smem, s>>>(Q);
+      (int)std::min<long long>(tiles, resident_blocks<Real, N, PML, KAPPA, STORED, QC>());
+  stage_kernel<Real, N, PML, KAPPA, STORED, QC><<<grid, TL::THREADS, TL::smem, s>>>(Q);
   return cudaGetLastError();
 }
 
@@ -56,6 +57,8 @@ static cudaError_t configure_n() {
   cudaError_t e = configure_one<Real, N, false, false>();
   if (e == cudaSuccess) e = configure_one<Real, N, true, false>();
   if (e == cudaSuccess) e = configure_one<Real, N, true, true>();
+  if (e == cudaSuccess) e = configure_one<Real, N, true, false, false, 1>();
+  if (e == cudaSuccess) e = configure_one<Real, N, true, true, false, 1>();
   return e;
 }
 
@@ -75,28 +78,32 @@ template cudaError_t configure_stage_kernels<float>(int);
 
 template <typename Real, int N>
 static cudaError_t dispatch_pml(bool pml, bool kappa, const StageParams<Real>& P, int nb,
-                                cudaStream_t s) {
+                                cudaStream_t s, int qc) {
   if (!pml) return launch_one<Real, N, false, false>(P, nb, s);
+  if (qc) {
+    if (kappa) return launch_one<Real, N, true, true, false, 1>(P, nb, s);
+    return launch_one<Real, N, true, false, false, 1>(P, nb, s);
+  }
   if (kappa) return launch_one<Real, N, true, true>(P, nb, s);
   return launch_one<Real, N, true, false>(P, nb, s);
 }
 
 template <typename Real>
 cudaError_t launch_stage(int N, bool pml, bool kappa, const StageParams<Real>& P, int nb,
-                         cudaStream_t s) {
+                         cudaStream_t s, int qc) {
   switch (N) {
-    case 1: return dispatch_pml<Real, 1>(pml, kappa, P, nb, s);
-    case 2: return dispatch_pml<Real, 2>(pml, kappa, P, nb, s);
-    case 3: return dispatch_pml<Real, 3>(pml, kappa, P, nb, s);
-    case 4: return dispatch_pml<Real, 4>(pml, kappa, P, nb, s);
-    case 5: return dispatch_pml<Real, 5>(pml, kappa, P, nb, s);
+    case 1: return dispatch_pml<Real, 1>(pml, kappa, P, nb, s, qc);
+    case 2: return dispatch_pml<Real, 2>(pml, kappa, P, nb, s, qc);
+    case 3: return dispatch_pml<Real, 3>(pml, kappa, P, nb, s, qc);
+    case 4: return dispatch_pml<Real, 4>(pml, kappa, P, nb, s, qc);
+    case 5: return dispatch_pml<Real, 5>(pml, kappa, P, nb, s, qc);
     default: return cudaErrorInvalidValue;
   }
 }
 template cudaError_t launch_stage<double>(int, bool, bool, const StageParams<double>&, int,
-                                          cudaStream_t);
+                                          cudaStream_t, int);
 template cudaError_t launch_stage<float>(int, bool, bool, const StageParams<float>&, int,
-                                         cudaStream_t);
+                                         cudaStream_t, int);
 
 // ------------------------------------------------------- stored-matrix scheme
 template <typename Real>
@@ -367,5 +374,51 @@ cudaError_t launch_check_finite(const Real* a, int64_t n, int* flag, cudaStream_
 }
 template cudaError_t launch_check_finite<double>(const double*, int64_t, int*, cudaStream_t);
 template cudaError_t launch_check_finite<float>(const float*, int64_t, int*, cudaStream_t);
+
+// State exchange with a caller's device array in the layout of the C ABI,
+// user[b][k][12][Np] (double, caller element order k = perm[e]), against the
+// internal E,H blocks q[b][e][6][Np] and P blocks p[b][e - K0][6][Np]
+// (Real).  One thread per (b, e, component, node); consecutive threads walk
+// the nodes of one internal block (contiguous on both sides).
+template <typename Real>
+__global__ void state_exchange_kernel(bool to_internal, const int* perm, int64_t K, int64_t K0,
+                                      int Np, int nb, double* user, Real* q, Real* p) {
+  const int64_t n = (int64_t)nb * K * 12 * Np;
+  const int64_t K1 = K - K0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int node = (int)(i % Np);
+    int64_t r = i / Np;
+    const int c = (int)(r % 12);
+    r /= 12;
+    const int64_t e = r % K;
+    const int64_t b = r / K;
+    double* u = user + ((b * K + perm[e]) * 12 + c) * Np + node;
+    Real* in = nullptr;
+    if (c < 6) in = q + ((b * K + e) * 6 + c) * Np + node;
+    else if (e >= K0) in = p + ((b * K1 + (e - K0)) * 6 + (c - 6)) * Np + node;
+    if (to_internal) {
+      if (in) *in = (Real)*u;
+    } else {
+      *u = in ? (double)*in : 0.0;
+    }
+  }
+}
+
+template <typename Real>
+cudaError_t launch_state_exchange(bool to_internal, const int* perm, int64_t K, int64_t K0,
+                                  int Np, int nb, double* user, Real* q, Real* p,
+                                  cudaStream_t s) {
+  const int64_t n = (int64_t)nb * K * 12 * Np;
+  if (n == 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 8);
+  state_exchange_kernel<Real><<<(unsigned)blocks, 256, 0, s>>>(to_internal, perm, K, K0, Np, nb,
+                                                               user, q, p);
+  return cudaGetLastError();
+}
+template cudaError_t launch_state_exchange<double>(bool, const int*, int64_t, int64_t, int, int,
+                                                   double*, double*, double*, cudaStream_t);
+template cudaError_t launch_state_exchange<float>(bool, const int*, int64_t, int64_t, int, int,
+                                                  double*, float*, float*, cudaStream_t);
 
 }  // namespace wadg

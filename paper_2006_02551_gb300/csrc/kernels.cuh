@@ -38,6 +38,18 @@ __device__ __forceinline__ bool wadg_index_ok(bool ok, int* status) {
 #define WADG_INDEX_OK(cond, status) true
 #endif
 
+// Volume quadrature capacity of the PML stage kernels (eqs. 20, 21, 26-29).
+// Class 0: the default conical-product rule of (N+1)^3 points.  Class 1:
+// compact rules of degree 2N of at most compact_nq(N) points (a rule with
+// fewer points is padded with zero-weight points).  The kernels are compiled
+// for both classes; the context picks one from the size of its rule.
+__host__ __device__ constexpr int compact_nq(int N) {
+  return N == 1 ? 4 : N == 2 ? 14 : N == 3 ? 24 : N == 4 ? 48 : N == 5 ? 84 : 0;
+}
+__host__ __device__ constexpr int quad_capacity(int N, int qc) {
+  return qc ? compact_nq(N) : (N + 1) * (N + 1) * (N + 1);
+}
+
 struct SrcDev {
   int elem;     // internal element id
   int batch;
@@ -123,24 +135,31 @@ struct ProbeParams {
 };
 
 // launchers (return cudaError_t of the launch)
+// qc: quadrature class of the PML kernels (quad_capacity)
 template <typename Real>
 cudaError_t configure_stage_kernels(int N);  // once per device, outside graph capture
 template <typename Real>
 cudaError_t launch_stage(int N, bool pml, bool kappa, const StageParams<Real>& P, int nb,
-                         cudaStream_t s);
+                         cudaStream_t s, int qc = 0);
 cudaError_t launch_probes(bool fp64, const ProbeParams& P, cudaStream_t s);
 template <typename Real>
 cudaError_t configure_adjoint_kernels(int N);
 template <typename Real>
-cudaError_t launch_adjoint_stage(int N, const AdjParams<Real>& P, int nb, cudaStream_t s);
+cudaError_t launch_adjoint_stage(int N, const AdjParams<Real>& P, int nb, cudaStream_t s,
+                                 int qc = 0);
 template <typename Real>
 cudaError_t launch_adjoint_probes(const Real* q, int64_t strideQ, int nprobe, int nb, int Np,
                                   const int* elem, const double* ell, Real* lam, cudaStream_t s);
 // tensor-core (tcgen05) stage kernels: TF32 operands, or BF16 operands (bf16)
-bool tc_supported(int N, bool kappa, bool bf16);
+// tc_supported: whether a tensor-core stage exists for (N, bf16, qc)
+bool tc_supported(int N, bool kappa, bool bf16, int qc = 0);
 cudaError_t configure_tc_kernels(int N, bool bf16);
 cudaError_t launch_stage_tc(int N, bool pml, const StageParams<float>& P, int nb, cudaStream_t s,
-                            bool bf16);
+                            bool bf16, int qc = 0);
+// row-owned tensor-core PML stage kernels (compact volume rules)
+cudaError_t configure_tc_rows(int N, bool bf16);
+cudaError_t launch_pml_tc_rows(int N, const StageParams<float>& P, int nb, cudaStream_t s,
+                               bool bf16);
 cudaError_t launch_advance(double* t_dev, int64_t* step_dev, double dt, cudaStream_t s);
 template <typename Real>
 cudaError_t launch_pml_samples(int Nq, int K1, int K0, const double* verts,
@@ -181,5 +200,13 @@ cudaError_t launch_group_stage(const GroupParams& G, int nblocks, size_t smem, i
                                cudaStream_t s);
 template <typename Real>
 cudaError_t launch_check_finite(const Real* a, int64_t n, int* flag, cudaStream_t s);
+// state exchange between a caller's device array user[nb][K][12][Np] (double,
+// caller element order, perm[internal] = caller id) and the internal E,H and
+// P blocks; to_internal selects the direction (P of non-PML elements: ignored
+// / written as zero)
+template <typename Real>
+cudaError_t launch_state_exchange(bool to_internal, const int* perm, int64_t K, int64_t K0,
+                                  int Np, int nb, double* user, Real* q, Real* p,
+                                  cudaStream_t s);
 
 }  // namespace wadg

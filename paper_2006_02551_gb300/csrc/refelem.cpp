@@ -13,6 +13,7 @@
 // weights from the Christoffel function.
 #include "refelem.hpp"
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -243,6 +244,70 @@ void stroud_rule(int n, std::vector<double>& r, std::vector<double>& s, std::vec
       }
 }
 
+bool set_volume_rule(RefOps& o, const std::vector<double>& r, const std::vector<double>& s,
+                     const std::vector<double>& t, const std::vector<double>& w, int pad_to,
+                     const char** err) {
+  const int Np = o.Np;
+  const int n = static_cast<int>(w.size());
+  if (n < 1 || r.size() != w.size() || s.size() != w.size() || t.size() != w.size()) {
+    *err = "empty or inconsistent quadrature rule";
+    return false;
+  }
+  for (int q = 0; q < n; ++q) {
+    // barycentric coordinates of the point on the reference tetrahedron
+    const double l1 = 0.5 * (1.0 + r[q]), l2 = 0.5 * (1.0 + s[q]), l3 = 0.5 * (1.0 + t[q]);
+    const double l0 = 1.0 - l1 - l2 - l3;
+    if (!(w[q] > 0.0) || l0 < -1e-12 || l1 < -1e-12 || l2 < -1e-12 || l3 < -1e-12) {
+      *err = "quadrature weights must be positive and points inside the tetrahedron";
+      return false;
+    }
+  }
+  const int Nq = pad_to > n ? pad_to : n;
+  // padding points: zero weight at the centroid (no contribution to P_q)
+  std::vector<double> rr(r), ss(s), tt(t), ww(w);
+  for (int q = n; q < Nq; ++q) {
+    rr.push_back(-0.5);
+    ss.push_back(-0.5);
+    tt.push_back(-0.5);
+    ww.push_back(0.0);
+  }
+  std::vector<double> Vq(static_cast<size_t>(Nq) * Np), Pq(static_cast<size_t>(Np) * Nq);
+  for (int q = 0; q < Nq; ++q) {
+    std::vector<double> l = o.lagrange_at(rr[q], ss[q], tt[q]);
+    for (int i = 0; i < Np; ++i) Vq[static_cast<size_t>(q) * Np + i] = l[i];
+  }
+  // P_q = M^{-1} V_q^T W
+  for (int i = 0; i < Np; ++i)
+    for (int q = 0; q < Nq; ++q) {
+      double a = 0.0;
+      for (int j = 0; j < Np; ++j) a += o.Minv[i * Np + j] * Vq[static_cast<size_t>(q) * Np + j];
+      Pq[static_cast<size_t>(i) * Nq + q] = a * ww[q];
+    }
+  // the rule must integrate products of two degree-N polynomials exactly:
+  // P_q V_q = M^{-1} (V_q^T W V_q) is then the identity
+  double dev = 0.0;
+  for (int i = 0; i < Np; ++i)
+    for (int j = 0; j < Np; ++j) {
+      double a = 0.0;
+      for (int q = 0; q < Nq; ++q)
+        a += Pq[static_cast<size_t>(i) * Nq + q] * Vq[static_cast<size_t>(q) * Np + j];
+      dev = std::max(dev, std::fabs(a - (i == j ? 1.0 : 0.0)));
+    }
+  if (!(dev < 1e-10)) {
+    *err = "the quadrature rule is not exact for polynomials of degree 2N (P_q V_q != I)";
+    return false;
+  }
+  o.rq = rr;
+  o.sq = ss;
+  o.tq = tt;
+  o.wq = ww;
+  o.Nq = Nq;
+  o.Nq_rule = n;
+  o.Vq = Vq;
+  o.Pq = Pq;
+  return true;
+}
+
 bool build_ref_ops(int N, RefOps& o, const char** err) {
   if (N < 1 || N > 6) {
     *err = "polynomial order N must be in 1..6";
@@ -321,23 +386,12 @@ bool build_ref_ops(int N, RefOps& o, const char** err) {
       }
   }
   o.LIFT = matmul(o.Minv, E, Np, Np, 4 * Nfp);
-  // volume quadrature of degree 2N+1
-  stroud_rule(N + 1, o.rq, o.sq, o.tq, o.wq);
-  o.Nq = static_cast<int>(o.rq.size());
-  const int Nq = o.Nq;
-  o.Vq.assign(static_cast<size_t>(Nq) * Np, 0.0);
-  for (int q = 0; q < Nq; ++q) {
-    std::vector<double> l = o.lagrange_at(o.rq[q], o.sq[q], o.tq[q]);
-    for (int i = 0; i < Np; ++i) o.Vq[static_cast<size_t>(q) * Np + i] = l[i];
+  // default volume quadrature: the conical-product rule of degree 2N+1
+  {
+    std::vector<double> qr, qs, qt, qw;
+    stroud_rule(N + 1, qr, qs, qt, qw);
+    if (!set_volume_rule(o, qr, qs, qt, qw, 0, err)) return false;
   }
-  // P_q = M^{-1} V_q^T W
-  o.Pq.assign(static_cast<size_t>(Np) * Nq, 0.0);
-  for (int i = 0; i < Np; ++i)
-    for (int q = 0; q < Nq; ++q) {
-      double a = 0.0;
-      for (int j = 0; j < Np; ++j) a += o.Minv[i * Np + j] * o.Vq[static_cast<size_t>(q) * Np + j];
-      o.Pq[static_cast<size_t>(i) * Nq + q] = a * o.wq[q];
-    }
   // face-node permutation table
   o.fperm.assign(4 * 24 * Nfp, -1);
   o.fmap.assign(4 * 24 * Nfp, 0);

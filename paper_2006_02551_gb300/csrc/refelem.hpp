@@ -17,7 +17,10 @@ struct RefOps {
   std::vector<double> Dr, Ds, Dt;     // [Np][Np]
   std::vector<int> Fmask;             // [4][Nfp] volume node of face node
   std::vector<double> LIFT;           // [Np][4 Nfp]
-  std::vector<double> rq, sq, tq, wq; // quadrature [Nq]
+  // volume quadrature [Nq]: the rule's Nq_rule points, then zero-weight
+  // padding points (at the centroid) up to the kernels' capacity Nq
+  int Nq_rule = 0;
+  std::vector<double> rq, sq, tq, wq;
   std::vector<double> Vq;             // [Nq][Np]
   std::vector<double> Pq;             // [Np][Nq]
   // face-node permutation table: for local face f, neighbour face nf and
@@ -34,8 +37,18 @@ struct RefOps {
 void stroud_rule(int n, std::vector<double>& r, std::vector<double>& s, std::vector<double>& t,
                  std::vector<double>& w);
 
-// Builds all operators; returns false (and a message) on failure.
+// Builds all operators (with the default conical-product volume rule of
+// degree 2N+1); returns false (and a message) on failure.
 bool build_ref_ops(int N, RefOps& out, const char** err);
+
+// Replaces the volume quadrature (eqs. 20, 21) by the rule (r, s, t, w),
+// padded with zero-weight points up to pad_to points, and rebuilds V_q and
+// P_q = M^-1 V_q^T W.  Refuses (false and a message) a rule with a weight
+// that is not positive, a point outside the tetrahedron, or one that does not
+// integrate degree 2N exactly (P_q V_q must be the identity to 1e-10).
+bool set_volume_rule(RefOps& o, const std::vector<double>& r, const std::vector<double>& s,
+                     const std::vector<double>& t, const std::vector<double>& w, int pad_to,
+                     const char** err);
 
 // the six permutations of three face vertices used to encode rotations
 extern const int kFacePerm[6][3];

@@ -24,11 +24,11 @@
 
 namespace wadg {
 
-template <int N>
+template <int N, int QC = 0>
 struct Dims {
   static constexpr int Np = (N + 1) * (N + 2) * (N + 3) / 6;
   static constexpr int Nfp = (N + 1) * (N + 2) / 2;
-  static constexpr int Nq = (N + 1) * (N + 1) * (N + 1);
+  static constexpr int Nq = quad_capacity(N, QC);   // volume quadrature points
   static constexpr int NF = 4 * Nfp;
   static constexpr int NpP = (Np + 3) & ~3;   // padded to whole quads
   static constexpr int NqP = (Nq + 3) & ~3;
@@ -38,9 +38,9 @@ struct Dims {
 
 // Launch configuration: persistent blocks, the reference operators staged in
 // shared memory once per block, tiles of T elements processed in a loop.
-template <typename Real, int N, bool PML, int NT_ = 0>
+template <typename Real, int N, bool PML, int NT_ = 0, int QC = 0>
 struct Tile {
-  using D = Dims<N>;
+  using D = Dims<N, QC>;
   // threads of a block: the single-class launches use 512 for FP32 PML tiles;
   // the grouped launch fixes 256 for every class
   static constexpr int THREADS = NT_ > 0 ? NT_ : ((sizeof(Real) == 4 && PML) ? 512 : 256);
@@ -117,13 +117,13 @@ __device__ __forceinline__ void lds2(const double* p, double* v) {
 // takes tiles bid, bid + nblk, ...  Dynamic schedule (dyn != nullptr, the
 // grouped launch): the block takes tiles from the counter *dyn until they run
 // out.
-template <typename Real, int N, bool PML, bool KAPPA, bool STORED, int NT_>
+template <typename Real, int N, bool PML, bool KAPPA, bool STORED, int NT_, int QC = 0>
 __device__ __forceinline__ void stage_body(const StageParams<Real>& P, unsigned char* smem_raw,
                                            int bid, int nblk, int* dyn = nullptr) {
-  using D = Dims<N>;
+  using D = Dims<N, QC>;
   constexpr int Np = D::Np, Nfp = D::Nfp, Nq = D::Nq, NF = D::NF;
   constexpr int NpP = D::NpP, NqP = D::NqP, NIQ = D::NIQ, NQQ = D::NQQ;
-  using TL = Tile<Real, N, PML, NT_>;
+  using TL = Tile<Real, N, PML, NT_, QC>;
   constexpr int T = TL::T, CF = TL::CF, NT = TL::THREADS;
   Real* sm = reinterpret_cast<Real*>(smem_raw);
   const Real* DrT = TL::OPS_SMEM ? sm : P.ops;   // operators

@@ -23,8 +23,7 @@
 // Waits on the MMA-completion mbarrier are bounded; on timeout the kernel
 // records an error and stops after releasing its tensor memory.
 #include "kernels.cuh"
-
-#include <cuda_bf16.h>
+#include "tc_ptx.cuh"
 
 #include <algorithm>
 #include <cstdint>
@@ -32,275 +31,24 @@
 namespace wadg {
 namespace tc {
 
-__device__ __forceinline__ uint32_t saddr(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte
-// offsets, fixed 0b001 at bits 46-48, no swizzle
-__device__ __forceinline__ uint64_t make_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= static_cast<uint64_t>((addr & 0x3FFFFu) >> 4);
-  d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16;
-  d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32;
-  d |= static_cast<uint64_t>(1) << 46;
-  return d;
-}
-
-// instruction descriptor, kind::tf32: D f32, A and B tf32, both K-major
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
-         (static_cast<uint32_t>(M >> 4) << 24);
-}
-
-// instruction descriptor, kind::f16 with BF16 A and B: D f32, both K-major
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
-         (static_cast<uint32_t>(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accum) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(idesc), "r"(accum)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accum) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(idesc), "r"(accum)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-      : "memory");
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t a, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(a), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// wait for the given phase parity; gives up (false) after about a second of
-// global time, or after 2^24 polls, whichever comes first.  A product or an
-// operand tile takes microseconds, so only a signal that never comes reaches
-// the limit.
-constexpr uint64_t kWaitLimitNs = 1000000000ull;
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
-  if (mbar_try_wait(a, parity)) return true;
-  const uint64_t t0 = global_ns();
-  for (int i = 0; i < (1 << 24); ++i) {
-    if (mbar_try_wait(a, parity)) return true;
-    if (global_ns() - t0 > kWaitLimitNs) break;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t dst, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst),
-               "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
-               : "memory");
-}
-__device__ __forceinline__ void fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// this thread's lane of 2 / 4 consecutive TMEM columns (load and wait fused so
-// the registers are valid when the statement ends)
-__device__ __forceinline__ void tld2(uint32_t taddr, float* v) {
-  uint32_t r0, r1;
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];\n\t"
-      "tcgen05.wait::ld.sync.aligned;"
-      : "=r"(r0), "=r"(r1)
-      : "r"(taddr)
-      : "memory");
-  v[0] = __uint_as_float(r0);
-  v[1] = __uint_as_float(r1);
-}
-__device__ __forceinline__ void tld4(uint32_t taddr, float* v) {
-  uint32_t r0, r1, r2, r3;
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];\n\t"
-      "tcgen05.wait::ld.sync.aligned;"
-      : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-      : "r"(taddr)
-      : "memory");
-  v[0] = __uint_as_float(r0);
-  v[1] = __uint_as_float(r1);
-  v[2] = __uint_as_float(r2);
-  v[3] = __uint_as_float(r3);
-}
-__device__ __forceinline__ void tld6(uint32_t taddr, float* v) {
-  tld4(taddr, v);
-  tld2(taddr + 4, v + 4);
-}
-
-// 6 consecutive columns at each of two / four column addresses, one wait
-// the same at two pairs of column addresses (two elements), one wait
-__device__ __forceinline__ void tld_6x2x2(uint32_t a0, uint32_t a1, uint32_t b0, uint32_t b1,
-                                          float* v) {
-  uint32_t r[24];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%24];\n\t"
-      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%4, %5}, [%25];\n\t"
-      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%6, %7, %8, %9}, [%26];\n\t"
-      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%10, %11}, [%27];\n\t"
-      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%12, %13, %14, %15}, [%28];\n\t"
-      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%16, %17}, [%29];\n\t"
-      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%18, %19, %20, %21}, [%30];\n\t"
-      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%22, %23}, [%31];\n\t"
-      "tcgen05.wait::ld.sync.aligned;"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23])
-      : "r"(a0), "r"(a0 + 4), "r"(a1), "r"(a1 + 4), "r"(b0), "r"(b0 + 4), "r"(b1), "r"(b1 + 4)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 24; ++i) v[i] = __uint_as_float(r[i]);
-}
-__device__ __forceinline__ void tld_6x2(uint32_t a0, uint32_t a1, float* v) {
-  uint32_t r[12];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%12];\n\t"
-      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%4, %5}, [%13];\n\t"
-      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%6, %7, %8, %9}, [%14];\n\t"
-      "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%10, %11}, [%15];\n\t"
-      "tcgen05.wait::ld.sync.aligned;"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11])
-      : "r"(a0), "r"(a0 + 4), "r"(a1), "r"(a1 + 4)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 12; ++i) v[i] = __uint_as_float(r[i]);
-}
-__device__ __forceinline__ void tld_6x4(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                        float* v) {
-  tld_6x2(a0, a1, v);
-  tld_6x2(a2, a3, v + 12);
-}
-
-// named barrier 1 among the compute warps (warp-aligned, nthreads a multiple of 32)
-__device__ __forceinline__ void cbar_sync(int nthreads) {
-  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
-}
-// the same barrier with an AND reduction of a per-thread flag
-__device__ __forceinline__ bool cbar_and(int nthreads, bool v) {
-  uint32_t r;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
-      "bar.red.and.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}\n"
-      : "=r"(r)
-      : "r"((uint32_t)v), "r"(nthreads)
-      : "memory");
-  return r != 0;
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t a) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
-}
-
-// bulk global -> shared copy (both addresses 16-byte aligned, size a
-// multiple of 16) whose bytes complete on mbarrier `bar`
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
-                                         uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(dst), "l"(src), "r"(bytes), "r"(bar)
-      : "memory");
-}
-// arrive on `bar` and add `bytes` to the transaction count its phase waits for
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-
-// operand element: TF32 held in 32 bits (4 per 16-byte core-matrix row, 8 K
-// per instruction) or BF16 (8 per core-matrix row, 16 K per instruction)
-template <bool BF>
-struct OpT {
-  static constexpr int ES = BF ? 2 : 4;    // bytes
-  static constexpr int CW = 16 / ES;       // K per core-matrix row
-  static constexpr int KS = 2 * CW;        // K per instruction
-};
-
-__device__ __forceinline__ float to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
-// byte offset of (row r, k) in a K-major canonical tile: 8-row x 16-byte core
-// matrices, K-adjacent core matrices lbo bytes apart, 8-row groups sbo apart.
-// The field operands use lbo = 144 (one 16-byte gap per core matrix) so that
-// consecutive K written by consecutive lanes fall on distinct banks.
-template <bool BF>
-__host__ __device__ constexpr uint32_t cofs(int r, int k, uint32_t sbo, uint32_t lbo) {
-  using O = OpT<BF>;
-  return static_cast<uint32_t>(r >> 3) * sbo + static_cast<uint32_t>(k / O::CW) * lbo +
-         static_cast<uint32_t>(r & 7) * 16u + static_cast<uint32_t>(k % O::CW) * O::ES;
-}
-
-// one operand value, rounded to nearest in the operand type
-template <bool BF>
-__device__ __forceinline__ void put_op(unsigned char* p, float x) {
-  if constexpr (BF) *reinterpret_cast<__nv_bfloat16*>(p) = __float2bfloat16_rn(x);
-  else *reinterpret_cast<float*>(p) = to_tf32(x);
-}
-
-constexpr int rup8(int x) { return (x + 7) & ~7; }
-constexpr int rup16(int x) { return (x + 15) & ~15; }
-
-// Shared-memory plan of one tile (all offsets in bytes).
-template <int N, bool PML, bool BF = false>
+// Shared-memory plan of one tile (all offsets in bytes).  QC: quadrature
+// class of the volume rule (quad_capacity).
+template <int N, bool PML, bool BF = false, int QC = 0>
 struct Plan {
   using O = OpT<BF>;
   static constexpr int Np = (N + 1) * (N + 2) * (N + 3) / 6;
   static constexpr int Nfp = (N + 1) * (N + 2) / 2;
   static constexpr int NF = 4 * Nfp;
-  static constexpr int Nq = (N + 1) * (N + 1) * (N + 1);
+  static constexpr int Nq = quad_capacity(N, QC);
   __host__ __device__ static constexpr int rupK(int x) { return (x + O::KS - 1) / O::KS * O::KS; }
   static constexpr int NpK = rupK(Np), NFK = rupK(NF), NqK = rupK(Nq);
   // elements per tile: 8; 4 for BF16 PML tiles, whose smaller operands then
-  // let two blocks share an SM (N <= 4) or fit at all (N = 5)
+  // let two blocks share an SM (N <= 4) or fit at all (N = 5), and for TF32
+  // PML tiles at N = 5 (compact rule only)
   static constexpr bool PAIR = PML && BF && N <= 4;
-  static constexpr int T = PML && BF ? 4 : 8;
-  // one block per SM with 16 compute warps (TF32 PML; every BF16 N = 5 tile)
-  static constexpr bool ONE = PML ? !PAIR : (BF && N == 5);
+  static constexpr int T = PML && (BF || N == 5) ? 4 : 8;
+  // one block per SM with 16 compute warps (TF32 PML; every N = 5 tile)
+  static constexpr bool ONE = PML ? !PAIR : N == 5;
   static constexpr int NV = rup16(6 * T);            // columns of E,H products
   static constexpr int NQ = rup16(12 * T);           // columns of 12-component products
   static constexpr int G_p = NpK / 8;                // 8-row groups of an Np-row operator
@@ -325,14 +73,21 @@ struct Plan {
   static constexpr int RV = rup8(3 * Np);
   static constexpr uint32_t oVol = oL + G_p * SBO_L;
   static constexpr uint32_t oVq = oVol + (RV / 8) * SBO_V;
-  // V_q read as VQT products of 128 rows (quadrature points q and q + 128)
+  // V_q read as VQT products of 128 rows (quadrature points q and q + 128);
+  // the rows an instruction reads past the operator's own fall on the
+  // buffers that follow it
   static constexpr int VQT = (Nq + 127) / 128;
   // B operands
-  static constexpr uint32_t oBF = PML ? oVq + 16 * VQT * SBO_V : oVq;
+  static constexpr uint32_t oBF = PML ? oVq + (rup8(Nq) / 8) * SBO_V : oVq;
   static constexpr int ROWS_F = PML ? NQ : NV;        // E,H (+ P) rows
   static constexpr uint32_t oBFL = oBF + (ROWS_F / 8) * SBB_V;
   static constexpr uint32_t oBTZ = oBFL + (NV / 8) * SBB_L;
-  static constexpr uint32_t oRS = PML ? oBTZ + (NQ / 8) * SBB_Q : oBTZ;
+  // the (t, z) operand buffer later holds the P_q columns copied out of
+  // TMEM ([T][12][Np] floats), which can be the larger of the two
+  static constexpr uint32_t BTZ_BYTES = (NQ / 8) * SBB_Q;
+  static constexpr uint32_t DP_BYTES = T * 12 * Np * 4;
+  static constexpr uint32_t oRS =
+      PML ? oBTZ + (BTZ_BYTES > DP_BYTES ? BTZ_BYTES : DP_BYTES) : oBTZ;
   static constexpr int NpP = (Np + 3) & ~3;
   static constexpr uint32_t oGeo = oRS + (PML ? T * 6 * NpP * 4 : 0);
   static constexpr int TS = T * 6 * Np;               // floats of one staged field block
@@ -361,7 +116,6 @@ struct Plan {
   // to the field-operand buffers (free once the first products are done), the
   // P_q columns to the (t, z) buffer (free once P_q is done).
   static constexpr uint32_t DV_BYTES = T * 24 * Np * 4;
-  static constexpr uint32_t DP_BYTES = T * 12 * Np * 4;
   // (BF16 operand buffers are too small for the volume/LIFT dump: it gets its
   // own region)
   static constexpr bool DV_ALIAS = PML && !BF;
@@ -393,6 +147,7 @@ struct Plan {
   static_assert(oL + 16 * SBO_L <= bytes, "LIFT span");
   static_assert(oVol + ((VT - 1) * DPT * Np / 8 + 16) * SBO_V <= bytes, "volume operator span");
   static_assert(!PML || oVq + 16 * VQT * SBO_V <= bytes, "V_q span");
+  static_assert(VQT == 1 || Nq % 8 == 0, "second V_q product starts on a row group");
   static_assert(bytes <= 227 * 1024, "shared memory");
 };
 
@@ -408,9 +163,9 @@ struct Plan {
 // launch allocation to the compute warps (setmaxnreg), which removes their
 // spills (the launch holds every thread to the share of 5 or 6 warps per
 // scheduler).
-template <int N, bool PML, bool BF>
+template <int N, bool PML, bool BF, int QC = 0>
 struct TcWarps {
-  static constexpr bool ONE = Plan<N, PML, BF>::ONE;   // one block per SM
+  static constexpr bool ONE = Plan<N, PML, BF, QC>::ONE;   // one block per SM
   static constexpr int compute = ONE ? 16 : 8;
   static constexpr int issue = 4;
   static constexpr int threads = 32 * (compute + issue);
@@ -427,13 +182,15 @@ struct TcWarps {
                 "register split within the launch allocation");
 };
 
-template <int N, bool PML, bool BF>
-__global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, BF>::ONE ? 1 : 2)
+template <int N, bool PML, bool BF, int QC>
+__global__ void __launch_bounds__(TcWarps<N, PML, BF, QC>::threads,
+                                  TcWarps<N, PML, BF, QC>::ONE ? 1 : 2)
     tc_stage_kernel(const StageParams<float> P) {
-  using PL = Plan<N, PML, BF>;
-  constexpr int NW = TcWarps<N, PML, BF>::compute;
+  using PL = Plan<N, PML, BF, QC>;
+  using TW = TcWarps<N, PML, BF, QC>;
+  constexpr int NW = TW::compute;
   constexpr int kTcThreads = 32 * NW;          // compute threads
-  constexpr int kAll = TcWarps<N, PML, BF>::threads;
+  constexpr int kAll = TW::threads;
   constexpr int NGRP = NW / 4;                 // warps sharing a TMEM lane quadrant
   constexpr int Np = PL::Np, Nfp = PL::Nfp, NF = PL::NF, Nq = PL::Nq, T = PL::T;
   constexpr int NpK = PL::NpK, NFK = PL::NFK, NqK = PL::NqK;
@@ -678,7 +435,7 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
     // ---- issuing warpgroup: lane 0 of its first warp issues every product
     // of every tile of this block.  It first hands registers to the compute
     // warps (warpgroup-uniform).
-    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(TcWarps<N, PML, BF>::issue_regs));
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(TW::issue_regs));
     if (warp == NW && lane == 0) {
       uint32_t rph[3] = {0, 0, 0};   // parity of the operand-ready barriers 3, 4, 5
       bool issued = false, mfail = false;
@@ -757,7 +514,7 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
     }
     __syncwarp();
   } else {
-  asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(TcWarps<N, PML, BF>::compute_regs));
+  asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(TW::compute_regs));
   float Ep[FT][3], Hp[FT][3], ZPv[FT];
   int nbv[FT], codev[FT];
   float sgv[PML ? EH : 1][VQT][3];
@@ -1149,26 +906,26 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF>::threads, TcWarps<N, PML, 
   if (warp == 0) tmem_dealloc(tmem, PL::TMEM_COLS);
 }
 
-template <int N, bool PML, bool BF>
+template <int N, bool PML, bool BF, int QC>
 cudaError_t configure_n() {
-  using TW = TcWarps<N, PML, BF>;
+  using TW = TcWarps<N, PML, BF, QC>;
   // the compute warps' setmaxnreg.inc waits until the block's launch
   // allocation can cover the split: refuse a build whose compiled register
   // count would leave it short
   cudaFuncAttributes fa{};
-  cudaError_t e = cudaFuncGetAttributes(&fa, tc_stage_kernel<N, PML, BF>);
+  cudaError_t e = cudaFuncGetAttributes(&fa, tc_stage_kernel<N, PML, BF, QC>);
   if (e != cudaSuccess) return e;
   if ((long)fa.numRegs * TW::threads <
       32L * TW::compute * TW::compute_regs + 32L * TW::issue * TW::issue_regs)
     return cudaErrorInvalidConfiguration;
-  return cudaFuncSetAttribute(tc_stage_kernel<N, PML, BF>,
+  return cudaFuncSetAttribute(tc_stage_kernel<N, PML, BF, QC>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)Plan<N, PML, BF>::bytes);
+                              (int)Plan<N, PML, BF, QC>::bytes);
 }
 
-template <int N, bool PML, bool BF>
+template <int N, bool PML, bool BF, int QC>
 cudaError_t launch_n(const StageParams<float>& P, int nb, cudaStream_t s) {
-  using PL = Plan<N, PML, BF>;
+  using PL = Plan<N, PML, BF, QC>;
   if (P.n_elem <= 0) return cudaSuccess;
   static int sms = 0;
   if (sms == 0) {
@@ -1182,55 +939,77 @@ cudaError_t launch_n(const StageParams<float>& P, int nb, cudaStream_t s) {
   const long long tiles = (long long)((P.n_elem + PL::T - 1) / PL::T) * nb;
   const int per_sm = PL::ONE ? 1 : 512 / (int)PL::TMEM_COLS;
   const int grid = (int)std::min<long long>(tiles, (long long)per_sm * sms);
-  tc_stage_kernel<N, PML, BF><<<grid, TcWarps<N, PML, BF>::threads, PL::bytes, s>>>(Q);
+  tc_stage_kernel<N, PML, BF, QC><<<grid, TcWarps<N, PML, BF, QC>::threads, PL::bytes, s>>>(Q);
   return cudaGetLastError();
 }
 
 }  // namespace tc
 
-// TF32: N <= 4; BF16 operands, whose tiles are half the size, also N = 5
-bool tc_supported(int N, bool kappa, bool bf16) { return N >= 1 && N <= (bf16 ? 5 : 4) && !kappa; }
+// Tensor-core stages built: TF32 operands for N <= 4 (both rules) and N = 5
+// with the compact rule (its N = 5 operands with the (N+1)^3 rule do not fit
+// shared memory); BF16 operands for N <= 5 with either rule.  kappa = 1.
+bool tc_supported(int N, bool kappa, bool bf16, int qc) {
+  if (kappa || N < 1 || N > 5) return false;
+  return bf16 || N <= 4 || qc == 1;
+}
+
+template <int N, bool BF>
+cudaError_t configure_tc_n() {
+  cudaError_t e = cudaSuccess;
+  // the non-PML kernel has no quadrature; the PML kernels of both classes
+  if constexpr (BF || N <= 4) {
+    e = tc::configure_n<N, false, BF, 0>();
+    if (e == cudaSuccess) e = tc::configure_n<N, true, BF, 0>();
+  } else {
+    e = tc::configure_n<N, false, BF, 1>();
+  }
+  if (e == cudaSuccess) e = tc::configure_n<N, true, BF, 1>();
+  return e;
+}
 
 template <bool BF>
 cudaError_t configure_tc_bf(int N) {
-  cudaError_t e = cudaErrorInvalidValue;
   switch (N) {
-    case 1: e = tc::configure_n<1, false, BF>(); if (e == cudaSuccess) e = tc::configure_n<1, true, BF>(); break;
-    case 2: e = tc::configure_n<2, false, BF>(); if (e == cudaSuccess) e = tc::configure_n<2, true, BF>(); break;
-    case 3: e = tc::configure_n<3, false, BF>(); if (e == cudaSuccess) e = tc::configure_n<3, true, BF>(); break;
-    case 4: e = tc::configure_n<4, false, BF>(); if (e == cudaSuccess) e = tc::configure_n<4, true, BF>(); break;
-    case 5:
-      if constexpr (BF) {
-        e = tc::configure_n<5, false, true>();
-        if (e == cudaSuccess) e = tc::configure_n<5, true, true>();
-      }
-      break;
-    default: break;
+    case 1: return configure_tc_n<1, BF>();
+    case 2: return configure_tc_n<2, BF>();
+    case 3: return configure_tc_n<3, BF>();
+    case 4: return configure_tc_n<4, BF>();
+    case 5: return configure_tc_n<5, BF>();
+    default: return cudaErrorInvalidValue;
   }
-  return e;
 }
 
 cudaError_t configure_tc_kernels(int N, bool bf16) {
   return bf16 ? configure_tc_bf<true>(N) : configure_tc_bf<false>(N);
 }
 
+template <int N, bool BF>
+cudaError_t launch_tc_n(bool pml, const StageParams<float>& P, int nb, cudaStream_t s, int qc) {
+  if constexpr (BF || N <= 4) {
+    if (!pml) return tc::launch_n<N, false, BF, 0>(P, nb, s);
+    if (qc == 0) return tc::launch_n<N, true, BF, 0>(P, nb, s);
+  } else {
+    if (!pml) return tc::launch_n<N, false, BF, 1>(P, nb, s);
+    if (qc == 0) return cudaErrorInvalidValue;
+  }
+  return tc::launch_n<N, true, BF, 1>(P, nb, s);
+}
+
 template <bool BF>
-cudaError_t launch_tc_bf(int N, bool pml, const StageParams<float>& P, int nb, cudaStream_t s) {
+cudaError_t launch_tc_bf(int N, bool pml, const StageParams<float>& P, int nb, cudaStream_t s,
+                         int qc) {
   switch (N) {
-    case 1: return pml ? tc::launch_n<1, true, BF>(P, nb, s) : tc::launch_n<1, false, BF>(P, nb, s);
-    case 2: return pml ? tc::launch_n<2, true, BF>(P, nb, s) : tc::launch_n<2, false, BF>(P, nb, s);
-    case 3: return pml ? tc::launch_n<3, true, BF>(P, nb, s) : tc::launch_n<3, false, BF>(P, nb, s);
-    case 4: return pml ? tc::launch_n<4, true, BF>(P, nb, s) : tc::launch_n<4, false, BF>(P, nb, s);
-    case 5:
-      if constexpr (BF)
-        return pml ? tc::launch_n<5, true, true>(P, nb, s) : tc::launch_n<5, false, true>(P, nb, s);
-      return cudaErrorInvalidValue;
+    case 1: return launch_tc_n<1, BF>(pml, P, nb, s, qc);
+    case 2: return launch_tc_n<2, BF>(pml, P, nb, s, qc);
+    case 3: return launch_tc_n<3, BF>(pml, P, nb, s, qc);
+    case 4: return launch_tc_n<4, BF>(pml, P, nb, s, qc);
+    case 5: return launch_tc_n<5, BF>(pml, P, nb, s, qc);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_stage_tc(int N, bool pml, const StageParams<float>& P, int nb, cudaStream_t s,
-                            bool bf16) {
+                            bool bf16, int qc) {
   // the kernels stage element blocks as bulk copies of their 16-byte-aligned
   // cover, sized for blocks that start 0 or 8 bytes past a boundary: every
   // field buffer must start on a 16-byte boundary
@@ -1239,7 +1018,8 @@ cudaError_t launch_stage_tc(int N, bool pml, const StageParams<float>& P, int nb
                       (pml ? reinterpret_cast<uintptr_t>(P.p) | reinterpret_cast<uintptr_t>(P.resp)
                            : 0);
   if (a & 15) return cudaErrorMisalignedAddress;
-  return bf16 ? launch_tc_bf<true>(N, pml, P, nb, s) : launch_tc_bf<false>(N, pml, P, nb, s);
+  return bf16 ? launch_tc_bf<true>(N, pml, P, nb, s, qc)
+              : launch_tc_bf<false>(N, pml, P, nb, s, qc);
 }
 
 }  // namespace wadg

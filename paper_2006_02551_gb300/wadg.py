@@ -54,8 +54,12 @@ _SIG = {
     "wadg_set_pml_profile": [_P, C.POINTER(wadg_pml_profile), C.c_int],
     "wadg_set_sources": [_P, C.c_int32, C.POINTER(wadg_dipole)],
     "wadg_set_probes": [_P, C.c_int32, _D],
-    "wadg_set_state": [_P, _D, C.c_double],
-    "wadg_get_state": [_P, _D, _D],
+    "wadg_set_quadrature": [_P, C.c_int32, _D],
+    "wadg_set_state": [_P, _P, C.c_double, C.c_int],
+    "wadg_get_state": [_P, _P, _D, C.c_int],
+    "wadg_state_bytes": [_P, C.POINTER(C.c_size_t)],
+    "wadg_bind_state": [_P, _P, C.c_size_t],
+    "wadg_transfer_bytes": [_P, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)],
     "wadg_rk_stage": [_P, C.c_int, C.c_double, C.c_double],
     "wadg_run_steps": [_P, C.c_int64, C.c_double, _D],
     "wadg_run_steps_noalloc": [_P, C.c_int64, C.c_double, _D],
@@ -201,6 +205,15 @@ class Solver:
             arr[i].batch = d.batch
         self._c(self.lib.wadg_set_sources(self.ctx, len(dipoles), arr))
 
+    def set_quadrature(self, rstw=None):
+        """Volume quadrature of the PML terms: rows (r, s, t, w) on the
+        reference tetrahedron, or None for the default (N+1)^3-point rule."""
+        if rstw is None:
+            self._c(self.lib.wadg_set_quadrature(self.ctx, 0, None))
+            return
+        a = np.ascontiguousarray(np.asarray(rstw, np.float64).reshape(-1, 4))
+        self._c(self.lib.wadg_set_quadrature(self.ctx, a.shape[0], _ptr(a)))
+
     def set_probes(self, xyz):
         p = np.ascontiguousarray(np.asarray(xyz, np.float64).reshape(-1, 3))
         self.n_probe = p.shape[0]
@@ -213,16 +226,63 @@ class Solver:
                                         C.byref(Nq)))
         return dict(K=K.value, K_pml=K1.value, Np=Np.value, Nq=Nq.value)
 
-    def set_state(self, q=None, t=0.0):
-        a = None if q is None else np.ascontiguousarray(q, np.float64)
-        self._c(self.lib.wadg_set_state(self.ctx, _ptr(a), t))
-
-    def get_state(self):
+    def _state_shape(self):
         inf = self.info()
-        q = np.empty((self.n_batch, inf["K"], 12, inf["Np"]))
+        return (self.n_batch, inf["K"], 12, inf["Np"])
+
+    def _device_ptr(self, x):
+        """Address of a contiguous float64 device tensor of the state's shape
+        (any object with data_ptr(), is_cuda, dtype and shape, e.g. torch)."""
+        if tuple(x.shape) != self._state_shape() or str(x.dtype) != "torch.float64" \
+                or not x.is_cuda or not x.is_contiguous():
+            raise ValueError(f"device state must be a contiguous float64 CUDA tensor of shape "
+                             f"{self._state_shape()}")
+        return _P(x.data_ptr())
+
+    def set_state(self, q=None, t=0.0):
+        """q: host array (numpy) or a CUDA tensor (device exchange, no host
+        copy; ordered on the context's stream) of shape [nb][K][12][Np]."""
+        if q is not None and hasattr(q, "data_ptr") and getattr(q, "is_cuda", False):
+            self._c(self.lib.wadg_set_state(self.ctx, self._device_ptr(q), t, 1))
+            return
+        a = None if q is None else np.ascontiguousarray(q, np.float64)
+        self._c(self.lib.wadg_set_state(self.ctx, _P(a.ctypes.data) if a is not None else None,
+                                        t, 0))
+
+    def get_state(self, out=None):
+        """(q, t).  With out = a CUDA tensor of the state's shape the state is
+        written there on the device (no host copy) and out is returned."""
         t = C.c_double()
-        self._c(self.lib.wadg_get_state(self.ctx, _ptr(q), C.byref(t)))
+        if out is not None:
+            self._c(self.lib.wadg_get_state(self.ctx, self._device_ptr(out), C.byref(t), 1))
+            return out, t.value
+        q = np.empty(self._state_shape())
+        self._c(self.lib.wadg_get_state(self.ctx, _P(q.ctypes.data), C.byref(t), 0))
         return q, t.value
+
+    def state_bytes(self):
+        n = C.c_size_t()
+        self._c(self.lib.wadg_state_bytes(self.ctx, C.byref(n)))
+        return n.value
+
+    def bind_state(self, buf):
+        """Keep the state buffers in caller-owned device memory buf (a CUDA
+        tensor of at least state_bytes() bytes, 256-byte aligned), or
+        None to return them to the library.  The solver keeps a reference to
+        buf while it is bound."""
+        if buf is None:
+            self._c(self.lib.wadg_bind_state(self.ctx, None, 0))
+            self._bound = None
+            return
+        nbytes = buf.numel() * buf.element_size()
+        self._c(self.lib.wadg_bind_state(self.ctx, _P(buf.data_ptr()), nbytes))
+        self._bound = buf
+
+    def transfer_bytes(self):
+        """(host-to-device, device-to-host) bytes copied by this context."""
+        a, b = C.c_size_t(), C.c_size_t()
+        self._c(self.lib.wadg_transfer_bytes(self.ctx, C.byref(a), C.byref(b)))
+        return a.value, b.value
 
     def rk_stage(self, stage, t, dt):
         self._c(self.lib.wadg_rk_stage(self.ctx, stage, t, dt))

@@ -92,9 +92,14 @@ def test_tc_small_workload_full_run():
 
 def test_tc_rejects_kappa_and_high_order():
     from paper_2006_02551_gb300 import Solver, WadgError, wadg
+    from synthetic import cube_tet_mesh
+    # TF32 at N = 5 takes a PML only with a compact volume rule
+    t = Solver(5, "tf32")
+    t.set_mesh(*cube_tet_mesh(2, 0.1, 0))
     with pytest.raises(WadgError) as e:
-        Solver(5, "tf32")
+        t.set_pml(PML3)
     assert e.value.status == wadg.WADG_EUNSUPPORTED
+    t.close()
     s, sim, mask = make_pair(2, 2, 0.1, 0, None, "tf32")
     with pytest.raises(WadgError) as e:
         s.set_pml(PmlProfile(kappa_max=2.0))
