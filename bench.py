@@ -33,24 +33,22 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
-FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (no measured figure available)
 
 
-# DRAM traffic per PML element of the TF32 PML stage kernel, from one
-# ncu --set full capture of the small case of the benchmark recipe (summary
-# and command in profiles/tc_stage_kernels_cube24_n4_full.md), valid for the
-# kernel source it was taken on (sha256 of csrc/tc_kernels.cu)
-TC_PML_TRAFFIC = {"sha256": "5cfe46d2f115bc85c1d72ea3ba5e8be2e75c8fe060566677b5bc905d0eea0bae",
-                  "bytes_per_pml_element": {"tf32": 7487.0, "bf16": 7516.0}, "N": 4}
+# DRAM traffic per PML element of the tensor-core PML stage kernel, from
+# one ncu capture of the small case of the benchmark recipe, valid only for
+# the kernel source it was taken on (sha256 of that source file): None until
+# a capture of the current source is recorded here
+TC_PML_TRAFFIC = {"file": "tc_rows.cu", "sha256": None, "N": 4,
+                  "bytes_per_pml_element": {}}
 
 
 def tc_pml_traffic(K1, N, precision):
     """Per-launch DRAM bytes of the PML kernel, or None once the kernel changed."""
     import hashlib
-    src = os.path.join(ROOT, "paper_2006_02551_gb300", "csrc", "tc_kernels.cu")
+    if not TC_PML_TRAFFIC["sha256"]:
+        return None
+    src = os.path.join(ROOT, "paper_2006_02551_gb300", "csrc", TC_PML_TRAFFIC["file"])
     try:
         with open(src, "rb") as f:
             h = hashlib.sha256(f.read()).hexdigest()
@@ -69,12 +67,18 @@ def describe(w):
             f"{len(w.probes)} probes, {w.n_batch} excitation(s)")
 
 
-def algorithmic_costs(N, Np, Nfp, Nq, rs, kappa):
+def algorithmic_costs(N, Np, Nfp, Nq, rs, kappa, rows=False):
     """Per element per stage launch: (bytes, flops) of the non-PML and the PML
-    stage kernel (minimum traffic: each field read and written once)."""
-    meta = 9 * 8 + 3 * rs + 4 * 4 + 4          # metric (double), material, nbr, code
+    stage kernel (minimum traffic: each field read and written once).  Per
+    element: the fields (read q, res; write res, q; and P, its register in
+    PML elements), the metric (double; float in the row-owned tensor-core
+    kernel), normals and Fscale (4 x 4 Real), material (3 Real), neighbour
+    ids and face codes (4 x 4 + 4 bytes), and the coefficient samples (3 per
+    quadrature point; the row-owned kernel reads its capacity)."""
+    meta = 9 * 8 + 3 * rs + 4 * 4 + 4 + 16 * rs
+    meta_rows = 9 * 4 + 3 * rs + 4 * 4 + 4 + 16 * rs
     b_std = 4 * rs * 6 * Np + meta              # read q, res; write res, q
-    b_pml = 4 * rs * 12 * Np + meta + (6 if kappa else 3) * Nq * rs
+    b_pml = 4 * rs * 12 * Np + (meta_rows if rows else meta) + (6 if kappa else 3) * Nq * rs
     f_std = 36 * Np * Np + 90 * Np + 240 * Nfp + 48 * Np * Nfp + 4 * 6 * Np
     f_pml = f_std + 48 * Nq * Np + 24 * Nq + 12 * Np + 4 * 6 * Np
     if kappa:
@@ -130,11 +134,15 @@ class ClockSampler:
                 "samples": len(rows), "reasons": reasons}
 
 
-def setup_solver(w, precision, stream, device, scheme="waa"):
+def setup_solver(w, precision, stream, device, scheme="waa", rule="compact"):
+    """rule: "compact" (the fully symmetric degree-2N rule of synthetic/,
+    46 points at N = 4) or "default" (the library's (N+1)^3-point rule)."""
     from paper_2006_02551_gb300 import Solver
-    from synthetic import cube_tet_mesh
+    from synthetic import compact_rule, cube_tet_mesh
     v, e = cube_tet_mesh(w.n_hex, w.jitter, w.mesh_seed)
     s = Solver(w.N, precision, n_batch=w.n_batch, device=device, stream=stream)
+    if rule == "compact":
+        s.set_quadrature(compact_rule(w.N))
     s.set_mesh(v, e)
     s.set_pml(w.pml, scheme)
     s.set_sources(list(w.sources))
@@ -143,16 +151,17 @@ def setup_solver(w, precision, stream, device, scheme="waa"):
     return s
 
 
-def oracle_rate(w, n_hex, steps, warmup=1):
+def oracle_rate(w, n_hex, steps, warmup=1, rule="compact"):
     """The FP64 oracle (as it stands) on a smaller cube of the same recipe:
     DOF-updates/s over `steps` LSERK steps after `warmup` steps."""
     from dataclasses import replace
     from oracle.solver import Simulation
-    from synthetic import cube_tet_mesh
+    from synthetic import compact_rule, cube_tet_mesh
     ws = replace(w, n_hex=n_hex)
     v, e = cube_tet_mesh(ws.n_hex, ws.jitter, ws.mesh_seed)
     sim = Simulation(ws.N, v, e, profile=ws.pml, sources=ws.sources, probes=ws.probes,
-                     n_batch=ws.n_batch)
+                     n_batch=ws.n_batch,
+                     volume_rule=compact_rule(ws.N) if rule == "compact" else None)
     dt = sim.stable_dt(1.0)
     st = sim.zero_state()
     t = 0.0
@@ -179,7 +188,7 @@ def cpu_cores():
 
 
 def run_reference(args, w):
-    dofs, times, ws = oracle_rate(w, args.ref_hex, args.steps, warmup=args.warmup)
+    dofs, times, ws = oracle_rate(w, args.ref_hex, args.steps, warmup=args.warmup, rule=args.rule)
     tot = sum(times)
     value = dofs * len(times) / tot
     sample = (f"FP64 numpy oracle on {ws.n_hex}^3x6={ws.K} tets of the same recipe "
@@ -299,19 +308,23 @@ def batching_runs(sh, local, stream):
 
 
 def precision_form_run(sh, local, stream):
-    """The precision form: 64^3 x 6 = 1,572,864 tets, N = 5, the contractions on
-    the tensor cores with BF16 operands and FP32 accumulation and state, against
-    the FP32 CUDA-core path (itself within 1.3e-7 of FP64): DOF-updates/s of
-    each and the relative L2 difference of E, H after 20 steps."""
+    """The precision form: 64^3 x 6 = 1,572,864 tets, N = 5, compact volume
+    rule, the contractions on the tensor cores with TF32 or BF16 operands and
+    FP32 accumulation and state, against the FP32 CUDA-core path (itself
+    within 1.3e-7 of FP64): DOF-updates/s of each and the relative L2
+    difference of E, H after 20 steps."""
     import torch
     from paper_2006_02551_gb300 import Solver
     from synthetic import cube_tet_mesh, workload
+    from synthetic import compact_rule
     w = workload("cube64_n5")
     v, e = cube_tet_mesh(w.n_hex, w.jitter, w.mesh_seed)
-    out = {"workload": describe(w)}
+    out = {"workload": describe(w), "volume_rule": f"compact degree-10 rule, "
+                                                   f"{compact_rule(w.N).shape[0]} points"}
     states = {}
-    for prec, nrate in (("bf16", 20), ("fp32", 10)):
+    for prec, nrate in (("tf32", 20), ("bf16", 20), ("fp32", 10)):
         s = Solver(w.N, prec, device=local, stream=sh)
+        s.set_quadrature(compact_rule(w.N))
         s.set_mesh(v, e)
         s.set_pml(w.pml)
         s.set_sources(list(w.sources))
@@ -334,8 +347,9 @@ def precision_form_run(sh, local, stream):
         out[prec] = {"ms_per_step": ms, "value": dofs / (ms * 1e-3), "unit": "DOF-updates/s"}
         s.close()
     out["dofs_per_step"] = dofs
-    out["l2_rel_bf16_vs_fp32_20_steps"] = float(
-        np.linalg.norm(states["bf16"] - states["fp32"]) / np.linalg.norm(states["fp32"]))
+    for prec in ("tf32", "bf16"):
+        out[f"l2_rel_{prec}_vs_fp32_20_steps"] = float(
+            np.linalg.norm(states[prec] - states["fp32"]) / np.linalg.norm(states["fp32"]))
     return out
 
 
@@ -376,6 +390,95 @@ def gradient_run(sh, local, stream):
             "J": float(J[0]), "parameters": int(ge.shape[1]) + 6}
 
 
+def accuracy_runs(sh, local, rule):
+    """Relative L2 error of E, H (all elements) and of the probe records at
+    each workload's final time (its full step count), mixed precision against
+    the FP64 GPU path (parity-proven against the oracle to 1e-12), or against
+    the FP32 path where FP64 at full size takes hours (the N = 5 workload; the
+    FP32 path is within ~1e-7 of FP64 at N = 4).  States are compared on the
+    device (state exchange into CUDA tensors)."""
+    import torch
+    from paper_2006_02551_gb300 import Solver
+    from synthetic import Dipole, compact_rule, cube_tet_mesh, workload
+    from synthetic.workloads import eps_r
+
+    def run(w, prec, steps, sources=None, n_batch=None, eps=None):
+        v, e = cube_tet_mesh(w.n_hex, w.jitter, w.mesh_seed)
+        nb = n_batch or w.n_batch
+        s = Solver(w.N, prec, n_batch=nb, device=local, stream=sh)
+        if rule == "compact":
+            s.set_quadrature(compact_rule(w.N))
+        s.set_mesh(v, e)
+        if eps is not None:
+            s.set_materials(eps)
+        s.set_pml(w.pml)
+        s.set_sources(list(sources if sources is not None else w.sources))
+        s.set_probes(list(w.probes))
+        dt = s.stable_dt(1.0)
+        s.set_state(None, 0.0)
+        t0 = time.perf_counter()
+        rec = s.run_steps(steps, dt)
+        wall = time.perf_counter() - t0
+        q = torch.empty(s._state_shape(), dtype=torch.float64, device=f"cuda:{local}")
+        s.get_state(q)
+        s.synchronize()
+        J = s.objective()
+        s.close()
+        return q[:, :, 0:6].contiguous(), rec, J, wall
+
+    def rel(a, b):
+        if isinstance(a, np.ndarray):
+            return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+
+    out = {"rule": rule}
+    # N = 4 production workload: 1000 steps
+    w = workload("cube40_n4")
+    q64, r64, J64, t64 = run(w, "fp64", w.steps)
+    row = {"steps": w.steps, "reference": "fp64 (GPU)", "fp64_wall_s": t64}
+    for prec in ("fp32", "tf32", "bf16"):
+        q, r, J, _ = run(w, prec, w.steps)
+        row[prec] = {"state": rel(q, q64), "probes": rel(r, r64), "objective": abs(J[0] - J64[0]) / J64[0]}
+        del q
+    del q64
+    out["cube40_n4"] = row
+    torch.cuda.empty_cache()
+    # N = 5 precision workload: 500 steps against FP32
+    w = workload("cube64_n5")
+    q32, r32, J32, t32 = run(w, "fp32", w.steps)
+    row = {"steps": w.steps, "reference": "fp32 (GPU; FP64 at this size takes hours)",
+           "fp32_wall_s": t32}
+    for prec in ("tf32", "bf16"):
+        q, r, J, _ = run(w, prec, w.steps)
+        row[prec] = {"state": rel(q, q32), "probes": rel(r, r32), "objective": abs(J[0] - J32[0]) / J32[0]}
+        del q
+    del q32
+    out["cube64_n5"] = row
+    torch.cuda.empty_cache()
+    # batching workload: 800 steps of the 64-excitation FP32 batch; its first
+    # two excitations against an FP64 run of those two alone
+    w = workload("cube30_n3_batch64")
+    qb, rb, Jb, _ = run(w, "fp32", w.steps)
+    two = [Dipole(x=d.x, dir=d.dir, t0=d.t0, width=d.width, amplitude=d.amplitude, batch=d.batch)
+           for d in w.sources if d.batch < 2]
+    q2, r2, J2, t2 = run(w, "fp64", w.steps, sources=two, n_batch=2)
+    out["cube30_n3_batch64"] = {
+        "steps": w.steps, "reference": "fp64 (GPU) runs of excitations 0 and 1",
+        "fp32": {"state": rel(qb[:2], q2), "probes": rel(rb[..., :2], r2),
+                 "objective": float(np.max(np.abs(Jb[:2] - J2) / J2))}}
+    del qb, q2
+    torch.cuda.empty_cache()
+    # differentiation workload: 2000 steps, FP32 forward against FP64
+    w = workload("cube24_n3_grad")
+    er = eps_r(w)
+    q64, r64, J64, _ = run(w, "fp64", w.steps, eps=er)
+    q32, r32, J32, _ = run(w, "fp32", w.steps, eps=er)
+    out["cube24_n3_grad"] = {"steps": w.steps, "reference": "fp64 (GPU)",
+                             "fp32": {"state": rel(q32, q64), "probes": rel(r32, r64),
+                                      "objective": abs(J32[0] - J64[0]) / J64[0]}}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -384,6 +487,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cube40_n4")
     ap.add_argument("--precision", default="tf32", choices=["fp32", "fp64", "tf32", "bf16"])
+    ap.add_argument("--rule", default="compact", choices=["compact", "default"],
+                    help="volume quadrature of the PML terms: the compact degree-2N rule "
+                         "(46 points at N = 4) or the (N+1)^3-point conical rule")
     ap.add_argument("--hex", type=int, default=None,
                     help="override the cube size of the workload (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -400,6 +506,9 @@ def main():
                     help="cube size of the oracle sample for --impl reference")
     ap.add_argument("--cpu-hex", type=int, default=12,
                     help="cube size of the oracle sample for the cpu_baseline entry")
+    ap.add_argument("--accuracy", action="store_true",
+                    help="only the L2 errors at every workload's final time (about 15 "
+                         "minutes: the FP64 references), one JSON line")
     args = ap.parse_args()
     args.metric = "DOF-updates/s (WADG-PML DGTD, N=4), mixed-precision vs FP64 at stated L2 error"
     if args.warmup < 3:
@@ -435,8 +544,12 @@ def main():
         dist.barrier()
     stream = torch.cuda.Stream(device=local)
     sh = stream.cuda_stream
+    if args.accuracy:
+        if rank == 0:
+            print(json.dumps({"accuracy_at_t_end": accuracy_runs(sh, local, args.rule)}))
+        return
 
-    s = setup_solver(w, args.precision, sh, local)
+    s = setup_solver(w, args.precision, sh, local, rule=args.rule)
     info = s.info()
     K, K1, Np, Nq = info["K"], info["K_pml"], info["Np"], info["Nq"]
     N = w.N
@@ -469,7 +582,12 @@ def main():
 
     # per-kernel durations (CUDA events on the library stream, eager launches)
     kms = s.profile_stage(50, dt)
-    cost = algorithmic_costs(N, Np, Nfp, Nq, rs, w.pml.kappa_max != 1.0)
+    rows = args.precision in ("tf32", "bf16") and args.rule == "compact"
+    mem0 = s.memory_report()
+    # coefficient samples per element as stored (the kernels read the stored
+    # stride, which includes a compact rule's padding to its capacity)
+    nq_read = mem0["pml_coeff"] / max(1, K1 * 3 * rs) if K1 else Nq
+    cost = algorithmic_costs(N, Np, Nfp, nq_read, rs, w.pml.kappa_max != 1.0, rows=rows)
     per = {"std": (kms[0], cost["bytes_std"] * (K - K1) * w.n_batch,
                    cost["flops_std"] * (K - K1) * w.n_batch),
            "pml": (kms[1], cost["bytes_pml"] * K1 * w.n_batch,
@@ -485,19 +603,19 @@ def main():
     if args.precision in ("tf32", "bf16"):
         # tensor-core contractions: the stage is bound by HBM traffic
         traffic = tc_pml_traffic(K1 * w.n_batch, N, args.precision) if dom == "pml" else None
+        kname = "tc_rows_kernel" if (rows and dom == "pml") else "tc_stage_kernel"
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
                     "frac": achieved_gbs / hbm, "traffic": traffic,
-                    "traffic_source": "profiles/tc_stage_kernels_cube24_n4_full.md (scaled by elements)",
-                    "kernel": f"tc_stage_kernel<{dom}>",
+                    "traffic_note": "ncu DRAM bytes per PML element of the small case, scaled "
+                                    "by elements (null when the kernel source has changed since)",
+                    "kernel": f"{kname}<{dom}>",
                     "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                     "alu": {"achieved_tflops": achieved}}
     else:
-        if args.precision == "fp64":
-            peak = FP64_PEAK_TFLOPS
-            peak_note = "nominal GB300 FP64 (1.25 TFLOP/s)"
-        else:
-            peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-            peak_note = "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
+        from paper_2006_02551_gb300.wadg import fma_peak
+        peak = fma_peak(local, fp64=args.precision == "fp64")
+        peak_note = (f"measured {'FP64' if args.precision == 'fp64' else 'FP32'} FMA "
+                     f"throughput (wadg_fma_peak: register FMA chains on every SM)")
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": None, "kernel": f"stage_kernel<{dom}>",
                     "peak_source": peak_note,
@@ -534,7 +652,7 @@ def main():
         for prec in ("fp64", "fp32", "bf16"):
             if prec == args.precision or (prec == "bf16" and N > 4):
                 continue
-            so = setup_solver(w, prec, sh, local)
+            so = setup_solver(w, prec, sh, local, rule=args.rule)
             nrate = 20 if prec == "fp64" else 200
             so.run_steps(3, dt, record=False)
             so.set_state(None, 0.0)
@@ -563,6 +681,20 @@ def main():
             out_extra["accuracy"] = acc
         for prec, (rate, _) in others.items():
             out_extra[prec] = rate
+        # the CUDA-core paths against the measured FMA throughput (the
+        # algorithmic flops of a step: 5 stages of both classes)
+        from paper_2006_02551_gb300.wadg import fma_peak
+        peaks_fma = {"fp32": fma_peak(local, fp64=False), "fp64": fma_peak(local, fp64=True)}
+        out_extra["cuda_core_peaks_tflops"] = peaks_fma
+        for prec in ("fp32", "fp64"):
+            if prec in out_extra:
+                c2 = algorithmic_costs(N, Np, Nfp, Nq, 8 if prec == "fp64" else 4,
+                                       w.pml.kappa_max != 1.0)
+                fl = 5 * (c2["flops_std"] * (K - K1) + c2["flops_pml"] * K1) * w.n_batch
+                ach = fl / (out_extra[prec]["ms_per_step"] * 1e-3) / 1e12
+                out_extra[prec]["alu"] = {"achieved_tflops": ach, "peak_tflops": peaks_fma[prec],
+                                          "frac": ach / peaks_fma[prec],
+                                          "peak_source": "measured FMA throughput"}
     else:
         s.close()
 
@@ -597,7 +729,12 @@ def main():
             "pml_kernel_hbm": {"bytes_per_launch": sb, "achieved_gbs": sb / (kss[1] * 1e-3) / 1e9,
                                "peak_gbs": hbm, "frac": sb / (kss[1] * 1e-3) / 1e9 / hbm},
             "vs_waa": {"memory_ratio": mems["pml_coeff"] / max(mem["pml_coeff"], 1),
-                       "time_ratio_vs_this_run": mss / (ms / args.steps)}}
+                       "time_ratio_vs_this_run": mss / (ms / args.steps),
+                       "this_run_precision": args.precision,
+                       # the same arithmetic on both sides: FP32 CUDA-core
+                       # kernels, stored matrices against weight-adjusted
+                       "time_ratio_fp32_vs_fp32": (mss / out_extra["fp32"]["ms_per_step"]
+                                                   if "fp32" in out_extra else None)}}
 
     if not args.no_batching and rank == 0:
         out_extra["batching"] = batching_runs(sh, local, stream)
@@ -608,7 +745,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cdofs, ctimes, ws = oracle_rate(w, args.cpu_hex, 2, warmup=1)
+        cdofs, ctimes, ws = oracle_rate(w, args.cpu_hex, 2, warmup=1, rule=args.rule)
         cpu = {"value": cdofs * len(ctimes) / sum(ctimes), "unit": "DOF-updates/s",
                "cores": cpu_cores(), "kind": "oracle",
                "sample": (f"FP64 numpy oracle on {ws.n_hex}^3x6={ws.K} tets of the same "
@@ -625,7 +762,10 @@ def main():
                           "bf16": "bf16 x bf16 -> f32"}[args.precision],
                 "data": "synthetic",
                 "config": {"workload": describe(w), "K": K, "K_pml": K1, "N": N, "Np": Np,
-                           "Nq": Nq, "dofs_per_step": dofs, "precision": args.precision,
+                           "Nq": Nq, "volume_rule": (f"compact fully symmetric degree-{2 * N} "
+                                                     f"rule, {Nq} points" if args.rule == "compact"
+                                                     else f"conical product, {Nq} points"),
+                           "dofs_per_step": dofs, "precision": args.precision,
                            "l2_flush": f"inputs larger than L2 (state {mem['state'] / 1e9:.2f} GB)",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,

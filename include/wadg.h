@@ -354,6 +354,13 @@ wadg_status wadg_set_memory_limit(wadg_ctx* ctx, size_t bytes, size_t* held_out)
  * path.) */
 wadg_status wadg_arm_wait_timeout(wadg_ctx* ctx);
 
+/* Measured fused multiply-add throughput of device `device`'s CUDA cores in
+ * TFLOP/s (2 flops per FMA): FP64 (fp64 != 0) or FP32, from independent
+ * register FMA chains in every thread of 4 blocks per SM, timed with CUDA
+ * events.  The roofline denominator of the FP64 and FP32 CUDA-core stage
+ * kernels.  (The paper has no counterpart; this is a measurement aid.) */
+wadg_status wadg_fma_peak(int device, int fp64, double* tflops);
+
 /* Reference-element operator of order N (host only, no device needed), for
  * checking the library's set-up against an independent construction.
  * which: 0 Dr, 1 Ds, 2 Dt ([Np][Np]), 3 LIFT ([Np][4 Nfp]), 4 V_q ([Nq][Np]),

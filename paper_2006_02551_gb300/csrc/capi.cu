@@ -97,7 +97,7 @@ struct wadg_ctx {
   int64_t K0 = 0, K1 = 0;
 
   // device
-  DevPtr q[2], rq, p, rp, geo, fnrm, mat, nbr, code, sig, kap, ops, tabs, verts;
+  DevPtr q[2], rq, p, rp, geo, geof, fnrm, mat, nbr, code, sig, kap, ops, tabs, verts;
   DevPtr src, srcw, pr_elem, pr_ell, pr_out, obj, tdev, stepdev, flag, tcops, errflag;
   DevPtr stored;     // stored-matrix scheme: per PML element operators
   DevPtr dperm;      // internal -> caller element id (int32), device state exchange
@@ -474,6 +474,11 @@ wadg_status rebuild_typed(wadg_ctx* ctx) {
   }
   CK(dalloc(ctx->geo, geo.size() * 8));
   CK(cudaMemcpy(ctx->geo.p, geo.data(), geo.size() * 8, cudaMemcpyHostToDevice));
+  if (ctx->tc) {   // the metric in float for the row-owned tensor-core kernels
+    std::vector<float> gf(geo.begin(), geo.end());
+    CK(dalloc(ctx->geof, gf.size() * 4));
+    CK(cudaMemcpy(ctx->geof.p, gf.data(), gf.size() * 4, cudaMemcpyHostToDevice));
+  }
   CK(dalloc(ctx->fnrm, fn.size() * sizeof(Real)));
   CK(cudaMemcpy(ctx->fnrm.p, fn.data(), fn.size() * sizeof(Real), cudaMemcpyHostToDevice));
   CK(dalloc(ctx->verts, verts.size() * 8));
@@ -648,6 +653,7 @@ StageParams<Real> stage_params(wadg_ctx* ctx, int stage, double dt, double t, bo
   P.p = (Real*)ctx->p.p;
   P.resp = (Real*)ctx->rp.p;
   P.geo = (const double*)ctx->geo.p;
+  P.geof = (const float*)ctx->geof.p;
   P.fnrm = (const Real*)ctx->fnrm.p;
   P.mat = (const Real*)ctx->mat.p;
   P.nbr = (const int*)ctx->nbr.p;
@@ -968,7 +974,7 @@ wadg_status wadg_destroy(wadg_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   invalidate_graphs(ctx);
-  for (DevPtr* d : {&ctx->q[0], &ctx->q[1], &ctx->rq, &ctx->p, &ctx->rp, &ctx->geo, &ctx->fnrm, &ctx->mat,
+  for (DevPtr* d : {&ctx->q[0], &ctx->q[1], &ctx->rq, &ctx->p, &ctx->rp, &ctx->geo, &ctx->geof, &ctx->fnrm, &ctx->mat,
                     &ctx->nbr, &ctx->code, &ctx->sig, &ctx->kap, &ctx->ops, &ctx->tabs,
                     &ctx->verts, &ctx->src, &ctx->srcw, &ctx->pr_elem, &ctx->pr_ell,
                     &ctx->pr_out, &ctx->obj, &ctx->tdev, &ctx->stepdev, &ctx->flag,
@@ -1669,7 +1675,8 @@ wadg_status wadg_memory_report(const wadg_ctx* ctx, size_t* bytes_state, size_t*
                                                        : ctx->sig.bytes + ctx->kap.bytes;
   if (bytes_operators) *bytes_operators = ctx->ops.bytes + ctx->tabs.bytes;
   if (bytes_geometry)
-    *bytes_geometry = ctx->geo.bytes + ctx->fnrm.bytes + ctx->mat.bytes + ctx->nbr.bytes + ctx->code.bytes;
+    *bytes_geometry = ctx->geo.bytes + ctx->geof.bytes + ctx->fnrm.bytes + ctx->mat.bytes +
+                      ctx->nbr.bytes + ctx->code.bytes;
   return WADG_OK;
 }
 

@@ -7,6 +7,7 @@
 //   P^E,P^H  p[b][e'][6][Np]       PML elements only (e' = e - K0), updated in place
 //   res      rp[b][e'][6][Np]
 //   geometry geo[e][9]             double: r_x r_y r_z s_x s_y s_z t_x t_y t_z
+//            geof[e][9]            the same in float (tensor-core contexts)
 //            fnrm[e][4][4]         unit outward normal and Fscale = sJ/J per face
 //                                  (computed in double on the host)
 //   material mat[e][3]             1/eps, 1/mu, Z = sqrt(mu/eps)
@@ -65,6 +66,7 @@ struct StageParams {
   Real* p;
   Real* resp;
   const double* geo;
+  const float* geof;        // [e][9]: the metric in float (tensor-core contexts)
   const Real* fnrm;         // [e][4][4]: unit outward normal, Fscale (from FP64)
   const Real* mat;
   const int* nbr;

@@ -97,6 +97,30 @@ __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
   return false;
 }
 
+// try_wait that may suspend the thread in hardware for up to hint_ns
+// nanoseconds while the phase is incomplete (instead of returning at once)
+__device__ __forceinline__ bool mbar_try_wait_hint(uint32_t a, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+// mbar_wait with the waiting thread suspended between polls: gives up after
+// about a second of global time (or 2^20 polls)
+__device__ __forceinline__ bool mbar_wait_sleep(uint32_t a, uint32_t parity) {
+  if (mbar_try_wait(a, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (int i = 0; i < (1 << 20); ++i) {
+    if (mbar_try_wait_hint(a, parity, 20000u)) return true;
+    if (global_ns() - t0 > kWaitLimitNs) break;
+  }
+  return false;
+}
+
 __device__ __forceinline__ void tmem_alloc(uint32_t dst, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst),
                "r"(ncols)
@@ -242,6 +266,12 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(r);
 }
 
+// TF32 round to nearest (ties away from zero) by integer operations on the
+// FP32 bit pattern: add half of the dropped part, clear the 13 low bits
+__device__ __forceinline__ float to_tf32_int(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
 // byte offset of (row r, k) in a K-major canonical tile: 8-row x 16-byte core
 // matrices, K-adjacent core matrices lbo bytes apart, 8-row groups sbo apart.
 // The field operands use lbo = 144 (one 16-byte gap per core matrix) so that
@@ -357,6 +387,58 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes
 // named barrier id among nthreads threads (warp-aligned)
 __device__ __forceinline__ void nbar_sync(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+}  // namespace tc
+}  // namespace wadg
+
+namespace wadg {
+namespace tc {
+
+// tensor-memory loads without the wait: several are issued back to back and
+// one tmem_wait_ld() makes all their registers valid
+__device__ __forceinline__ void tld16_nw(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tld8_nw(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tld4_nw(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+// n consecutive columns (n a multiple of 4, at most 32) into r, no wait
+template <int n>
+__device__ __forceinline__ void tld_cols_nw(uint32_t taddr, uint32_t* r) {
+  static_assert(n % 4 == 0 && n <= 32, "column count");
+  constexpr int a16 = n >= 16 ? 1 : 0;
+  constexpr int r1 = n - 16 * a16;
+  if constexpr (a16) tld16_nw(taddr, r);
+  constexpr int a16b = r1 >= 16 ? 1 : 0;
+  if constexpr (a16b) tld16_nw(taddr + 16, r + 16);
+  constexpr int r2 = r1 - 16 * a16b;
+  constexpr int o2 = n - r2;
+  if constexpr (r2 >= 8) tld8_nw(taddr + o2, r + o2);
+  constexpr int r3 = r2 >= 8 ? r2 - 8 : r2;
+  constexpr int o3 = n - r3;
+  if constexpr (r3 >= 4) tld4_nw(taddr + o3, r + o3);
 }
 
 }  // namespace tc

@@ -74,6 +74,7 @@ _SIG = {
     "wadg_arm_wait_timeout": [_P],
     "wadg_set_memory_limit": [_P, C.c_size_t, _P],
     "wadg_reference_operator": [C.c_int, C.c_int, _D, C.c_int64, _I64],
+    "wadg_fma_peak": [C.c_int, C.c_int, _D],
     "wadg_group_create": [C.c_int32, C.POINTER(_P), C.POINTER(_P)],
     "wadg_group_destroy": [_P],
     "wadg_group_autotune": [_P, _D, C.c_int32, _D],
@@ -127,6 +128,14 @@ def reference_operator(N: int, which: int) -> np.ndarray:
     out = np.empty(n.value)
     _check(lib.wadg_reference_operator(N, which, _ptr(out), n.value, C.byref(n)))
     return out
+
+
+def fma_peak(device=0, fp64=False) -> float:
+    """Measured CUDA-core FMA throughput (TFLOP/s) of a device."""
+    lib = load()
+    t = C.c_double()
+    _check(lib.wadg_fma_peak(device, 1 if fp64 else 0, C.byref(t)))
+    return t.value
 
 
 def make_profile(u0, L, sigma_max, p_sigma, kappa_max=1.0, eps0=1.0):

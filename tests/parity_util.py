@@ -82,18 +82,22 @@ def round_states(states, precision):
 
 
 def make_pair(N, n_hex, jitter, seed, prof, precision="fp64", sources=(), probes=(),
-              eps=None, mu=None, n_batch=1, scheme="waa", mesh=None):
+              eps=None, mu=None, n_batch=1, scheme="waa", mesh=None, volume_rule=None):
     """scheme: "waa", "stored" (eqs. 10-13) or "ec" (the weight-adjusted
     scheme with the profile evaluated at each element's centroid).  mesh:
-    (vertices, elements) to use instead of the jittered cube."""
+    (vertices, elements) to use instead of the jittered cube.  volume_rule:
+    (nq, 4) points and weights given to both sides instead of the default."""
     from paper_2006_02551_gb300 import Solver
     v, e = cube_tet_mesh(n_hex, jitter, seed) if mesh is None else mesh
     sim = Simulation(N, v, e, profile=prof, eps=eps, mu=mu, sources=sources,
                      probes=probes, n_batch=n_batch,
-                     scheme="stored" if scheme == "stored" else "waa")
+                     scheme="stored" if scheme == "stored" else "waa",
+                     volume_rule=volume_rule)
     if scheme == "ec" and prof is not None:
         sim.disc.set_profile(prof, element_constant_at=sim.geom.verts.mean(axis=1).T)
     s = Solver(N, precision, n_batch=n_batch)
+    if volume_rule is not None:
+        s.set_quadrature(volume_rule)
     s.set_mesh(v, e)
     if eps is not None or mu is not None:
         s.set_materials(eps, mu)

@@ -35,11 +35,18 @@ def _status_of(call):
     return 0
 
 
+@pytest.mark.parametrize("rule", ["default", "compact"])
 @pytest.mark.parametrize("precision", ["tf32", "bf16"])
 @pytest.mark.parametrize("prof", [PML3, None], ids=["pml", "nopml"])
-def test_withheld_signal_reports_timeout_and_context_recovers(precision, prof):
+def test_withheld_signal_reports_timeout_and_context_recovers(precision, prof, rule):
+    """Both tensor-core PML kernels (the (N+1)^3-rule kernel and the
+    row-owned kernel of compact rules) and the non-PML kernel."""
     from paper_2006_02551_gb300.wadg import WADG_ETIMEOUT
-    s, sim, mask = make_pair(3, 4, 0.15, 5, prof, precision)
+    from synthetic import compact_rule
+    if rule == "compact" and prof is None:
+        pytest.skip("the rule only concerns the PML class")
+    s, sim, mask = make_pair(3, 4, 0.15, 5, prof, precision,
+                             volume_rule=compact_rule(3) if rule == "compact" else None)
     q0 = to_lib(random_states(sim.K, sim.Np, 1, 17, mask))
     dt = s.stable_dt(0.5)
 

@@ -25,10 +25,13 @@ def built():
     build.build()
 
 
-def make(w, precision="fp64", scheme="waa"):
+def make(w, precision="fp64", scheme="waa", rule="default"):
     from paper_2006_02551_gb300 import Solver
+    from synthetic import compact_rule
     v, e = cube_tet_mesh(w.n_hex, w.jitter, w.mesh_seed)
     s = Solver(w.N, precision)
+    if rule == "compact":
+        s.set_quadrature(compact_rule(w.N))
     s.set_mesh(v, e)
     s.set_pml(w.pml, scheme)
     s.set_sources(list(w.sources))
@@ -41,13 +44,13 @@ def close_to(a, b, tol):
     return np.abs(a - b).max() <= tol * max(np.abs(a).max(), 1e-300)
 
 
-@pytest.mark.parametrize("precision,scheme", [("fp64", "waa"), ("fp32", "waa"),
-                                              ("fp32", "stored"), ("fp32", "ec"),
-                                              ("tf32", "waa"), ("bf16", "waa"),
-                                              ("tf32", "stored")])
-def test_noalloc_steps_match_run_steps_twice(precision, scheme):
+@pytest.mark.parametrize("precision,scheme,rule", [
+    ("fp64", "waa", "default"), ("fp32", "waa", "default"), ("fp32", "stored", "default"),
+    ("fp32", "ec", "default"), ("tf32", "waa", "default"), ("bf16", "waa", "default"),
+    ("tf32", "stored", "default"), ("tf32", "waa", "compact"), ("bf16", "waa", "compact")])
+def test_noalloc_steps_match_run_steps_twice(precision, scheme, rule):
     w = workload("cube4_n3")
-    a, b = make(w, precision, scheme), make(w, precision, scheme)
+    a, b = make(w, precision, scheme, rule), make(w, precision, scheme, rule)
     dt = a.stable_dt(1.0)
     tol = TOL[precision]
     for n in (23, 17):   # two calls in a row on each path
