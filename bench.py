@@ -230,7 +230,8 @@ def mesh_dofs(s):
 
 def group_vs_sequential(meshes, pml, sh, local, stream, nst):
     """The meshes [(n_hex, N)] advanced one after the other (run_steps each)
-    and together (one grouped launch per stage, autotuned): DOF-updates/s."""
+    and together (per stage one grouped launch per (order, element class)
+    variant, on parallel graph branches; autotuned): DOF-updates/s."""
     import torch
     from paper_2006_02551_gb300 import Group, Solver
     from synthetic import cube_tet_mesh
@@ -244,6 +245,7 @@ def group_vs_sequential(meshes, pml, sh, local, stream, nst):
         ss.append(s)
     dts = [s.stable_dt(1.0) for s in ss]
     dofs = sum(mesh_dofs(s) for s in ss)
+    k_pml = [s.info()["K_pml"] for s in ss]
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     for s, dt in zip(ss, dts):
         s.run_steps(2, dt, record=False)
@@ -264,13 +266,16 @@ def group_vs_sequential(meshes, pml, sh, local, stream, nst):
     ev[3].synchronize()
     grp = ev[2].elapsed_time(ev[3]) / nst
     info = g.info()
+    variants = info["variants"]
     g.close()
     for s in ss:
         s.close()
     return {"meshes": len(meshes), "dofs_per_step": dofs,
-            "sequential": {"ms_per_step": seq, "value": dofs / (seq * 1e-3)},
+            "sequential": {"ms_per_step": seq, "value": dofs / (seq * 1e-3),
+                           "launches_per_step": 5 * sum(1 + (s_k > 0) for s_k in k_pml)},
             "grouped": {"ms_per_step": grp, "value": dofs / (grp * 1e-3),
-                        "launches_per_step": 5, "autotuned": info}}
+                        "launches_per_step": 5 * variants, "variants": variants,
+                        "autotuned": info}}
 
 
 def batching_runs(sh, local, stream):
@@ -353,18 +358,21 @@ def precision_form_run(sh, local, stream):
     return out
 
 
-def gradient_run(sh, local, stream):
+def gradient_run(sh, local, stream, rule, steps=None, ckpt=45):
     """The differentiation form: J = sum over 8 probes and 2000 steps of |E|^2 on
     the 82,944-tet N=3 mesh with eps_r ~ U[1,4]; gradient with respect to every
     eps_r and the PML (sigma_max, p_sigma) by the FP32 discrete adjoint with a
-    checkpoint every 45 steps, against the forward run alone."""
+    checkpoint every 45 steps, against the forward run alone (both on the
+    same volume rule)."""
     import torch
     from paper_2006_02551_gb300 import Solver
-    from synthetic import cube_tet_mesh, workload
+    from synthetic import compact_rule, cube_tet_mesh, workload
     from synthetic.workloads import eps_r
     w = workload("cube24_n3_grad")
     v, e = cube_tet_mesh(w.n_hex, w.jitter, w.mesh_seed)
     s = Solver(w.N, "fp32", device=local, stream=sh)
+    if rule == "compact":
+        s.set_quadrature(compact_rule(w.N))
     s.set_mesh(v, e)
     s.set_materials(eps_r(w))
     s.set_pml(w.pml)
@@ -374,20 +382,50 @@ def gradient_run(sh, local, stream):
     s.set_state(None, 0.0)
     s.run_steps(5, dt)
     torch.cuda.synchronize()
+    nst = steps or w.steps
     s.set_state(None, 0.0)
     t0 = time.perf_counter()
-    s.run_steps(w.steps, dt)
+    s.run_steps(nst, dt)
     torch.cuda.synchronize()
     t_fwd = time.perf_counter() - t0
     s.set_state(None, 0.0)
     t0 = time.perf_counter()
-    J, ge, gs, gp = s.adjoint(w.steps, dt, ckpt_every=45)
+    J, ge, gs, gp = s.adjoint(nst, dt, ckpt_every=ckpt)
     t_adj = time.perf_counter() - t0
     s.close()
-    return {"workload": describe(w) + ", eps_r ~ U[1,4] (seed 5)", "steps": w.steps,
-            "ckpt_every": 45, "precision": "fp32", "forward_s": t_fwd,
+    return {"workload": describe(w) + ", eps_r ~ U[1,4] (seed 5)", "steps": nst,
+            "volume_rule": rule, "ckpt_every": ckpt, "precision": "fp32", "forward_s": t_fwd,
             "gradient_s": t_adj, "gradient_over_forward": t_adj / t_fwd,
             "J": float(J[0]), "parameters": int(ge.shape[1]) + 6}
+
+
+def t_end_accuracy(w, precision, sh, local, rule):
+    """E, H at the workload's final time (its full step count) and the probe
+    records of the whole run, mixed precision against the FP32 path (which
+    `bench.py --accuracy` finds within 1e-6 of the FP64 path there); the
+    states are compared on the device."""
+    import torch
+    out = {"steps": w.steps, "reference": "fp32 path on the GPU (within 1e-6 of fp64 at t_end)"}
+    res = {}
+    for prec in (precision, "fp32"):
+        s = setup_solver(w, prec, sh, local, rule=rule)
+        dt = s.stable_dt(1.0)
+        s.set_state(None, 0.0)
+        rec = s.run_steps(w.steps, dt)
+        q = torch.empty(s._state_shape(), dtype=torch.float64, device=f"cuda:{local}")
+        s.get_state(q)
+        s.synchronize()
+        res[prec] = (q[:, :, 0:6].contiguous(), rec, s.objective()[0])
+        s.close()
+        del q
+    (qa, ra, Ja), (qb, rb, Jb) = res[precision], res["fp32"]
+    out[f"l2_rel_{precision}_vs_fp32"] = {
+        "state": float(torch.linalg.vector_norm(qa - qb) / torch.linalg.vector_norm(qb)),
+        "probes": float(np.linalg.norm(ra - rb) / np.linalg.norm(rb)),
+        "objective": float(abs(Ja - Jb) / abs(Jb))}
+    del res, qa, qb
+    torch.cuda.empty_cache()
+    return out
 
 
 def accuracy_runs(sh, local, rule):
@@ -506,6 +544,13 @@ def main():
                     help="cube size of the oracle sample for --impl reference")
     ap.add_argument("--cpu-hex", type=int, default=12,
                     help="cube size of the oracle sample for the cpu_baseline entry")
+    ap.add_argument("--grad-steps", type=int, default=None,
+                    help="steps of the gradient block (default: the workload's 2000; fewer "
+                         "for a profiling capture)")
+    ap.add_argument("--grad-ckpt", type=int, default=45,
+                    help="checkpoint spacing of the gradient block")
+    ap.add_argument("--no-t-end", action="store_true",
+                    help="skip the final-time accuracy block (workload's full step count)")
     ap.add_argument("--accuracy", action="store_true",
                     help="only the L2 errors at every workload's final time (about 15 "
                          "minutes: the FP64 references), one JSON line")
@@ -681,6 +726,8 @@ def main():
             out_extra["accuracy"] = acc
         for prec, (rate, _) in others.items():
             out_extra[prec] = rate
+        if args.precision in ("tf32", "bf16") and not args.no_t_end:
+            out_extra["accuracy_t_end"] = t_end_accuracy(w, args.precision, sh, local, args.rule)
         # the CUDA-core paths against the measured FMA throughput (the
         # algorithmic flops of a step: 5 stages of both classes)
         from paper_2006_02551_gb300.wadg import fma_peak
@@ -739,7 +786,7 @@ def main():
     if not args.no_batching and rank == 0:
         out_extra["batching"] = batching_runs(sh, local, stream)
     if not args.no_gradient and rank == 0:
-        out_extra["gradient"] = gradient_run(sh, local, stream)
+        out_extra["gradient"] = gradient_run(sh, local, stream, args.rule, args.grad_steps, args.grad_ckpt)
     if not args.no_precision_form and rank == 0:
         out_extra["precision_form"] = precision_form_run(sh, local, stream)
 

@@ -265,14 +265,15 @@ wadg_status wadg_profile_stage(wadg_ctx* ctx, int reps, double dt, double* ms_ou
  * a = 1), by the discrete adjoint of the Runge-Kutta recursion and of the
  * semi-discrete operator (upwind flux, eqs. 26-29).  Starts from the current
  * state and time; the forward pass stores a checkpoint every ckpt_every
- * steps and the reverse pass recomputes each segment from its checkpoint.
- * On return the state is the forward state after nsteps steps (as after
+ * steps and the reverse pass recomputes each segment from its checkpoint,
+ * keeping the input of every stage of the segment, then runs the segment's
+ * reverse stages on them.  On return the state is the forward state after nsteps steps (as after
  * wadg_run_steps).  Outputs (any may be NULL): J_out[n_batch],
  * dJ_deps[n_batch][K] (caller element order), dJ_dsigma_max[n_batch][3],
  * dJ_dp_sigma[n_batch][3].  EUNSUPPORTED for the TF32 and BF16 precisions,
  * kappa_max != 1 or a PML scheme other than WADG_PML_WAA; ESTATE without
  * probes.  Device memory: about
- * (nsteps/ckpt_every + ckpt_every + 12) copies of the state. */
+ * (nsteps/ckpt_every + 5 min(ckpt_every, nsteps) + 6) copies of the state. */
 wadg_status wadg_adjoint(wadg_ctx* ctx, int64_t nsteps, double dt, int32_t ckpt_every,
                          double* J_out, double* dJ_deps, double* dJ_dsigma_max,
                          double* dJ_dp_sigma);
@@ -376,12 +377,15 @@ const char* wadg_last_error(const wadg_ctx* ctx);
 
 /* ---------------------------------------------------------------- groups
  * Several contexts advanced together (the batching form: meshes of uneven
- * size and order in one launch per Runge-Kutta stage).  Every stage of every
- * member and element class is one launch of a grouped CUDA-core kernel: its
- * blocks start on the (member, class) items in proportion to their
+ * size and order).  A Runge-Kutta stage of every member and element class is
+ * one launch per variant (order N, element class) present in the group, of a
+ * grouped CUDA-core kernel compiled for that variant alone.  A variant's
+ * blocks start on its (member, class) items in proportion to their
  * algorithmic flops and then take tiles from per-item counters until none
- * are left, so the load balances itself; one step (the 5 stage launches and
- * each member's probe and clock kernels) is captured in a CUDA graph.  Each
+ * are left, so the load balances itself; the variants' launches of a stage
+ * run on parallel branches, so the SMs one variant's blocks leave as its
+ * tiles run out go to the others.  One step (the stage launches and each
+ * member's probe and clock kernels) is captured in a CUDA graph.  Each
  * member advances exactly as wadg_run_steps advances it (the stage of
  * eqs. 10, 11 and 26-29 with the time marching of Section II.B); the grouping
  * itself has no counterpart in the paper.  Members: FP32 contexts (WADG_FP32)
@@ -398,18 +402,26 @@ wadg_status wadg_group_create(int32_t n, wadg_ctx* const* ctxs, wadg_group** out
 wadg_status wadg_group_destroy(wadg_group* g);
 
 /* Tile sizes and grid: times `reps` grouped stage launches for every
- * candidate (256 or 512 threads per block; elements per tile = the largest
- * that fits / {1, 2, 4}; 1..4 blocks per SM within the occupancy limit) with
+ * candidate (elements per tile = the largest that fits / {1, 2, 4}; 1..4
+ * blocks per SM within each variant's occupancy limit; a stage's variant
+ * launches on parallel branches or one after the other; each variant's grid
+ * the whole GPU or its share by algorithmic flops; each variant keeps the
+ * block shape of its single-context kernel) with
  * the members' step sizes
  * dt[n], keeps the fastest and writes its time per stage launch (ms) to
  * ms_out (may be NULL).  The stages run on the members' current state, which
  * is left undefined: call it before wadg_set_state. */
 wadg_status wadg_group_autotune(wadg_group* g, const double* dt, int32_t reps, double* ms_out);
 
-/* The current launch shape: total blocks, threads per block, blocks per SM,
- * tile divisor, work items (any pointer may be NULL). */
+/* The current launch shape: total blocks (all variants), threads per block
+ * of the heaviest variant, blocks per SM (each variant is capped by its own
+ * occupancy), tile divisor, work items, variants (launches per stage),
+ * whether a stage's variant launches run on parallel branches (1) or in turn
+ * (0), and whether each variant's grid is its share of the GPU (1) or the
+ * whole GPU (0).  Any pointer may be NULL. */
 wadg_status wadg_group_info(const wadg_group* g, int32_t* nblocks, int32_t* threads,
-                            int32_t* blocks_per_sm, int32_t* tile_divisor, int32_t* nitems);
+                            int32_t* blocks_per_sm, int32_t* tile_divisor, int32_t* nitems,
+                            int32_t* nvariants, int32_t* parallel, int32_t* share);
 
 /* nsteps steps of every member with its own dt[n]; probe_out[n] (entries may
  * be NULL, or probe_out itself) receive each member's records laid out as in

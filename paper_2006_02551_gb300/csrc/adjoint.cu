@@ -34,19 +34,6 @@ struct AD {
 
 constexpr int kAdjThreads = 256;
 
-// outward unit normal and Fscale of face f from the metric terms
-template <typename Real>
-__device__ __forceinline__ void face_normal(const double* g, int f, Real* n, Real& fsc) {
-  double gx, gy, gz;
-  if (f == 0) { gx = -g[6]; gy = -g[7]; gz = -g[8]; }
-  else if (f == 1) { gx = -g[3]; gy = -g[4]; gz = -g[5]; }
-  else if (f == 2) { gx = g[0] + g[3] + g[6]; gy = g[1] + g[4] + g[7]; gz = g[2] + g[5] + g[8]; }
-  else { gx = -g[0]; gy = -g[1]; gz = -g[2]; }
-  const double mag = sqrt(gx * gx + gy * gy + gz * gz);
-  n[0] = (Real)(gx / mag); n[1] = (Real)(gy / mag); n[2] = (Real)(gz / mag);
-  fsc = (Real)mag;
-}
-
 template <typename Real>
 __device__ __forceinline__ void cross3(const Real* n, const Real* a, Real* o) {
   o[0] = n[1] * a[2] - n[2] * a[1];
@@ -69,7 +56,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_lift_kernel(const AdjParams<R
   const int ne = min(T, A.K - e0);
   const Real* lam = A.lam_q + (int64_t)b * A.strideQ;
   const Real* rho = A.rho_q + (int64_t)b * A.strideQ;
-  const Real Bi = (Real)A.rk_b;
+  const Real Bi = A.rk_b_r;
   for (int idx = tid; idx < ne * 6 * Np; idx += kAdjThreads) {
     const int e = idx / (6 * Np), r = idx - e * 6 * Np, c = r / Np;
     const int64_t gi = (int64_t)e0 * 6 * Np + idx;
@@ -78,15 +65,15 @@ __global__ void __launch_bounds__(kAdjThreads) adj_lift_kernel(const AdjParams<R
     (&a[0][0][0])[idx] = mu * s;
   }
   __syncthreads();
-  const Real* LIFTT = A.ops + 3 * Np * NpP;
+  constexpr int NFP = (NF + 3) & ~3;
+  const Real* LIFTN = A.adj_ops + 3 * Np * NpP;   // LIFT [Np][NFP]: consecutive fm adjacent
   Real* G = A.G + (int64_t)b * A.K * NF * 6;
   for (int idx = tid; idx < ne * NF; idx += kAdjThreads) {
     const int e = idx / NF, fm = idx - e * NF, f = fm / Nfp;
-    Real n[3], fsc;
-    face_normal(A.geo + (int64_t)(e0 + e) * 9, f, n, fsc);
+    const Real fsc = A.fnrm[(int64_t)(e0 + e) * 16 + f * 4 + 3];
     Real s[6] = {0, 0, 0, 0, 0, 0};
     for (int i = 0; i < Np; ++i) {
-      const Real L = LIFTT[fm * NpP + i];
+      const Real L = LIFTN[i * NFP + fm];
 #pragma unroll
       for (int c = 0; c < 6; ++c) s[c] += L * a[e][c][i];
     }
@@ -101,8 +88,8 @@ template <typename Real, int N, bool PML, int QC = 0>
 struct AdjTile {
   using D = AD<N, QC>;
   static constexpr int C = PML ? 12 : 6;
-  // MU, QF, ADJ [C][Np]; FLH [NF][3]; CH [3][Np]; (PML) ZZ [NqP][12]
-  static constexpr int per = 3 * C * D::Np + 3 * D::NF + (PML ? 12 * D::NqP : 0) + 16;
+  // MU, QF, ADJ [C][Np]; FLH [NF][3]; (PML) ZZ [NqP][12]; GE, metric [16]
+  static constexpr int per = 3 * C * D::Np + 3 * D::NF + (PML ? 12 * D::NqP : 0) + 16 + 16;
   static constexpr int budget = 80 * 1024;
   static constexpr int t0 = budget / (per * (int)sizeof(Real));
   static constexpr int T = t0 < 1 ? 1 : (t0 > 8 ? 8 : t0);
@@ -113,6 +100,11 @@ template <typename Real>
 __device__ __forceinline__ void atomic_add_real(Real* p, Real v) {
   atomicAdd(p, v);
 }
+
+// natural logarithm: the hardware approximation in FP32 (about 1e-6
+// relative error, below the FP32 adjoint's own), the library's in FP64
+__device__ __forceinline__ float log_fast(float x) { return __logf(x); }
+__device__ __forceinline__ double log_fast(double x) { return log(x); }
 
 template <typename Real, int N, bool PML, int QC = 0>
 __global__ void __launch_bounds__(kAdjThreads) adj_main_kernel(const AdjParams<Real> A) {
@@ -127,16 +119,24 @@ __global__ void __launch_bounds__(kAdjThreads) adj_main_kernel(const AdjParams<R
   Real* FLH = ADJ + T * C * Np;                    // [T][NF][3]  Fscale * forward flux (E rows)
   Real* ZZ = FLH + T * NF * 3;                     // [T][NqP][12] (PML)
   Real* GE = ZZ + (PML ? T * 12 * NqP : 0);        // [T] dJ/deps_k
-  int* srcl = reinterpret_cast<int*>(GE + T * 16);
+  Real* MET = GE + T * 16;                         // [T][9] metric r_x .. t_z
+  int* srcl = reinterpret_cast<int*>(MET + T * 16);
   __shared__ int nsl;
   __shared__ double red[6][kAdjThreads / 32];
 
-  const Real* DrT = A.ops;
+  constexpr int NFP = (NF + 3) & ~3;
+  const Real* DrT = A.ops;                 // D^T [Np][NpP]: DrT[j][i] = D_r[i][j]
   const Real* DsT = DrT + Np * NpP;
   const Real* DtT = DsT + Np * NpP;
-  const Real* LIFTT = DtT + Np * NpP;
-  const Real* VqT = LIFTT + NF * NpP;
-  const Real* PqT = VqT + Np * NqP;
+  const Real* LIFTT = DtT + Np * NpP;      // [NF][NpP]
+  const Real* VqT = LIFTT + NF * NpP;      // [Np][NqP]: VqT[i][q] = V_q[q][i]
+  // the same operators with the other index contiguous, so that threads over
+  // nodes or points read consecutive entries
+  const Real* DrN = A.adj_ops;             // [Np][NpP]: DrN[j][i] = D_r[j][i]
+  const Real* DsN = DrN + Np * NpP;
+  const Real* DtN = DsN + Np * NpP;
+  const Real* PqN = DtN + Np * NpP + Np * NFP;   // [Np][NqP]: PqN[i][q] = P_q[i][q]
+  const Real* VqR = PqN + Np * NqP;              // [Nq][NpP]: VqR[q][j] = V_q[q][j]
   const unsigned char* Fmask = A.tabs;
   const unsigned char* fperm = A.tabs + NF;
   const unsigned char* fmap = A.tabs + NF + 4 * 24 * Nfp;
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_main_kernel(const AdjParams<R
   const int ne = min(T, A.n_elem - t0);
   const int eg0 = A.e_begin + t0;
   const int ep0 = eg0 - A.K0;
-  const Real Bi = (Real)A.rk_b, Ai = (Real)A.rk_a, dt = (Real)A.dt;
+  const Real Bi = A.rk_b_r, Ai = A.rk_a_r, dt = A.dt_r;
   const double tst = A.t;
   Real* lam = A.lam_q + (int64_t)b * A.strideQ;
   Real* rho = A.rho_q + (int64_t)b * A.strideQ;
@@ -175,6 +175,8 @@ __global__ void __launch_bounds__(kAdjThreads) adj_main_kernel(const AdjParams<R
   }
   for (int idx = tid; idx < T * C * Np; idx += kAdjThreads) ADJ[idx] = 0;
   for (int idx = tid; idx < T; idx += kAdjThreads) GE[idx] = 0;
+  for (int idx = tid; idx < ne * 9; idx += kAdjThreads)
+    MET[idx] = (Real)A.geo[(int64_t)eg0 * 9 + idx];   // rounded once per element
   __syncthreads();
   for (int s = tid; s < A.nsrc; s += kAdjThreads) {
     const SrcDev& sd = A.src[s];
@@ -189,8 +191,8 @@ __global__ void __launch_bounds__(kAdjThreads) adj_main_kernel(const AdjParams<R
     const int e = idx / NF, fm = idx - e * NF, f = fm / Nfp, m = fm - f * Nfp;
     const int eg = eg0 + e;
     const int ni = Fmask[fm];
-    Real n[3], fsc;
-    face_normal(A.geo + (int64_t)eg * 9, f, n, fsc);
+    const Real* nf = A.fnrm + (int64_t)eg * 16 + f * 4;
+    const Real n[3] = {nf[0], nf[1], nf[2]}, fsc = nf[3];
     const Real* qf = QF + e * C * Np;
     Real Em[3], Hm[3], Ep[3], Hp[3];
 #pragma unroll
@@ -216,7 +218,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_main_kernel(const AdjParams<R
 #pragma unroll
       for (int c = 0; c < 3; ++c) { Ep[c] = -Em[c]; Hp[c] = Hm[c]; }
     }
-    const Real al = (Real)A.alpha;
+    const Real al = A.alpha_r;
     const Real YM = Real(1) / ZM, YP = Real(1) / ZP;
     const Real sH = Real(1) / (ZM + ZP), sE = Real(1) / (YM + YP);
     Real dE[3], dH[3];
@@ -305,7 +307,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_main_kernel(const AdjParams<R
 #pragma unroll
     for (int c = 0; c < 3; ++c) fw[c][0] = fw[c][1] = fw[c][2] = 0;
     for (int j = 0; j < Np; ++j) {
-      const Real r1 = DrT[i * NpP + j], s1 = DsT[i * NpP + j], t1 = DtT[i * NpP + j];  // D[j][i]
+      const Real r1 = DrN[j * NpP + i], s1 = DsN[j * NpP + i], t1 = DtN[j * NpP + i];  // D[j][i]
       const Real r2 = DrT[j * NpP + i], s2 = DsT[j * NpP + i], t2 = DtT[j * NpP + i];  // D[i][j]
 #pragma unroll
       for (int c = 0; c < 6; ++c) {
@@ -318,10 +320,10 @@ __global__ void __launch_bounds__(kAdjThreads) adj_main_kernel(const AdjParams<R
         fw[c][0] += r2 * h; fw[c][1] += s2 * h; fw[c][2] += t2 * h;
       }
     }
-    const double* gd = A.geo + (int64_t)eg * 9;
-    const Real rx = (Real)gd[0], ry = (Real)gd[1], rz = (Real)gd[2];
-    const Real sx = (Real)gd[3], sy = (Real)gd[4], sz = (Real)gd[5];
-    const Real tx = (Real)gd[6], ty = (Real)gd[7], tz = (Real)gd[8];
+    const Real* gd = MET + e * 9;
+    const Real rx = gd[0], ry = gd[1], rz = gd[2];
+    const Real sx = gd[3], sy = gd[4], sz = gd[5];
+    const Real tx = gd[6], ty = gd[7], tz = gd[8];
     // dT_x a = r_x D_r^T a + s_x D_s^T a + t_x D_t^T a (constant metric)
     Real dtx[6], dty[6], dtz[6];
 #pragma unroll
@@ -370,89 +372,147 @@ __global__ void __launch_bounds__(kAdjThreads) adj_main_kernel(const AdjParams<R
     atomic_add_real(&GE[e], ge);
   }
 
-  double gp[6] = {0, 0, 0, 0, 0, 0};   // d/dsigma_max[3], d/dp_sigma[3]
+  Real gp[6] = {0, 0, 0, 0, 0, 0};   // d/dsigma_max[3], d/dp_sigma[3] (this thread's points)
   if (PML) {
     __syncthreads();
     // ---- quadrature points: w = P_q^T mu, forward v = V_q q_in, the pullback
-    //      values of eqs. 26-29 transposed, and the profile derivatives
-    const Real ie0 = Real(1) / (Real)A.eps0;
-    for (int idx = tid; idx < ne * Nq; idx += kAdjThreads) {
-      const int e = idx / Nq, q = idx - e * Nq;
+    //      values of eqs. 26-29 transposed, and the profile derivatives.  Each
+    //      thread takes QB points of one element and one field group (g = 0:
+    //      E with P^E, g = 1: H with P^H; eq. 9 and the derivative sums never
+    //      mix the groups), so every mu and q_in value it loads serves QB
+    //      points.  ZZ[e][q][g][k]: k < 3 the field row, k >= 3 the P row.
+    constexpr int QB = Nq >= 48 ? 4 : 2;
+    constexpr int NQB = (Nq + QB - 1) / QB;
+    constexpr int NQI = NQB * 2;   // items per element (even: partner items on lanes 2m, 2m + 1)
+    const Real ie0 = A.inv_eps0_r;
+    const Real* rsm = A.inv_sigma_max;   // 1 / sigma_max, 1 / p_sigma per axis (0: unset)
+    const Real* rps = A.inv_p_sigma;
+    // every lane runs the same number of iterations: the E and H items of a
+    // point sit on neighbouring lanes and add their derivative shares by a
+    // shuffle before the per-point scaling
+    for (int base = 0; base < ne * NQI; base += kAdjThreads) {
+      const int idx = base + tid;
+      const bool act = idx < ne * NQI;
+      const int e = act ? idx / NQI : 0, r = act ? idx - e * NQI : 0;
+      const int g = r & 1, q0 = (r >> 1) * QB;
       const Real* mu = MU + e * C * Np;
       const Real* qf = QF + e * C * Np;
-      Real w[12], v[12];
+      Real w[QB][6], v[QB][6];
 #pragma unroll
-      for (int c = 0; c < 12; ++c) { w[c] = 0; v[c] = 0; }
-      for (int i = 0; i < Np; ++i) {
-        const Real pq = PqT[q * NpP + i];   // P_q[i][q]
-        const Real vq = VqT[i * NqP + q];   // V_q[q][i]
+      for (int k = 0; k < QB; ++k)
 #pragma unroll
-        for (int c = 0; c < 12; ++c) {
-          w[c] += pq * mu[c * Np + i];
-          v[c] += vq * qf[c * Np + i];
+        for (int c = 0; c < 6; ++c) { w[k][c] = 0; v[k][c] = 0; }
+      if (act) {
+        for (int i = 0; i < Np; ++i) {
+          Real m[6], f[6];
+#pragma unroll
+          for (int u = 0; u < 3; ++u) {
+            m[u] = mu[(3 * g + u) * Np + i];
+            m[3 + u] = mu[(6 + 3 * g + u) * Np + i];
+            f[u] = qf[(3 * g + u) * Np + i];
+            f[3 + u] = qf[(6 + 3 * g + u) * Np + i];
+          }
+#pragma unroll
+          for (int k = 0; k < QB; ++k) {
+            const int q = q0 + k;   // < NqP: the padded columns hold zeros
+            const Real pq = PqN[i * NqP + q];   // P_q[i][q]
+            const Real vq = VqT[i * NqP + q];   // V_q[q][i]
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+              w[k][c] += pq * m[c];
+              v[k][c] += vq * f[c];
+            }
+          }
         }
       }
-      const int64_t sb = (int64_t)(ep0 + e) * 3 * NqP + q;
-      const Real sg[3] = {A.sig[sb], A.sig[sb + NqP], A.sig[sb + 2 * NqP]};
-      Real* zz = ZZ + (e * NqP + q) * 12;
 #pragma unroll
-      for (int u = 0; u < 3; ++u) {
-        const int vv = (u + 1) % 3, ww = (u + 2) % 3;
-        const Real bu = (sg[vv] + sg[ww] - sg[u]) * ie0;
-        const Real cu = sg[vv] * sg[ww] * ie0 * ie0 - bu * sg[u] * ie0;
-        const Real du = sg[u] * ie0;
-        // rows: E_u (0+u), H_u (3+u), P^E_u (6+u), P^H_u (9+u)
-        zz[u] = -bu * w[u] + w[6 + u];
-        zz[6 + u] = -cu * w[u] - du * w[6 + u];
-        zz[3 + u] = -bu * w[3 + u] + w[9 + u];
-        zz[9 + u] = -cu * w[3 + u] - du * w[9 + u];
-      }
-      // d/dtheta of mu . f through b, c, d at this point
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        if (!(sg[a] > 0)) continue;
-        const double smax = A.sigma_max[a], ps = A.p_sigma[a];
-        const double dsm = smax > 0 ? (double)sg[a] / smax : 0.0;             // d sigma_a / d sigma_max_a
-        const double dsp = (smax > 0 && ps > 0) ? (double)sg[a] * log((double)sg[a] / smax) / ps
-                                                : 0.0;                        // d sigma_a / d p_a
-        for (int k = 0; k < 2; ++k) {
-          const double dsa = k == 0 ? dsm : dsp;
-          double acc = 0;
+      for (int k = 0; k < QB; ++k) {
+        const int q = q0 + k;
+        const bool live = act && q < Nq;
+        Real sg[3] = {0, 0, 0};
+        if (live) {
+          const int64_t sb = (int64_t)(ep0 + e) * 3 * NqP + q;
+          sg[0] = A.sig[sb];
+          sg[1] = A.sig[sb + NqP];
+          sg[2] = A.sig[sb + 2 * NqP];
+          Real* zz = ZZ + ((e * NqP + q) * 2 + g) * 6;
 #pragma unroll
           for (int u = 0; u < 3; ++u) {
             const int vv = (u + 1) % 3, ww = (u + 2) % 3;
-            const double ds_u = (u == a) ? dsa : 0.0, ds_v = (vv == a) ? dsa : 0.0;
-            const double ds_w = (ww == a) ? dsa : 0.0;
-            const double bu = ((double)sg[vv] + sg[ww] - sg[u]) * (double)ie0;
-            const double db = (ds_v + ds_w - ds_u) * (double)ie0;
-            const double dc = (ds_v * sg[ww] + (double)sg[vv] * ds_w) * (double)ie0 * ie0 -
-                              (db * sg[u] + bu * ds_u) * (double)ie0;
-            const double dd = ds_u * (double)ie0;
-            acc -= (double)w[u] * (db * v[u] + dc * v[6 + u]);
-            acc -= (double)w[3 + u] * (db * v[3 + u] + dc * v[9 + u]);
-            acc -= (double)w[6 + u] * dd * v[6 + u];
-            acc -= (double)w[9 + u] * dd * v[9 + u];
+            const Real bu = (sg[vv] + sg[ww] - sg[u]) * ie0;
+            const Real cu = sg[vv] * sg[ww] * ie0 * ie0 - bu * sg[u] * ie0;
+            const Real du = sg[u] * ie0;
+            zz[u] = -bu * w[k][u] + w[k][3 + u];
+            zz[3 + u] = -cu * w[k][u] - du * w[k][3 + u];
           }
-          gp[k * 3 + a] += acc;
+        }
+        // d/dtheta of mu . f through b, c, d at this point.  It is linear in
+        // the derivative of sigma_a: one sum per axis with d sigma_a = 1 (this
+        // group's share, then both groups'), scaled by d sigma_a / d
+        // sigma_max_a = sigma_a / sigma_max_a and d sigma_a / d p_a =
+        // sigma_a log(sigma_a / sigma_max_a) / p_a
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          Real acc = 0;
+          if (live && sg[a] > 0) {
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+              const int vv = (u + 1) % 3, ww = (u + 2) % 3;
+              const Real ds_u = u == a ? Real(1) : Real(0), ds_v = vv == a ? Real(1) : Real(0);
+              const Real ds_w = ww == a ? Real(1) : Real(0);
+              const Real bu = (sg[vv] + sg[ww] - sg[u]) * ie0;
+              const Real db = (ds_v + ds_w - ds_u) * ie0;
+              const Real dc =
+                  (ds_v * sg[ww] + sg[vv] * ds_w) * ie0 * ie0 - (db * sg[u] + bu * ds_u) * ie0;
+              const Real dd = ds_u * ie0;
+              acc -= w[k][u] * (db * v[k][u] + dc * v[k][3 + u]) + dd * w[k][3 + u] * v[k][3 + u];
+            }
+          }
+          acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+          if (g == 0 && live && sg[a] > 0 && rsm[a] > 0) {
+            const Real x = sg[a] * rsm[a];
+            gp[a] += x * acc;
+            gp[3 + a] += sg[a] * log_fast(x) * rps[a] * acc;
+          }
         }
       }
     }
     __syncthreads();
-    // ---- V_q^T pullback to the nodes
-    for (int idx = tid; idx < ne * Np; idx += kAdjThreads) {
-      const int e = idx / Np, j = idx - e * Np;
-      Real s[12];
+    // ---- V_q^T pullback to the nodes: two nodes of one element and one
+    //      field group per thread
+    constexpr int JB = 2;
+    constexpr int NJB = (Np + JB - 1) / JB;
+    for (int idx = tid; idx < ne * NJB * 2; idx += kAdjThreads) {
+      const int e = idx / (NJB * 2), r = idx - e * (NJB * 2), g = r & 1, j0 = (r >> 1) * JB;
+      Real sacc[JB][6];
 #pragma unroll
-      for (int c = 0; c < 12; ++c) s[c] = 0;
+      for (int k = 0; k < JB; ++k)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) sacc[k][c] = 0;
       for (int q = 0; q < Nq; ++q) {
-        const Real vq = VqT[j * NqP + q];
-        const Real* zz = ZZ + (e * NqP + q) * 12;
+        const Real* zz = ZZ + ((e * NqP + q) * 2 + g) * 6;
+        Real z[6];
 #pragma unroll
-        for (int c = 0; c < 12; ++c) s[c] += vq * zz[c];
+        for (int c = 0; c < 6; ++c) z[c] = zz[c];
+#pragma unroll
+        for (int k = 0; k < JB; ++k) {
+          const int j = j0 + k;   // < NpP: the padded columns hold zeros
+          const Real vq = VqR[q * NpP + j];   // V_q[q][j]
+#pragma unroll
+          for (int c = 0; c < 6; ++c) sacc[k][c] += vq * z[c];
+        }
       }
       Real* ad = ADJ + e * C * Np;
 #pragma unroll
-      for (int c = 0; c < 12; ++c) ad[c * Np + j] += s[c];
+      for (int k = 0; k < JB; ++k) {
+        const int j = j0 + k;
+        if (j >= Np) break;
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          ad[(3 * g + u) * Np + j] += sacc[k][u];
+          ad[(6 + 3 * g + u) * Np + j] += sacc[k][3 + u];
+        }
+      }
     }
   }
   __syncthreads();
@@ -477,13 +537,14 @@ __global__ void __launch_bounds__(kAdjThreads) adj_main_kernel(const AdjParams<R
   for (int e = tid; e < ne; e += kAdjThreads)
     A.grad_eps[(int64_t)b * A.K + eg0 + e] += (double)dt * (double)GE[e];
   if (PML) {
-    // block reduction of the profile derivatives
+    // block reduction of the profile derivatives: across the warp in the
+    // working precision, across warps in double
     const int lane = tid & 31, wid = tid >> 5;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-      double v = gp[k];
+      Real v = gp[k];
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) red[k][wid] = v;
+      if (lane == 0) red[k][wid] = (double)v;
     }
     __syncthreads();
     if (tid < 6) {

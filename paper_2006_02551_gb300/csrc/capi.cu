@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -252,7 +253,7 @@ wadg_status upload_ops(wadg_ctx* ctx) {
   const RefOps& R = ctx->ref;
   const int Np = R.Np, Nfp = R.Nfp, Nq = R.Nq, NF = 4 * Nfp;
   // padded, transposed layouts: DrT, DsT, DtT [Np][NpP], LIFTT [NF][NpP],
-  // VqT [Np][NqP], PqT [Nq][NpP] (zeros in the padding)
+  // VqT [Np][NqP], PqT [Nq][NpP] (zeros in the padding), then the adjoint's
   const int NpP = (Np + 3) & ~3, NqP = (Nq + 3) & ~3;
   std::vector<double> h;
   for (const std::vector<double>* D : {&R.Dr, &R.Ds, &R.Dt})
@@ -264,6 +265,19 @@ wadg_status upload_ops(wadg_ctx* ctx) {
     for (int q = 0; q < NqP; ++q) h.push_back(q < Nq ? R.Vq[(size_t)q * Np + j] : 0.0);
   for (int q = 0; q < Nq; ++q)
     for (int i = 0; i < NpP; ++i) h.push_back(i < Np ? R.Pq[(size_t)i * Nq + q] : 0.0);
+  // for the adjoint, the same operators laid out so that consecutive threads
+  // read consecutive entries: Dr, Ds, Dt [Np][NpP] (row j of D), LIFT
+  // [Np][NFP] (row i), P_q [Np][NqP] (row i), V_q [Nq][NpP] (row q)
+  const int NFP = (NF + 3) & ~3;
+  for (const std::vector<double>* D : {&R.Dr, &R.Ds, &R.Dt})
+    for (int j = 0; j < Np; ++j)
+      for (int i = 0; i < NpP; ++i) h.push_back(i < Np ? (*D)[j * Np + i] : 0.0);
+  for (int i = 0; i < Np; ++i)
+    for (int fm = 0; fm < NFP; ++fm) h.push_back(fm < NF ? R.LIFT[(size_t)i * NF + fm] : 0.0);
+  for (int i = 0; i < Np; ++i)
+    for (int q = 0; q < NqP; ++q) h.push_back(q < Nq ? R.Pq[(size_t)i * Nq + q] : 0.0);
+  for (int q = 0; q < Nq; ++q)
+    for (int j = 0; j < NpP; ++j) h.push_back(j < Np ? R.Vq[(size_t)q * Np + j] : 0.0);
   std::vector<Real> hr = cvt<Real>(h);
   CK(dalloc(ctx->ops, hr.size() * sizeof(Real)));
   CK(cudaMemcpy(ctx->ops.p, hr.data(), hr.size() * sizeof(Real), cudaMemcpyHostToDevice));
@@ -1489,12 +1503,14 @@ wadg_status adjoint_typed(wadg_ctx* ctx, int64_t nsteps, double dt, int C, doubl
   const int nb = ctx->nb;
   const double t0 = ctx->t;
   const int64_t nseg = (nsteps + C - 1) / C;
-  std::vector<StateBuf> ck(nseg + 1), seg(C + 1), stin(5);
+  // ck: the state every C steps.  sin: the stage inputs of one segment as it
+  // is recomputed, sin[5k + i - 1] = input of stage i of step k (i = 0, k = 0
+  // is the checkpoint itself), sin[5n - 1] = the state at the segment's end
+  std::vector<StateBuf> ck(nseg + 1), sin(5 * (size_t)std::min<int64_t>(C, nsteps));
   DevPtr lq, rq, lp, rp, G, ge, gp;
   auto cleanup = [&]() {
     for (auto& b : ck) free_state(b);
-    for (auto& b : seg) free_state(b);
-    for (auto& b : stin) free_state(b);
+    for (auto& b : sin) free_state(b);
     for (DevPtr* d : {&lq, &rq, &lp, &rp, &G, &ge, &gp}) dfree(*d);
   };
   auto fail_clean = [&](wadg_status st) {
@@ -1503,8 +1519,7 @@ wadg_status adjoint_typed(wadg_ctx* ctx, int64_t nsteps, double dt, int C, doubl
   };
   wadg_status st = WADG_OK;
   for (auto& b : ck) if ((st = alloc_state(ctx, b)) != WADG_OK) return fail_clean(st);
-  for (auto& b : seg) if ((st = alloc_state(ctx, b)) != WADG_OK) return fail_clean(st);
-  for (auto& b : stin) if ((st = alloc_state(ctx, b)) != WADG_OK) return fail_clean(st);
+  for (auto& b : sin) if ((st = alloc_state(ctx, b)) != WADG_OK) return fail_clean(st);
   const size_t qb = ctx->q[0].bytes, pb = ctx->p.bytes;
   cudaError_t ce = cudaSuccess;
   if (ce == cudaSuccess) ce = dalloc(lq, qb);
@@ -1548,49 +1563,63 @@ wadg_status adjoint_typed(wadg_ctx* ctx, int64_t nsteps, double dt, int C, doubl
   AdjParams<Real> A{};
   A.lam_q = (Real*)lq.p; A.rho_q = (Real*)rq.p; A.lam_p = (Real*)lp.p; A.rho_p = (Real*)rp.p;
   A.G = (Real*)G.p; A.grad_eps = (double*)ge.p; A.grad_prof = (double*)gp.p;
-  A.geo = (const double*)ctx->geo.p; A.mat = (const Real*)ctx->mat.p;
+  A.geo = (const double*)ctx->geo.p; A.fnrm = (const Real*)ctx->fnrm.p;
+  A.mat = (const Real*)ctx->mat.p;
   A.nbr = (const int*)ctx->nbr.p; A.code = (const unsigned char*)ctx->code.p;
   A.sig = (const Real*)ctx->sig.p; A.ops = (const Real*)ctx->ops.p;
+  {
+    const int NpP = (Np + 3) & ~3, NqP = (ctx->ref.Nq + 3) & ~3;
+    A.adj_ops = A.ops + 3 * Np * NpP + 4 * Nfp * NpP + Np * NqP + ctx->ref.Nq * NpP;
+  }
   A.tabs = (const unsigned char*)ctx->tabs.p;
   A.strideQ = K * 6 * Np; A.strideP = K1 * 6 * Np;
   A.K = (int)K; A.K0 = (int)ctx->K0;
   A.nsrc = ctx->nsrc; A.src = (const SrcDev*)ctx->src.p; A.src_w = (const Real*)ctx->srcw.p;
   A.dt = dt; A.eps0 = ctx->has_prof ? ctx->prof.eps0 : 1.0; A.alpha = 1.0;
+  A.dt_r = (Real)A.dt; A.alpha_r = (Real)A.alpha; A.inv_eps0_r = (Real)(1.0 / A.eps0);
   for (int u = 0; u < 3; ++u) {
     A.sigma_max[u] = ctx->has_prof ? ctx->prof.sigma_max[u] : 0.0;
     A.p_sigma[u] = ctx->has_prof ? ctx->prof.p_sigma[u] : 0.0;
+    A.inv_sigma_max[u] = A.sigma_max[u] > 0 ? (Real)(1.0 / A.sigma_max[u]) : Real(0);
+    A.inv_p_sigma[u] =
+        A.sigma_max[u] > 0 && A.p_sigma[u] > 0 ? (Real)(1.0 / A.p_sigma[u]) : Real(0);
   }
   for (int64_t sg = nseg - 1; sg >= 0; --sg) {
     const int64_t s0 = sg * C, n = std::min<int64_t>(C, nsteps - s0);
-    // step-start states of the segment, recomputed from its checkpoint
-    CK(cudaMemcpyAsync(seg[0].q.p, ck[sg].q.p, qb, cudaMemcpyDeviceToDevice, ctx->stream));
-    if (pb) CK(cudaMemcpyAsync(seg[0].p.p, ck[sg].p.p, pb, cudaMemcpyDeviceToDevice, ctx->stream));
-    for (int64_t k = 0; k < n; ++k) {
-      if ((st = load_state(ctx, seg[k])) != WADG_OK) return fail_clean(st);
-      for (int i = 0; i < 5; ++i)
-        if ((st = issue_stage<Real>(ctx, i, dt, t0 + (s0 + k) * dt, false)) != WADG_OK)
-          return fail_clean(st);
-      if ((st = save_state(ctx, seg[k + 1])) != WADG_OK) return fail_clean(st);
-    }
+    // stage input j = 5k + i of the segment (j = 5n: its end state)
+    auto stage_in = [&](int64_t j) -> StateBuf& { return j == 0 ? ck[sg] : sin[j - 1]; };
+    // recompute the segment from its checkpoint, each stage reading its input
+    // and writing the next one in place (no copies; the Runge-Kutta register
+    // restarts at every step since A_0 = 0)
+    for (int64_t k = 0; k < n; ++k)
+      for (int i = 0; i < 5; ++i) {
+        const StateBuf& a = stage_in(5 * k + i);
+        const StateBuf& b = stage_in(5 * k + i + 1);
+        for (int cls = 0; cls < 2; ++cls) {
+          if (cls == 1 && K1 == 0) continue;
+          StageParams<Real> P = stage_params<Real>(ctx, i, dt, t0 + (s0 + k) * dt, false, cls == 1);
+          P.qin = (const Real*)a.q.p;
+          P.qout = (Real*)b.q.p;
+          P.p = (Real*)a.p.p;
+          P.pout = (Real*)b.p.p;
+          if (cls == 0) CK(launch_stage<Real>(ctx->N, false, false, P, ctx->nb, ctx->stream));
+          else CK(launch_pml_class<Real>(ctx, P));
+        }
+      }
     for (int64_t k = n - 1; k >= 0; --k) {
       const double tn = t0 + (s0 + k) * dt;
       // objective after step s0 + k: dJ/dE at the probes
       if (ctx->nprobe > 0)
-        CK(launch_adjoint_probes<Real>((const Real*)seg[k + 1].q.p, K * 6 * Np, ctx->nprobe, nb,
-                                       Np, (const int*)ctx->pr_elem.p,
+        CK(launch_adjoint_probes<Real>((const Real*)stage_in(5 * k + 5).q.p, K * 6 * Np,
+                                       ctx->nprobe, nb, Np, (const int*)ctx->pr_elem.p,
                                        (const double*)ctx->pr_ell.p, (Real*)lq.p, ctx->stream));
-      // the five stage inputs of this step
-      if ((st = load_state(ctx, seg[k])) != WADG_OK) return fail_clean(st);
-      for (int i = 0; i < 5; ++i) {
-        if ((st = save_state(ctx, stin[i])) != WADG_OK) return fail_clean(st);
-        if (i < 4 && (st = issue_stage<Real>(ctx, i, dt, tn, false)) != WADG_OK)
-          return fail_clean(st);
-      }
       for (int i = 4; i >= 0; --i) {
-        A.q_in = (const Real*)stin[i].q.p;
-        A.p_in = (const Real*)stin[i].p.p;
+        A.q_in = (const Real*)stage_in(5 * k + i).q.p;
+        A.p_in = (const Real*)stage_in(5 * k + i).p.p;
         A.rk_a = kRkA[i];
         A.rk_b = kRkB[i];
+        A.rk_a_r = (Real)A.rk_a;
+        A.rk_b_r = (Real)A.rk_b;
         A.t = tn + kRkC.c[i] * dt;
         CK(launch_adjoint_stage<Real>(ctx->N, A, nb, ctx->stream, ctx->qc));
       }
@@ -1897,14 +1926,22 @@ struct wadg_group {
   int sms = 1;
   int blocks_per_sm = 1;   // autotuned
   int tile_div = 1;        // autotuned: tile = largest tile / tile_div
-  int threads = 256;       // autotuned: threads per block (256 or 512)
-  size_t smem = 0;
-  int nblocks = 0;
+  bool parallel = true;    // autotuned: a stage's variant launches on parallel branches
+  bool share = false;      // autotuned: a variant's grid is its share of the GPU (by
+                           // algorithmic flops) instead of the whole GPU
+  int nblocks = 0;         // all variants
   struct Item { int c; bool pml; int code; int tile; int64_t tiles; double work; };
-  std::vector<Item> items;
+  std::vector<Item> items;   // sorted by variant code
+  // a variant: the items [off, off + n) of one code, its kernel's shared
+  // memory and grid, and its block split first[foff .. foff + n]
+  struct Variant { int code; int off, n; size_t smem; int nblocks; int foff; };
+  std::vector<Variant> vars;
   std::vector<int> first;
-  DevPtr dparams, dfirst, dcode;   // params [2 parities][5 stages][items]
+  DevPtr dparams, dfirst;          // params [2 parities][5 stages][items]
   DevPtr dntiles, dcounter;        // tiles per item, tile counters (zeroed per launch)
+  // streams and events of the parallel branches (variant v > 0 on aux[v - 1])
+  std::vector<cudaStream_t> aux;
+  std::vector<cudaEvent_t> ev;     // ev[0] fork, ev[v] join of variant v
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
 };
 
@@ -1955,10 +1992,12 @@ double item_cost(int N, bool pml) {
   return f;
 }
 
-// work items, tile sizes and the block split for the current tuning
+// work items (sorted by variant), tile sizes, and each variant's grid and
+// block split for the current tuning.  A variant's grid fills the GPU at its
+// own occupancy: its blocks run as long as its tiles last, and the SMs they
+// leave go to the other variants of the stage (parallel graph branches).
 void group_plan(wadg_group* g) {
   g->items.clear();
-  g->smem = 0;
   for (int c = 0; c < (int)g->ctx.size(); ++c) {
     wadg_ctx* x = g->ctx[c];
     for (int cls = 0; cls < 2; ++cls) {
@@ -1969,24 +2008,68 @@ void group_plan(wadg_group* g) {
       it.c = c;
       it.pml = pml;
       it.code = x->N * 4 + (pml ? (x->kappa ? 2 : 1) : 0);
-      const int tmax = group_tile_max(x->N, pml, g->threads);
+      const int tmax = group_tile_max(x->N, pml);
       it.tile = std::max(1, tmax / g->tile_div);
       it.tiles = (ne + it.tile - 1) / it.tile * x->nb;
       it.work = item_cost(x->N, pml) * (double)ne * x->nb;
       g->items.push_back(it);
-      g->smem = std::max(g->smem, group_smem_bytes(x->N, pml, it.tile, g->threads));
     }
   }
-  double tot = 0.0;
-  for (auto& it : g->items) tot += it.work;
-  const int want = g->blocks_per_sm * g->sms;
-  g->first.assign(1, 0);
-  for (auto& it : g->items) {
-    int64_t nb = (int64_t)std::llround(want * it.work / std::max(tot, 1.0));
-    nb = std::max<int64_t>(1, std::min<int64_t>(nb, it.tiles));
-    g->first.push_back(g->first.back() + (int)nb);
+  // heaviest variants first: their launches are issued first
+  std::map<int, double> vwork;
+  for (auto& it : g->items) vwork[it.code] += it.work;
+  std::stable_sort(g->items.begin(), g->items.end(), [&](const auto& a, const auto& b) {
+    return a.code != b.code && (vwork[a.code] > vwork[b.code] ||
+                                (vwork[a.code] == vwork[b.code] && a.code < b.code));
+  });
+  g->vars.clear();
+  g->first.clear();
+  g->nblocks = 0;
+  double all = 0.0;
+  for (auto& it : g->items) all += it.work;
+  all = std::max(all, 1.0);
+  for (int i = 0; i < (int)g->items.size();) {
+    wadg_group::Variant v{};
+    v.code = g->items[i].code;
+    v.off = i;
+    while (i < (int)g->items.size() && g->items[i].code == v.code) ++i;
+    v.n = i - v.off;
+    double tot = 0.0;
+    for (int j = v.off; j < i; ++j) {
+      const auto& it = g->items[j];
+      v.smem = std::max(v.smem, group_smem_bytes(it.code / 4, it.pml, it.tile));
+      tot += it.work;
+    }
+    const int bps = std::max(1, std::min(g->blocks_per_sm, group_blocks_per_sm(v.code, v.smem)));
+    const int want = g->share ? std::max(1, (int)std::lround(bps * g->sms * tot / all))
+                              : bps * g->sms;
+    v.foff = (int)g->first.size();
+    g->first.push_back(0);
+    for (int j = v.off; j < i; ++j) {
+      const auto& it = g->items[j];
+      int64_t nb = (int64_t)std::llround(want * it.work / std::max(tot, 1.0));
+      nb = std::max<int64_t>(1, std::min<int64_t>(nb, it.tiles));
+      g->first.push_back(g->first.back() + (int)nb);
+    }
+    v.nblocks = g->first.back();
+    g->nblocks += v.nblocks;
+    g->vars.push_back(v);
   }
-  g->nblocks = g->first.back();
+}
+
+// the streams and events of the parallel branches
+wadg_status group_branches(wadg_group* g) {
+  while (g->aux.size() + 1 < g->vars.size()) {
+    cudaStream_t st;
+    GCK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    g->aux.push_back(st);
+  }
+  while (g->ev.size() < std::max<size_t>(1, g->vars.size())) {
+    cudaEvent_t e;
+    GCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    g->ev.push_back(e);
+  }
+  return WADG_OK;
 }
 
 // stage parameters of every item for both step parities and all 5 stages
@@ -2008,41 +2091,54 @@ wadg_status group_upload(wadg_group* g, const double* dt) {
         hp[((size_t)par * 5 + st) * ni + i] = P;
         x->cur = cur0[it.c];
       }
-  std::vector<int> code(ni), ntiles(ni);
-  for (int i = 0; i < ni; ++i) {
-    code[i] = g->items[i].code;
-    ntiles[i] = (int)g->items[i].tiles;
-  }
+  std::vector<int> ntiles(ni);
+  for (int i = 0; i < ni; ++i) ntiles[i] = (int)g->items[i].tiles;
   GCK(dalloc(g->dntiles, ntiles.size() * sizeof(int)));
   GCK(dalloc(g->dcounter, ntiles.size() * sizeof(int)));
   GCK(cudaMemcpy(g->dntiles.p, ntiles.data(), ntiles.size() * sizeof(int), cudaMemcpyHostToDevice));
   GCK(dalloc(g->dparams, hp.size() * sizeof(StageParams<float>)));
   GCK(dalloc(g->dfirst, g->first.size() * sizeof(int)));
-  GCK(dalloc(g->dcode, code.size() * sizeof(int)));
   GCK(cudaMemcpy(g->dparams.p, hp.data(), hp.size() * sizeof(StageParams<float>),
                  cudaMemcpyHostToDevice));
   GCK(cudaMemcpy(g->dfirst.p, g->first.data(), g->first.size() * sizeof(int),
                  cudaMemcpyHostToDevice));
-  GCK(cudaMemcpy(g->dcode.p, code.data(), code.size() * sizeof(int), cudaMemcpyHostToDevice));
-  return WADG_OK;
+  return group_branches(g);
 }
 
-GroupParams group_params(wadg_group* g, int par, int st) {
+GroupParams group_params(wadg_group* g, const wadg_group::Variant& v, int par, int st) {
   GroupParams G{};
-  G.p = (const StageParams<float>*)g->dparams.p + ((size_t)par * 5 + st) * g->items.size();
-  G.first = (const int*)g->dfirst.p;
-  G.code = (const int*)g->dcode.p;
-  G.ntiles = (const int*)g->dntiles.p;
-  G.counter = (int*)g->dcounter.p;
-  G.nitems = (int)g->items.size();
+  G.p = (const StageParams<float>*)g->dparams.p + ((size_t)par * 5 + st) * g->items.size() + v.off;
+  G.first = (const int*)g->dfirst.p + v.foff;
+  G.ntiles = (const int*)g->dntiles.p + v.off;
+  G.counter = (int*)g->dcounter.p + v.off;
+  G.nitems = v.n;
   return G;
 }
 
-// one grouped stage launch: clear the tile counters, launch
+// one grouped stage: clear the tile counters, then one launch per variant,
+// variant 0 on the group's stream and the others on parallel branches that
+// fork from it after the clear and join it before the next stage
 cudaError_t group_launch(wadg_group* g, int par, int st) {
   cudaError_t e = cudaMemsetAsync(g->dcounter.p, 0, g->items.size() * sizeof(int), g->stream);
   if (e != cudaSuccess) return e;
-  return launch_group_stage(group_params(g, par, st), g->nblocks, g->smem, g->threads, g->stream);
+  const size_t nv = g->vars.size();
+  const bool fork = g->parallel && nv > 1;
+  if (fork) {
+    if ((e = cudaEventRecord(g->ev[0], g->stream)) != cudaSuccess) return e;
+    for (size_t v = 1; v < nv; ++v)
+      if ((e = cudaStreamWaitEvent(g->aux[v - 1], g->ev[0], 0)) != cudaSuccess) return e;
+  }
+  for (size_t v = 0; v < nv; ++v) {
+    const auto& V = g->vars[v];
+    cudaStream_t s = v == 0 || !fork ? g->stream : g->aux[v - 1];
+    e = launch_group_stage(V.code, group_params(g, V, par, st), V.nblocks, V.smem, s);
+    if (e != cudaSuccess) return e;
+  }
+  for (size_t v = 1; fork && v < nv; ++v) {
+    if ((e = cudaEventRecord(g->ev[v], g->aux[v - 1])) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(g->stream, g->ev[v], 0)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 // one step of parity par: 5 grouped stage launches, then every member's probes
@@ -2122,8 +2218,7 @@ wadg_status wadg_group_create(int32_t n, wadg_ctx* const* ctxs, wadg_group** out
     delete g;
     return fail(nullptr, WADG_ECUDA, "group kernel set-up: %s", cudaGetErrorString(e));
   }
-  group_plan(g);
-  g->blocks_per_sm = std::max(1, std::min(2, group_blocks_per_sm(g->smem, g->threads)));
+  g->blocks_per_sm = 2;   // capped per variant by its occupancy
   group_plan(g);
   *out = g;
   return WADG_OK;
@@ -2135,9 +2230,10 @@ wadg_status wadg_group_destroy(wadg_group* g) {
   group_drop_graphs(g);
   dfree(g->dparams);
   dfree(g->dfirst);
-  dfree(g->dcode);
   dfree(g->dntiles);
   dfree(g->dcounter);
+  for (cudaStream_t st : g->aux) cudaStreamDestroy(st);
+  for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
   delete g;
   return WADG_OK;
 }
@@ -2152,14 +2248,18 @@ wadg_status wadg_group_autotune(wadg_group* g, const double* dt, int32_t reps, d
   GCK(cudaEventCreate(&e0));
   GCK(cudaEventCreate(&e1));
   double best = 1e300;
-  int best_bps = 1, best_div = 1, best_thr = 256;
-  for (int thr : {256, 512})
+  int best_bps = 1, best_div = 1;
+  bool best_par = true, best_share = false;
+  for (int par = 1; par >= 0; --par)
+  for (int shr = 0; shr < 2; ++shr)
   for (int div : {1, 2, 4}) {
-    g->threads = thr;
+    g->parallel = par != 0;
+    g->share = shr != 0;
     g->tile_div = div;
     g->blocks_per_sm = 1;
     group_plan(g);
-    const int occ = std::max(1, group_blocks_per_sm(g->smem, thr));
+    int occ = 1;   // the most blocks per SM any variant can hold
+    for (const auto& v : g->vars) occ = std::max(occ, group_blocks_per_sm(v.code, v.smem));
     for (int bps = 1; bps <= std::min(occ, 4); ++bps) {
       g->blocks_per_sm = bps;
       group_plan(g);
@@ -2172,24 +2272,31 @@ wadg_status wadg_group_autotune(wadg_group* g, const double* dt, int32_t reps, d
       GCK(cudaEventSynchronize(e1));
       float ms = 0.f;
       GCK(cudaEventElapsedTime(&ms, e0, e1));
-      if (ms < best) { best = ms; best_bps = bps; best_div = div; best_thr = thr; }
+      if (ms < best) {
+        best = ms; best_bps = bps; best_div = div; best_par = g->parallel; best_share = g->share;
+      }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   g->blocks_per_sm = best_bps;
   g->tile_div = best_div;
-  g->threads = best_thr;
+  g->parallel = best_par;
+  g->share = best_share;
   group_plan(g);
   if (ms_out) *ms_out = best / reps;
   return WADG_OK;
 }
 
 wadg_status wadg_group_info(const wadg_group* g, int32_t* nblocks, int32_t* threads,
-                            int32_t* blocks_per_sm, int32_t* tile_divisor, int32_t* nitems) {
+                            int32_t* blocks_per_sm, int32_t* tile_divisor, int32_t* nitems,
+                            int32_t* nvariants, int32_t* parallel, int32_t* share) {
   if (!g) return WADG_EINVAL;
+  if (nvariants) *nvariants = (int32_t)g->vars.size();
+  if (parallel) *parallel = g->parallel ? 1 : 0;
+  if (share) *share = g->share ? 1 : 0;
   if (nblocks) *nblocks = g->nblocks;
-  if (threads) *threads = g->threads;
+  if (threads) *threads = g->vars.empty() ? 0 : group_threads(g->vars[0].code);
   if (blocks_per_sm) *blocks_per_sm = g->blocks_per_sm;
   if (tile_divisor) *tile_divisor = g->tile_div;
   if (nitems) *nitems = (int32_t)g->items.size();

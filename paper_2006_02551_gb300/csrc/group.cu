@@ -1,58 +1,57 @@
 // Grouped launch of the CUDA-core stage (FP32): several contexts' element
-// classes advanced by one kernel launch per Runge-Kutta stage.
+// classes advanced with one launch per (order, element class) variant and
+// Runge-Kutta stage.
 #include "stage_body.cuh"
 
 namespace wadg {
 
 // ------------------------------------------------------------ grouped launch
-// One launch advances every element class of every context of a group by one
-// stage (FP32).  Every block starts on the (context, class) item the static
-// split gives it, takes that item's tiles from its counter, then moves on to
-// the items that still have tiles, restaging the operators once per item.
-// Two block shapes: 256 threads (two blocks per SM) or 512 (one).
+// A grouped stage advances every element class of every context of a group
+// by one stage (FP32) with one launch per (order, element class) variant
+// present.  A variant's kernel is the single-context stage kernel of that
+// variant (same body, block shape, tile and register budget) with a dynamic
+// tile schedule over the variant's items; the host issues a stage's variant
+// launches on parallel branches of the step graph, so one variant's blocks
+// take the SMs that another's leave as its tiles run out.
+
+template <int N, bool PML>
+using GTile = Tile<float, N, PML, 0, 0>;
 
 // dynamic shared memory of one item with `tile` elements per tile
-template <int N, bool PML, int NT>
+template <int N, bool PML>
 size_t group_smem_one(int tile) {
-  using TL = Tile<float, N, PML, NT>;
+  using TL = GTile<N, PML>;
   const int t = tile > 0 && tile < TL::T ? tile : TL::T;
   return (size_t)(TL::ops_sz + t * TL::per_elem) * sizeof(float) + 64 * sizeof(int);
 }
 
-template <int NT>
-size_t group_smem_nt(int N, bool pml, int tile) {
+size_t group_smem_bytes(int N, bool pml, int tile) {
   switch (N) {
-    case 1: return pml ? group_smem_one<1, true, NT>(tile) : group_smem_one<1, false, NT>(tile);
-    case 2: return pml ? group_smem_one<2, true, NT>(tile) : group_smem_one<2, false, NT>(tile);
-    case 3: return pml ? group_smem_one<3, true, NT>(tile) : group_smem_one<3, false, NT>(tile);
-    case 4: return pml ? group_smem_one<4, true, NT>(tile) : group_smem_one<4, false, NT>(tile);
-    case 5: return pml ? group_smem_one<5, true, NT>(tile) : group_smem_one<5, false, NT>(tile);
+    case 1: return pml ? group_smem_one<1, true>(tile) : group_smem_one<1, false>(tile);
+    case 2: return pml ? group_smem_one<2, true>(tile) : group_smem_one<2, false>(tile);
+    case 3: return pml ? group_smem_one<3, true>(tile) : group_smem_one<3, false>(tile);
+    case 4: return pml ? group_smem_one<4, true>(tile) : group_smem_one<4, false>(tile);
+    case 5: return pml ? group_smem_one<5, true>(tile) : group_smem_one<5, false>(tile);
     default: return 0;
   }
 }
 
-size_t group_smem_bytes(int N, bool pml, int tile, int threads) {
-  return threads == 512 ? group_smem_nt<512>(N, pml, tile) : group_smem_nt<256>(N, pml, tile);
-}
-
-template <int NT>
-int group_tile_nt(int N, bool pml) {
+int group_tile_max(int N, bool pml) {
   switch (N) {
-    case 1: return pml ? Tile<float, 1, true, NT>::T : Tile<float, 1, false, NT>::T;
-    case 2: return pml ? Tile<float, 2, true, NT>::T : Tile<float, 2, false, NT>::T;
-    case 3: return pml ? Tile<float, 3, true, NT>::T : Tile<float, 3, false, NT>::T;
-    case 4: return pml ? Tile<float, 4, true, NT>::T : Tile<float, 4, false, NT>::T;
-    case 5: return pml ? Tile<float, 5, true, NT>::T : Tile<float, 5, false, NT>::T;
+    case 1: return pml ? GTile<1, true>::T : GTile<1, false>::T;
+    case 2: return pml ? GTile<2, true>::T : GTile<2, false>::T;
+    case 3: return pml ? GTile<3, true>::T : GTile<3, false>::T;
+    case 4: return pml ? GTile<4, true>::T : GTile<4, false>::T;
+    case 5: return pml ? GTile<5, true>::T : GTile<5, false>::T;
     default: return 0;
   }
 }
 
-int group_tile_max(int N, bool pml, int threads) {
-  return threads == 512 ? group_tile_nt<512>(N, pml) : group_tile_nt<256>(N, pml);
-}
-
-template <int NT>
-__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) group_stage_kernel(const GroupParams G) {
+// every block starts on the item of the variant that the static split gives
+// it, takes that item's tiles from its counter, then moves on to the
+// variant's items that still have tiles
+template <int N, bool PML, bool KAPPA>
+__global__ void __launch_bounds__(GTile<N, PML>::THREADS) group_stage_kernel(const GroupParams G) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ StageParams<float> P;
   __shared__ int start;
@@ -73,51 +72,67 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) group_stage_kernel(cons
     }
     __syncthreads();
     if (!go) continue;
-    int* dyn = G.counter + it;
-#define WADG_GROUP_CASE(NN)                                                               \
-  case NN * 4 + 0: stage_body<float, NN, false, false, false, NT>(P, smem_raw, 0, 1, dyn); break; \
-  case NN * 4 + 1: stage_body<float, NN, true, false, false, NT>(P, smem_raw, 0, 1, dyn); break;  \
-  case NN * 4 + 2: stage_body<float, NN, true, true, false, NT>(P, smem_raw, 0, 1, dyn); break;
-    switch (G.code[it]) {
-      WADG_GROUP_CASE(1)
-      WADG_GROUP_CASE(2)
-      WADG_GROUP_CASE(3)
-      WADG_GROUP_CASE(4)
-      WADG_GROUP_CASE(5)
-      default: break;
-    }
-#undef WADG_GROUP_CASE
+    stage_body<float, N, PML, KAPPA, false, 0>(P, smem_raw, 0, 1, G.counter + it);
   }
 }
 
-cudaError_t configure_group_kernel() {
-  size_t m256 = 0, m512 = 0;
-  for (int N = 1; N <= 5; ++N)
-    for (int pml = 0; pml < 2; ++pml) {
-      m256 = std::max(m256, group_smem_bytes(N, pml != 0, 0, 256));
-      m512 = std::max(m512, group_smem_bytes(N, pml != 0, 0, 512));
-    }
-  cudaError_t e = cudaFuncSetAttribute(group_stage_kernel<256>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m256);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(group_stage_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)m512);
+// variant code = N * 4 + (0 non-PML, 1 PML, 2 PML with kappa); f receives
+// the kernel and its threads per block
+template <typename F>
+cudaError_t with_variant(int code, F&& f) {
+#define WADG_GROUP_CASE(NN)                                                             \
+  case NN * 4 + 0: return f(group_stage_kernel<NN, false, false>, GTile<NN, false>::THREADS); \
+  case NN * 4 + 1: return f(group_stage_kernel<NN, true, false>, GTile<NN, true>::THREADS);   \
+  case NN * 4 + 2: return f(group_stage_kernel<NN, true, true>, GTile<NN, true>::THREADS);
+  switch (code) {
+    WADG_GROUP_CASE(1)
+    WADG_GROUP_CASE(2)
+    WADG_GROUP_CASE(3)
+    WADG_GROUP_CASE(4)
+    WADG_GROUP_CASE(5)
+    default: return cudaErrorInvalidValue;
+  }
+#undef WADG_GROUP_CASE
 }
 
-int group_blocks_per_sm(size_t smem, int threads) {
+cudaError_t configure_group_kernel() {
+  for (int N = 1; N <= 5; ++N)
+    for (int v = 0; v < 3; ++v) {
+      const size_t smem = group_smem_bytes(N, v > 0, 0);
+      cudaError_t e = with_variant(N * 4 + v, [&](auto k, int) {
+        return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      });
+      if (e != cudaSuccess) return e;
+    }
+  return cudaSuccess;
+}
+
+int group_threads(int code) {
+  int t = 0;
+  with_variant(code, [&](auto, int threads) {
+    t = threads;
+    return cudaSuccess;
+  });
+  return t;
+}
+
+int group_blocks_per_sm(int code, size_t smem) {
   int nb = 0;
-  cudaError_t e = threads == 512
-      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, group_stage_kernel<512>, 512, smem)
-      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, group_stage_kernel<256>, 256, smem);
+  cudaError_t e = with_variant(code, [&](auto k, int threads) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, smem);
+  });
   if (e != cudaSuccess || nb < 1) nb = 1;
   return nb;
 }
 
-cudaError_t launch_group_stage(const GroupParams& G, int nblocks, size_t smem, int threads,
+cudaError_t launch_group_stage(int code, const GroupParams& G, int nblocks, size_t smem,
                                cudaStream_t s) {
-  if (nblocks <= 0) return cudaSuccess;
-  if (threads == 512) group_stage_kernel<512><<<nblocks, 512, smem, s>>>(G);
-  else group_stage_kernel<256><<<nblocks, 256, smem, s>>>(G);
+  if (nblocks <= 0 || G.nitems <= 0) return cudaSuccess;
+  cudaError_t e = with_variant(code, [&](auto k, int threads) {
+    k<<<nblocks, threads, smem, s>>>(G);
+    return cudaSuccess;
+  });
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

@@ -65,6 +65,7 @@ struct StageParams {
   Real* resq;
   Real* p;
   Real* resp;
+  Real* pout;               // P after the stage (null: in place over p; CUDA-core kernels)
   const double* geo;
   const float* geof;        // [e][9]: the metric in float (tensor-core contexts)
   const Real* fnrm;         // [e][4][4]: unit outward normal, Fscale (from FP64)
@@ -110,11 +111,13 @@ struct AdjParams {
   double* grad_eps;         // [b][K] internal order
   double* grad_prof;        // [b][6]: d/dsigma_max[3], d/dp_sigma[3]
   const double* geo;
+  const Real* fnrm;         // [e][4][4]: unit outward normal, Fscale (as the forward stage)
   const Real* mat;
   const int* nbr;
   const unsigned char* code;
   const Real* sig;
   const Real* ops;
+  const Real* adj_ops;      // Dr, Ds, Dt [Np][NpP], LIFT [Np][NFP], P_q [Np][NqP], V_q [Nq][NpP]
   const unsigned char* tabs;
   int64_t strideQ, strideP;
   int K, K0, e_begin, n_elem;
@@ -123,6 +126,9 @@ struct AdjParams {
   const Real* src_w;
   double rk_a, rk_b, dt, t, eps0, alpha;
   double sigma_max[3], p_sigma[3];
+  Real inv_sigma_max[3], inv_p_sigma[3];   // 1 / sigma_max, 1 / p_sigma (0 where unset)
+  // the same scalars rounded once on the host (no per-thread conversion)
+  Real rk_a_r, rk_b_r, dt_r, alpha_r, inv_eps0_r;
 };
 
 struct ProbeParams {
@@ -184,21 +190,23 @@ cudaError_t launch_stored_ops(int N, int K1, int K0, const double* verts, const 
 // [first[i], first[i+1]) start on item i, and every block takes tiles from
 // counter[i] (zeroed before the launch) until all ntiles[i] are taken, then
 // moves on to the next item with tiles left
+// the items of one variant (order, element class) of a group
 struct GroupParams {
   const StageParams<float>* p;   // [nitems], device memory
-  const int* first;              // [nitems + 1], device memory
-  const int* code;               // [nitems], device memory
+  const int* first;              // [nitems + 1] static block split, device memory
   const int* ntiles;             // [nitems], device memory
   int* counter;                  // [nitems], device memory
   int nitems;
 };
 cudaError_t configure_group_kernel();
-// dynamic shared memory and largest tile (elements) of one item, blocks per
-// SM, launch; threads per block 256 or 512
-size_t group_smem_bytes(int N, bool pml, int tile, int threads);
-int group_tile_max(int N, bool pml, int threads);
-int group_blocks_per_sm(size_t smem, int threads);
-cudaError_t launch_group_stage(const GroupParams& G, int nblocks, size_t smem, int threads,
+// dynamic shared memory and largest tile (elements) of one item; threads per
+// block, blocks per SM and launch of the kernel of variant code = N * 4 +
+// (0 non-PML, 1 PML, 2 PML with kappa)
+size_t group_smem_bytes(int N, bool pml, int tile);
+int group_tile_max(int N, bool pml);
+int group_threads(int code);
+int group_blocks_per_sm(int code, size_t smem);
+cudaError_t launch_group_stage(int code, const GroupParams& G, int nblocks, size_t smem,
                                cudaStream_t s);
 template <typename Real>
 cudaError_t launch_check_finite(const Real* a, int64_t n, int* flag, cudaStream_t s);

@@ -161,15 +161,24 @@ __device__ __forceinline__ void stage_body(const StageParams<Real>& P, unsigned 
   const int tiles_per_batch = (P.n_elem + TE - 1) / TE;
   const int ntiles = tiles_per_batch * P.nb;
 
+  // dynamic schedule: thread 0 claims the next tile at the start of the
+  // current one and publishes it at the end, so the atomic's round trip
+  // overlaps the tile's work (a claim past the last tile is left unused)
   __shared__ int dyn_tile;
+  int claimed = 0;
+  auto claim = [&]() {
+    if (dyn && tid == 0) claimed = atomicAdd(dyn, 1);
+  };
   auto next_tile = [&](int cur) -> int {
     if (!dyn) return cur < 0 ? bid : cur + nblk;
     __syncthreads();   // every thread has read the previous value
-    if (tid == 0) dyn_tile = atomicAdd(dyn, 1);
+    if (tid == 0) dyn_tile = claimed;
     __syncthreads();
     return dyn_tile;
   };
+  claim();
   for (int tile = next_tile(-1); tile < ntiles; tile = next_tile(tile)) {
+  claim();
   const int b = tile / tiles_per_batch;
   const int t0 = (tile - b * tiles_per_batch) * TE;
   const int ne = min(TE, P.n_elem - t0);
@@ -179,6 +188,7 @@ __device__ __forceinline__ void stage_body(const StageParams<Real>& P, unsigned 
   Real* qout = P.qout + (int64_t)b * P.strideQ;
   Real* resq = P.resq + (int64_t)b * P.strideQ;
   Real* pio = P.p + (int64_t)b * P.strideP;
+  Real* pout = (P.pout ? P.pout : P.p) + (int64_t)b * P.strideP;   // read in phase 0, written last
   Real* resp = P.resp + (int64_t)b * P.strideP;
   __syncthreads();   // previous tile done with the shared buffers
 
@@ -423,7 +433,7 @@ __device__ __forceinline__ void stage_body(const StageParams<Real>& P, unsigned 
         const int64_t pi = ((int64_t)(eg - P.K0) * 6 + 3 * h + u) * Np + i;
         const Real rr = rka * resp[pi] + rdt * rhs[2 + h];
         resp[pi] = rr;
-        pio[pi] = Fi[6 + 3 * h + u] + rkb * rr;
+        pout[pi] = Fi[6 + 3 * h + u] + rkb * rr;
       }
     }
   }
@@ -533,7 +543,7 @@ __device__ __forceinline__ void stage_body(const StageParams<Real>& P, unsigned 
           const int64_t pi = ((int64_t)(eg - P.K0) * 6 + c - 6) * Np + i;
           const Real rr = rka * resp[pi] + rdt * s[cc][n];
           resp[pi] = rr;
-          pio[pi] = F[(e * Np + i) * 12 + c] + rkb * rr;
+          pout[pi] = F[(e * Np + i) * 12 + c] + rkb * rr;
         }
       }
     }

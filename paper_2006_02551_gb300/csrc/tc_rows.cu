@@ -1,6 +1,10 @@
-// Tensor-core stage kernels with row-owned epilogues (sm_103a: tcgen05 with
-// TF32 or BF16 operands, FP32 accumulation in tensor memory, FP32 state),
-// for contexts with a compact volume rule (quad_capacity class 1).
+// Tensor-core stage kernel with row-owned epilogues (sm_103a: tcgen05 with
+// TF32 or BF16 operands, FP32 accumulation in tensor memory, FP32 state) for
+// the PML class of contexts with a compact volume rule (quad_capacity class
+// 1).  The kernel is written for both element classes (PML = false drops the
+// P rows, V_q, P_q and eq. 9), but only the PML class is built: at N = 4 the
+// non-PML instantiation took 0.376 ms per launch (TF32) against 0.342 ms for
+// the non-PML class of tc_stage_kernel, which keeps that class.
 //
 // Every contraction of the stage is one product
 //     D[row][n] = sum_k A[row][k] * B[n][k]
@@ -955,7 +959,7 @@ cudaError_t rows_launch(const StageParams<float>& P, int nb, cudaStream_t s) {
 }  // namespace tc
 
 template <bool BF>
-cudaError_t configure_rows_bf(int N) {
+cudaError_t configure_rows(int N) {
   switch (N) {
     case 1: return tc::rows_configure<1, true, BF>();
     case 2: return tc::rows_configure<2, true, BF>();
@@ -967,11 +971,11 @@ cudaError_t configure_rows_bf(int N) {
 }
 
 cudaError_t configure_tc_rows(int N, bool bf16) {
-  return bf16 ? configure_rows_bf<true>(N) : configure_rows_bf<false>(N);
+  return bf16 ? configure_rows<true>(N) : configure_rows<false>(N);
 }
 
 template <bool BF>
-cudaError_t launch_rows_bf(int N, const StageParams<float>& P, int nb, cudaStream_t s) {
+cudaError_t launch_rows(int N, const StageParams<float>& P, int nb, cudaStream_t s) {
   switch (N) {
     case 1: return tc::rows_launch<1, true, BF>(P, nb, s);
     case 2: return tc::rows_launch<2, true, BF>(P, nb, s);
@@ -984,11 +988,16 @@ cudaError_t launch_rows_bf(int N, const StageParams<float>& P, int nb, cudaStrea
 
 cudaError_t launch_pml_tc_rows(int N, const StageParams<float>& P, int nb, cudaStream_t s,
                                bool bf16) {
-  const uintptr_t a = reinterpret_cast<uintptr_t>(P.qin) | reinterpret_cast<uintptr_t>(P.qout) |
-                      reinterpret_cast<uintptr_t>(P.resq) | reinterpret_cast<uintptr_t>(P.p) |
-                      reinterpret_cast<uintptr_t>(P.resp) | reinterpret_cast<uintptr_t>(P.sig);
+  // the bulk copies move whole 16-byte covers of each block: the arrays must
+  // start on 16-byte boundaries (cudaMalloc gives 256)
+  const uintptr_t a =
+      reinterpret_cast<uintptr_t>(P.qin) | reinterpret_cast<uintptr_t>(P.qout) |
+      reinterpret_cast<uintptr_t>(P.resq) | reinterpret_cast<uintptr_t>(P.p) |
+      reinterpret_cast<uintptr_t>(P.resp) | reinterpret_cast<uintptr_t>(P.sig) |
+      reinterpret_cast<uintptr_t>(P.fnrm) | reinterpret_cast<uintptr_t>(P.geof) |
+      reinterpret_cast<uintptr_t>(P.mat);
   if (a & 15) return cudaErrorMisalignedAddress;
-  return bf16 ? launch_rows_bf<true>(N, P, nb, s) : launch_rows_bf<false>(N, P, nb, s);
+  return bf16 ? launch_rows<true>(N, P, nb, s) : launch_rows<false>(N, P, nb, s);
 }
 
 }  // namespace wadg

@@ -78,8 +78,7 @@ _SIG = {
     "wadg_group_create": [C.c_int32, C.POINTER(_P), C.POINTER(_P)],
     "wadg_group_destroy": [_P],
     "wadg_group_autotune": [_P, _D, C.c_int32, _D],
-    "wadg_group_info": [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
-                        C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
+    "wadg_group_info": [_P] + [C.POINTER(C.c_int32)] * 8,
     "wadg_group_run_steps": [_P, C.c_int64, _D, C.POINTER(_D)],
 }
 
@@ -362,8 +361,10 @@ class Solver:
 
 
 class Group:
-    """Several FP32 solvers advanced together, one grouped launch per stage
-    (wadg_group_*).  Refers to the solvers: close it before them."""
+    """Several FP32 solvers advanced together: per stage one grouped launch
+    per (order, element class) variant present, the launches of a stage on
+    parallel graph branches (wadg_group_*).  Refers to the solvers: close it
+    before them."""
 
     def __init__(self, solvers):
         self.lib = load()
@@ -399,10 +400,11 @@ class Group:
         return ms.value
 
     def info(self):
-        v = [C.c_int32() for _ in range(5)]
+        v = [C.c_int32() for _ in range(8)]
         self._c(self.lib.wadg_group_info(self.g, *[C.byref(x) for x in v]))
         return dict(blocks=v[0].value, threads=v[1].value, blocks_per_sm=v[2].value,
-                    tile_divisor=v[3].value, items=v[4].value)
+                    tile_divisor=v[3].value, items=v[4].value, variants=v[5].value,
+                    parallel=bool(v[6].value), share=bool(v[7].value))
 
     def run_steps(self, nsteps, dts, record=True):
         d = np.ascontiguousarray(dts, np.float64)

@@ -51,11 +51,11 @@ def test_adjoint_matches_oracle(case, prec, tol):
     s = gpu_solver(v, e, eps, prec)
     Jg, ge, gs, gp = s.adjoint(NSTEPS, dt, ckpt_every=7)
     s.close()
-    assert abs(Jg[0] - J) < tol * abs(J)
-    assert np.linalg.norm(ge[0] - gE) < tol * np.linalg.norm(gE), (ge[0][:5], gE[:5])
     # the three axes share sigma_max and p_sigma in the oracle
-    assert abs(gs[0].sum() - gS) < tol * abs(gS) + 1e-12
-    assert abs(gp[0].sum() - gP) < tol * abs(gP) + 1e-12
+    errs = (abs(Jg[0] - J) / abs(J), np.linalg.norm(ge[0] - gE) / np.linalg.norm(gE),
+            abs(gs[0].sum() - gS) / abs(gS), abs(gp[0].sum() - gP) / abs(gP))
+    print(f"{prec} adjoint vs oracle (J, eps, sigma_max, p_sigma):", ["%.2e" % x for x in errs])
+    assert max(errs) < tol, errs
 
 
 def test_checkpoint_spacing_does_not_change_gradient(case):
@@ -72,13 +72,16 @@ def test_checkpoint_spacing_does_not_change_gradient(case):
 
 
 def test_adjoint_matches_central_differences_of_gpu_forward(case):
+    """20 random directions in (eps_r, sigma_max, p_sigma): the adjoint's
+    directional derivative against the central difference (h = 1e-4) of the
+    GPU forward objective; sigma_max and p_sigma move all three axes."""
     v, e, eps, dt, _ = case
     s = gpu_solver(v, e, eps, "fp64")
     J, ge, gs, gp = s.adjoint(NSTEPS, dt, ckpt_every=5)
 
-    def Jf(eps_):
+    def Jf(eps_, sm, ps):
         s.set_materials(eps_)
-        s.set_pml(PROF)
+        s.set_pml(PmlProfile(u0=PROF.u0, L=PROF.L, sigma_max=sm, p_sigma=ps))
         s.set_sources(SRC)
         s.set_probes(PROBES)
         s.set_state(None, 0.0)
@@ -87,10 +90,16 @@ def test_adjoint_matches_central_differences_of_gpu_forward(case):
 
     rng = np.random.default_rng(11)
     h = 1e-4
-    for _ in range(5):
+    worst = 0.0
+    for _ in range(20):
         d = rng.normal(size=eps.size)
-        fd = (Jf(eps + h * d) - Jf(eps - h * d)) / (2 * h)
-        assert abs(fd - ge[0] @ d) < 1e-6 * abs(fd)
+        dsm, dps = rng.normal(size=2)
+        fd = (Jf(eps + h * d, PROF.sigma_max + h * dsm, PROF.p_sigma + h * dps) -
+              Jf(eps - h * d, PROF.sigma_max - h * dsm, PROF.p_sigma - h * dps)) / (2 * h)
+        ad = ge[0] @ d + gs[0].sum() * dsm + gp[0].sum() * dps
+        worst = max(worst, abs(fd - ad) / abs(fd))
+    print(f"adjoint vs central differences, 20 directions: worst relative error {worst:.2e}")
+    assert worst < 1e-6
     s.close()
 
 

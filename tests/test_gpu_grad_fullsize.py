@@ -7,11 +7,14 @@ signal at the probes inside the shortened windows (J is then of order one
 instead of 1e-35).  The 2000-step FP32 gradient is timed by bench.py.
 
 * The FP32 adjoint (checkpoints every 45 steps) against the FP64 adjoint over
-  the same 250 steps: dJ/deps_r, dJ/dsigma_max and dJ/dp_sigma agree to 1e-3
-  (relative L2; the FP64 adjoint itself matches the oracle's reverse-mode
-  derivative to 1e-10 in tests/test_gpu_adjoint.py).
+  the same 250 steps: J, dJ/deps_r, dJ/dsigma_max and dJ/dp_sigma agree to
+  1e-5 (relative L2; measured 2e-6 to 4e-6; the FP64 adjoint itself matches
+  the oracle's reverse-mode derivative to 1e-10 in tests/test_gpu_adjoint.py).
 * The FP64 adjoint against central differences (h = 1e-4) of the FP64 forward
-  along 3 random directions of eps_r, 250 steps: relative error 1e-6.
+  along 3 random directions of eps_r, 250 steps: relative error 1e-6.  (In
+  250 steps no wave reaches the PML and returns to the probes, so J does not
+  depend on sigma_max or p_sigma here; tests/test_gpu_adjoint.py checks those
+  derivatives along 20 random directions on a case where they matter.)
 """
 import numpy as np
 import pytest
@@ -69,7 +72,7 @@ def test_fp32_adjoint_matches_fp64_at_full_size(setup):
     errs = (abs(J32[0] - J64[0]) / J64[0], rel(ge32, ge64), rel(gs32, gs64), rel(gp32, gp64))
     print(f"J = {J64[0]:.4e}; FP32 vs FP64 adjoint (J, eps, sigma_max, p_sigma):",
           ["%.2e" % x for x in errs])
-    assert max(errs) < 1e-3, errs
+    assert max(errs) < 1e-5, errs
 
 
 def test_fp64_adjoint_matches_central_differences_at_full_size(setup):
@@ -97,3 +100,4 @@ def test_fp64_adjoint_matches_central_differences_at_full_size(setup):
         print(f"directional derivative: adjoint {ge[0] @ d:.10e}  central difference {fd:.10e}")
         assert abs(fd - ge[0] @ d) < 1e-6 * abs(fd)
     s.close()
+
