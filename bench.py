@@ -39,8 +39,9 @@ import numpy as np  # noqa: E402
 # one ncu capture of the small case of the benchmark recipe, valid only for
 # the kernel source it was taken on (sha256 of that source file): None until
 # a capture of the current source is recorded here
-TC_PML_TRAFFIC = {"file": "tc_rows.cu", "sha256": None, "N": 4,
-                  "bytes_per_pml_element": {}}
+TC_PML_TRAFFIC = {"file": "tc_rows.cu",
+                  "sha256": "f9bc0e087ce7fe4560678acd91da5064ad9b9ef97dc9a3e8eb0e37f428c160a3",
+                  "N": 4, "bytes_per_pml_element": {"tf32": 6352.0, "bf16": 6355.0}}
 
 
 def tc_pml_traffic(K1, N, precision):
@@ -647,12 +648,14 @@ def main():
     achieved_gbs = d_bytes / (d_ms * 1e-3) / 1e9
     if args.precision in ("tf32", "bf16"):
         # tensor-core contractions: the stage is bound by HBM traffic
-        traffic = tc_pml_traffic(K1 * w.n_batch, N, args.precision) if dom == "pml" else None
+        traffic = (tc_pml_traffic(K1 * w.n_batch, N, args.precision)
+                   if dom == "pml" and rows else None)
         kname = "tc_rows_kernel" if (rows and dom == "pml") else "tc_stage_kernel"
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
                     "frac": achieved_gbs / hbm, "traffic": traffic,
-                    "traffic_note": "ncu DRAM bytes per PML element of the small case, scaled "
-                                    "by elements (null when the kernel source has changed since)",
+                    "traffic_note": "ncu DRAM bytes per PML element of the 24^3 case (mean "
+                                    "of two launches), scaled by the PML elements of this "
+                                    "launch; null when the kernel source has changed since",
                     "kernel": f"{kname}<{dom}>",
                     "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                     "alu": {"achieved_tflops": achieved}}

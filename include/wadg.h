@@ -402,30 +402,46 @@ wadg_status wadg_group_create(int32_t n, wadg_ctx* const* ctxs, wadg_group** out
 wadg_status wadg_group_destroy(wadg_group* g);
 
 /* Tile sizes and grid: times `reps` grouped stage launches for every
- * candidate (elements per tile = the largest that fits / {1, 2, 4}; 1..4
- * blocks per SM within each variant's occupancy limit; a stage's variant
- * launches on parallel branches or one after the other; each variant's grid
- * the whole GPU or its share by algorithmic flops; each variant keeps the
- * block shape of its single-context kernel) with
+ * candidate (grouped variant kernels, or every (member, class) item launched
+ * as its single-context kernel; elements per tile = the largest that fits /
+ * {1, 2, 4}; 1..4 blocks per SM within each variant's occupancy limit; a
+ * stage's launches on parallel branches or one after the other; each
+ * variant's grid the whole GPU or its share by algorithmic flops; each
+ * variant keeps the block shape of its single-context kernel) with
  * the members' step sizes
  * dt[n], keeps the fastest and writes its time per stage launch (ms) to
  * ms_out (may be NULL).  The stages run on the members' current state, which
  * is left undefined: call it before wadg_set_state. */
 wadg_status wadg_group_autotune(wadg_group* g, const double* dt, int32_t reps, double* ms_out);
 
+/* Set the launch shape without timing (the values wadg_group_autotune
+ * chooses among): per_item (1: every item as its single-context kernel),
+ * parallel (1: a stage's launches on parallel branches), share (1: each
+ * variant's grid its share of the GPU), tile_divisor (1..64), blocks_per_sm
+ * (1..8, capped by each variant's occupancy).  EINVAL out of range. */
+wadg_status wadg_group_set_tuning(wadg_group* g, int32_t per_item, int32_t parallel,
+                                  int32_t share, int32_t tile_divisor, int32_t blocks_per_sm);
+
 /* The current launch shape: total blocks (all variants), threads per block
  * of the heaviest variant, blocks per SM (each variant is capped by its own
  * occupancy), tile divisor, work items, variants (launches per stage),
  * whether a stage's variant launches run on parallel branches (1) or in turn
  * (0), and whether each variant's grid is its share of the GPU (1) or the
- * whole GPU (0).  Any pointer may be NULL. */
+ * whole GPU (0), the number of L2 clusters of the last wadg_group_run_steps (1: all
+ * members advanced together), and whether each item is launched as its
+ * single-context kernel (1) instead of the grouped variant kernels (0).  Any
+ * pointer may be NULL. */
 wadg_status wadg_group_info(const wadg_group* g, int32_t* nblocks, int32_t* threads,
                             int32_t* blocks_per_sm, int32_t* tile_divisor, int32_t* nitems,
-                            int32_t* nvariants, int32_t* parallel, int32_t* share);
+                            int32_t* nvariants, int32_t* parallel, int32_t* share,
+                            int32_t* nclusters, int32_t* per_item);
 
 /* nsteps steps of every member with its own dt[n]; probe_out[n] (entries may
  * be NULL, or probe_out itself) receive each member's records laid out as in
- * wadg_run_steps.  Gives each member the values wadg_run_steps would. */
+ * wadg_run_steps.  Gives each member the values wadg_run_steps would.  The
+ * members are packed into clusters whose per-step device data fits half of
+ * the L2 (members above that form one cluster); each cluster runs all nsteps
+ * before the next, so small members step out of L2. */
 wadg_status wadg_group_run_steps(wadg_group* g, int64_t nsteps, const double* dt,
                                  double* const* probe_out);
 

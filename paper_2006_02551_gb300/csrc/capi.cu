@@ -132,6 +132,7 @@ struct wadg_ctx {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   double graph_dt = 0.0;
   bool graph_valid = false;
+  uint64_t gen = 0;   // advanced whenever the graphs are invalidated (every set-up change)
 };
 
 namespace {
@@ -190,6 +191,7 @@ void invalidate_graphs(wadg_ctx* c) {
   for (auto& g : c->graph)
     if (g) { cudaGraphExecDestroy(g); g = nullptr; }
   c->graph_valid = false;
+  ++c->gen;
 }
 
 // barycentric coordinates of x in user element k (lambda[4])
@@ -1926,7 +1928,9 @@ struct wadg_group {
   int sms = 1;
   int blocks_per_sm = 1;   // autotuned
   int tile_div = 1;        // autotuned: tile = largest tile / tile_div
-  bool parallel = true;    // autotuned: a stage's variant launches on parallel branches
+  bool per_item = false;   // autotuned: each (member, class) item launched as its
+                           // single-context kernel (else one grouped kernel per variant)
+  bool parallel = true;    // autotuned: a stage's launches on parallel branches
   bool share = false;      // autotuned: a variant's grid is its share of the GPU (by
                            // algorithmic flops) instead of the whole GPU
   int nblocks = 0;         // all variants
@@ -1938,11 +1942,26 @@ struct wadg_group {
   std::vector<Variant> vars;
   std::vector<int> first;
   DevPtr dparams, dfirst;          // params [2 parities][5 stages][items]
+  std::vector<StageParams<float>> hparams;   // the same on the host (per-item launches)
   DevPtr dntiles, dcounter;        // tiles per item, tile counters (zeroed per launch)
   // streams and events of the parallel branches (variant v > 0 on aux[v - 1])
   std::vector<cudaStream_t> aux;
   std::vector<cudaEvent_t> ev;     // ev[0] fork, ev[v] join of variant v
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  // what the graphs were built for: each member's generation, step size and
+  // buffer parity (a later call with the same generations and steps reuses
+  // them from the matching parity)
+  std::vector<uint64_t> built_gen;
+  std::vector<double> built_dt;
+  std::vector<int> built_cur;
+  // L2 clusters: the members packed so that each cluster's per-step data fits
+  // half of the L2, each cluster advanced through all the steps of a call
+  // before the next (members are independent, so only the order in time
+  // changes: a small member's state then stays in L2 from step to step);
+  // members larger than that form one cluster.  Empty when one cluster would
+  // hold every member.
+  std::vector<std::vector<int>> cluster_of;
+  std::vector<wadg_group*> clusters;
 };
 
 namespace {
@@ -1980,6 +1999,7 @@ wadg_status group_members_ready(wadg_group* g) {
 void group_drop_graphs(wadg_group* g) {
   for (auto& x : g->graph)
     if (x) { cudaGraphExecDestroy(x); x = nullptr; }
+  g->built_gen.clear();
 }
 
 // per-element flops of a stage (the algorithmic count used by the benchmark),
@@ -2059,18 +2079,62 @@ void group_plan(wadg_group* g) {
 
 // the streams and events of the parallel branches
 wadg_status group_branches(wadg_group* g) {
-  while (g->aux.size() + 1 < g->vars.size()) {
+  const size_t want = std::max(g->vars.size(), std::min<size_t>(g->items.size(), 8));
+  while (g->aux.size() + 1 < want) {
     cudaStream_t st;
     GCK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
     g->aux.push_back(st);
   }
-  while (g->ev.size() < std::max<size_t>(1, g->vars.size())) {
+  while (g->ev.size() < std::max<size_t>(1, want)) {
     cudaEvent_t e;
     GCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     g->ev.push_back(e);
   }
   return WADG_OK;
 }
+
+// device bytes a member reads or writes in a step
+size_t member_step_bytes(const wadg_ctx* x) {
+  return 2 * x->q[0].bytes + x->rq.bytes + x->p.bytes + x->rp.bytes + x->sig.bytes + x->kap.bytes +
+         x->geo.bytes + x->fnrm.bytes + x->mat.bytes + x->nbr.bytes + x->code.bytes;
+}
+
+// members packed into clusters of at most half the L2 (smallest first);
+// members above that go together into a last cluster
+std::vector<std::vector<int>> group_clusters(const wadg_group* g) {
+  int l2 = 0;
+  cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, g->device);
+  const size_t budget = (size_t)std::max(l2, 0) / 2;
+  std::vector<int> order(g->ctx.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return member_step_bytes(g->ctx[a]) < member_step_bytes(g->ctx[b]);
+  });
+  std::vector<std::vector<int>> cl;
+  std::vector<int> open, large;
+  size_t used = 0;
+  for (int m : order) {
+    const size_t b = member_step_bytes(g->ctx[m]);
+    if (b > budget) {
+      large.push_back(m);
+      continue;
+    }
+    if (used + b > budget && !open.empty()) {
+      cl.push_back(open);
+      open.clear();
+      used = 0;
+    }
+    open.push_back(m);
+    used += b;
+  }
+  if (!open.empty()) cl.push_back(open);
+  if (!large.empty()) cl.push_back(large);
+  if (cl.size() <= 1) cl.clear();
+  for (auto& c : cl) std::sort(c.begin(), c.end());
+  return cl;
+}
+
+void group_drop_clusters(wadg_group* g);
 
 // stage parameters of every item for both step parities and all 5 stages
 wadg_status group_upload(wadg_group* g, const double* dt) {
@@ -2091,6 +2155,7 @@ wadg_status group_upload(wadg_group* g, const double* dt) {
         hp[((size_t)par * 5 + st) * ni + i] = P;
         x->cur = cur0[it.c];
       }
+  g->hparams = hp;
   std::vector<int> ntiles(ni);
   for (int i = 0; i < ni; ++i) ntiles[i] = (int)g->items[i].tiles;
   GCK(dalloc(g->dntiles, ntiles.size() * sizeof(int)));
@@ -2115,10 +2180,39 @@ GroupParams group_params(wadg_group* g, const wadg_group::Variant& v, int par, i
   return G;
 }
 
+// one stage with per-item launches: every (member, class) item as its
+// single-context kernel with its own parameters, spread over up to 8
+// parallel branches (or all on the group's stream)
+cudaError_t group_launch_items(wadg_group* g, int par, int st) {
+  const size_t ni = g->items.size();
+  const size_t nbr = g->parallel ? std::min<size_t>(ni, g->aux.size() + 1) : 1;
+  cudaError_t e = cudaSuccess;
+  if (nbr > 1) {
+    if ((e = cudaEventRecord(g->ev[0], g->stream)) != cudaSuccess) return e;
+    for (size_t k = 1; k < nbr; ++k)
+      if ((e = cudaStreamWaitEvent(g->aux[k - 1], g->ev[0], 0)) != cudaSuccess) return e;
+  }
+  for (size_t i = 0; i < ni; ++i) {
+    const auto& it = g->items[i];
+    const wadg_ctx* x = g->ctx[it.c];
+    const size_t k = i % nbr;
+    cudaStream_t s = k == 0 ? g->stream : g->aux[k - 1];
+    const StageParams<float>& P = g->hparams[((size_t)par * 5 + st) * ni + i];
+    e = launch_stage<float>(x->N, it.pml, it.code % 4 == 2, P, x->nb, s, x->qc);
+    if (e != cudaSuccess) return e;
+  }
+  for (size_t k = 1; k < nbr; ++k) {
+    if ((e = cudaEventRecord(g->ev[k], g->aux[k - 1])) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(g->stream, g->ev[k], 0)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 // one grouped stage: clear the tile counters, then one launch per variant,
 // variant 0 on the group's stream and the others on parallel branches that
 // fork from it after the clear and join it before the next stage
 cudaError_t group_launch(wadg_group* g, int par, int st) {
+  if (g->per_item) return group_launch_items(g, par, st);
   cudaError_t e = cudaMemsetAsync(g->dcounter.p, 0, g->items.size() * sizeof(int), g->stream);
   if (e != cudaSuccess) return e;
   const size_t nv = g->vars.size();
@@ -2227,6 +2321,7 @@ wadg_status wadg_group_create(int32_t n, wadg_ctx* const* ctxs, wadg_group** out
 wadg_status wadg_group_destroy(wadg_group* g) {
   if (!g) return WADG_OK;
   cudaSetDevice(g->device);
+  group_drop_clusters(g);
   group_drop_graphs(g);
   dfree(g->dparams);
   dfree(g->dfirst);
@@ -2249,17 +2344,21 @@ wadg_status wadg_group_autotune(wadg_group* g, const double* dt, int32_t reps, d
   GCK(cudaEventCreate(&e1));
   double best = 1e300;
   int best_bps = 1, best_div = 1;
-  bool best_par = true, best_share = false;
+  bool best_par = true, best_share = false, best_item = false;
+  for (int item = 0; item < 2; ++item)
   for (int par = 1; par >= 0; --par)
-  for (int shr = 0; shr < 2; ++shr)
+  for (int shr = 0; shr < (item ? 1 : 2); ++shr)
   for (int div : {1, 2, 4}) {
+    g->per_item = item != 0;
     g->parallel = par != 0;
     g->share = shr != 0;
     g->tile_div = div;
     g->blocks_per_sm = 1;
     group_plan(g);
-    int occ = 1;   // the most blocks per SM any variant can hold
-    for (const auto& v : g->vars) occ = std::max(occ, group_blocks_per_sm(v.code, v.smem));
+    int occ = 1;   // the most blocks per SM any variant can hold (per-item: the
+                   // single-context launcher sizes its own grid)
+    if (!item)
+      for (const auto& v : g->vars) occ = std::max(occ, group_blocks_per_sm(v.code, v.smem));
     for (int bps = 1; bps <= std::min(occ, 4); ++bps) {
       g->blocks_per_sm = bps;
       group_plan(g);
@@ -2274,6 +2373,7 @@ wadg_status wadg_group_autotune(wadg_group* g, const double* dt, int32_t reps, d
       GCK(cudaEventElapsedTime(&ms, e0, e1));
       if (ms < best) {
         best = ms; best_bps = bps; best_div = div; best_par = g->parallel; best_share = g->share;
+        best_item = g->per_item;
       }
     }
   }
@@ -2283,15 +2383,34 @@ wadg_status wadg_group_autotune(wadg_group* g, const double* dt, int32_t reps, d
   g->tile_div = best_div;
   g->parallel = best_par;
   g->share = best_share;
+  g->per_item = best_item;
   group_plan(g);
   if (ms_out) *ms_out = best / reps;
   return WADG_OK;
 }
 
+wadg_status wadg_group_set_tuning(wadg_group* g, int32_t per_item, int32_t parallel,
+                                  int32_t share, int32_t tile_divisor, int32_t blocks_per_sm) {
+  if (!g) return WADG_EINVAL;
+  if (tile_divisor < 1 || tile_divisor > 64 || blocks_per_sm < 1 || blocks_per_sm > 8)
+    return gfail(g, WADG_EINVAL, "tile divisor must be 1..64 and blocks per SM 1..8");
+  group_drop_graphs(g);
+  g->per_item = per_item != 0;
+  g->parallel = parallel != 0;
+  g->share = share != 0;
+  g->tile_div = tile_divisor;
+  g->blocks_per_sm = blocks_per_sm;
+  group_plan(g);
+  return WADG_OK;
+}
+
 wadg_status wadg_group_info(const wadg_group* g, int32_t* nblocks, int32_t* threads,
                             int32_t* blocks_per_sm, int32_t* tile_divisor, int32_t* nitems,
-                            int32_t* nvariants, int32_t* parallel, int32_t* share) {
+                            int32_t* nvariants, int32_t* parallel, int32_t* share,
+                            int32_t* nclusters, int32_t* per_item) {
   if (!g) return WADG_EINVAL;
+  if (per_item) *per_item = g->per_item ? 1 : 0;
+  if (nclusters) *nclusters = (int32_t)std::max<size_t>(1, g->cluster_of.size());
   if (nvariants) *nvariants = (int32_t)g->vars.size();
   if (parallel) *parallel = g->parallel ? 1 : 0;
   if (share) *share = g->share ? 1 : 0;
@@ -2313,6 +2432,43 @@ wadg_status wadg_group_run_steps(wadg_group* g, int64_t nsteps, const double* dt
   if (nsteps == 0) return WADG_OK;
   if ((s0 = group_members_ready(g)) != WADG_OK) return s0;
   cudaSetDevice(g->device);
+  // L2 clusters, each a group of its own with this group's tuning
+  const auto cl = group_clusters(g);
+  if (cl != g->cluster_of) {
+    group_drop_clusters(g);
+    for (const auto& c : cl) {
+      std::vector<wadg_ctx*> m;
+      for (int i : c) m.push_back(g->ctx[i]);
+      wadg_group* sub = nullptr;
+      s0 = wadg_group_create((int32_t)m.size(), m.data(), &sub);
+      if (s0 != WADG_OK) {
+        group_drop_clusters(g);
+        return gfail(g, s0, "cluster set-up: %s", wadg_group_last_error(nullptr));
+      }
+      sub->stream = g->stream;
+      g->clusters.push_back(sub);
+    }
+    g->cluster_of = cl;
+  }
+  if (!g->clusters.empty()) {
+    for (size_t k = 0; k < g->clusters.size(); ++k) {
+      wadg_group* sub = g->clusters[k];
+      sub->tile_div = g->tile_div;
+      sub->blocks_per_sm = g->blocks_per_sm;
+      sub->parallel = g->parallel;
+      sub->share = g->share;
+      sub->per_item = g->per_item;
+      std::vector<double> d;
+      std::vector<double*> po;
+      for (int i : g->cluster_of[k]) {
+        d.push_back(dt[i]);
+        po.push_back(probe_out ? probe_out[i] : nullptr);
+      }
+      s0 = wadg_group_run_steps(sub, nsteps, d.data(), po.data());
+      if (s0 != WADG_OK) return gfail(g, s0, "%s", sub->err.c_str());
+    }
+    return WADG_OK;
+  }
   const int64_t chunk = std::min<int64_t>(nsteps, 4096);
   for (wadg_ctx* x : g->ctx) {
     const size_t need = (size_t)chunk * x->nprobe * 6 * x->nb * 8;
@@ -2322,15 +2478,32 @@ wadg_status wadg_group_run_steps(wadg_group* g, int64_t nsteps, const double* dt
       if (e != cudaSuccess) return gfail(g, WADG_ENOMEM, "probe records: %s", cudaGetErrorString(e));
     }
   }
-  // member buffers may have moved since the last call: rebuild the parameter
-  // tables and the graphs
-  group_plan(g);
-  wadg_status s = group_upload(g, dt);
-  if (s != WADG_OK) return s;
-  s = group_capture(g, dt);
-  if (s != WADG_OK) return s;
+  // the graphs of the last call still hold if no member changed since (same
+  // generation and step) and every member's buffer parity moved alike;
+  // otherwise rebuild the parameter tables and the graphs
+  bool reuse = g->graph[0] && g->graph[1] && g->built_gen.size() == g->ctx.size();
+  const int par0 = reuse ? (g->ctx[0]->cur ^ g->built_cur[0]) : 0;
+  for (size_t c = 0; reuse && c < g->ctx.size(); ++c) {
+    const wadg_ctx* x = g->ctx[c];
+    reuse = x->gen == g->built_gen[c] && dt[c] == g->built_dt[c] &&
+            (x->cur ^ g->built_cur[c]) == par0;
+  }
+  if (!reuse) {
+    group_plan(g);
+    wadg_status s = group_upload(g, dt);
+    if (s != WADG_OK) return s;
+    s = group_capture(g, dt);
+    if (s != WADG_OK) return s;
+    g->built_gen.clear();
+    g->built_dt.assign(dt, dt + g->ctx.size());
+    g->built_cur.clear();
+    for (const wadg_ctx* x : g->ctx) {
+      g->built_gen.push_back(x->gen);
+      g->built_cur.push_back(x->cur);
+    }
+  }
   int64_t done = 0;
-  int par = 0;
+  int par = reuse ? par0 : 0;
   while (done < nsteps) {
     const int64_t n = std::min(chunk, nsteps - done);
     for (size_t c = 0; c < g->ctx.size(); ++c) {
@@ -2366,3 +2539,13 @@ const char* wadg_group_last_error(const wadg_group* g) {
 }
 
 }  // extern "C"
+
+namespace {
+
+void group_drop_clusters(wadg_group* g) {
+  for (wadg_group* sub : g->clusters) wadg_group_destroy(sub);
+  g->clusters.clear();
+  g->cluster_of.clear();
+}
+
+}  // namespace

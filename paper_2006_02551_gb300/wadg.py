@@ -78,7 +78,8 @@ _SIG = {
     "wadg_group_create": [C.c_int32, C.POINTER(_P), C.POINTER(_P)],
     "wadg_group_destroy": [_P],
     "wadg_group_autotune": [_P, _D, C.c_int32, _D],
-    "wadg_group_info": [_P] + [C.POINTER(C.c_int32)] * 8,
+    "wadg_group_info": [_P] + [C.POINTER(C.c_int32)] * 10,
+    "wadg_group_set_tuning": [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32],
     "wadg_group_run_steps": [_P, C.c_int64, _D, C.POINTER(_D)],
 }
 
@@ -399,12 +400,19 @@ class Group:
         self._c(self.lib.wadg_group_autotune(self.g, _ptr(d), reps, C.byref(ms)))
         return ms.value
 
+    def set_tuning(self, per_item=False, parallel=True, share=False, tile_divisor=1,
+                   blocks_per_sm=1):
+        """Fix the launch shape without timing (see autotune)."""
+        self._c(self.lib.wadg_group_set_tuning(self.g, int(per_item), int(parallel), int(share),
+                                               tile_divisor, blocks_per_sm))
+
     def info(self):
-        v = [C.c_int32() for _ in range(8)]
+        v = [C.c_int32() for _ in range(10)]
         self._c(self.lib.wadg_group_info(self.g, *[C.byref(x) for x in v]))
         return dict(blocks=v[0].value, threads=v[1].value, blocks_per_sm=v[2].value,
                     tile_divisor=v[3].value, items=v[4].value, variants=v[5].value,
-                    parallel=bool(v[6].value), share=bool(v[7].value))
+                    parallel=bool(v[6].value), share=bool(v[7].value), clusters=v[8].value,
+                    per_item=bool(v[9].value))
 
     def run_steps(self, nsteps, dts, record=True):
         d = np.ascontiguousarray(dts, np.float64)

@@ -48,7 +48,7 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-@pytest.mark.parametrize("tune", [False, True])
+@pytest.mark.parametrize("tune", [False, True, "per_item", "per_item_serial"])
 def test_group_equals_single_runs(tune):
     from paper_2006_02551_gb300 import Group
     nsteps = 25
@@ -62,20 +62,25 @@ def test_group_equals_single_runs(tune):
         s.close()
     members = [make(*m) for m in MEMBERS]
     g = Group(members)
-    if tune:
+    if tune is True:
         g.autotune(dts, reps=10)
         for s in members:
             s.set_state(None, 0.0)   # the autotuner leaves the state undefined
+    elif tune:
+        g.set_tuning(per_item=True, parallel=tune == "per_item")
+        assert g.info()["per_item"]
     info = g.info()
     assert info["items"] == sum(2 if m[2] else 1 for m in MEMBERS)
-    # two calls, so the second starts from the other buffer parity
+    # three calls (10, 7, 8 steps): the second reuses the first's graphs from
+    # the same buffer parity, the third from the other one
     rec1 = g.run_steps(10, dts)
-    rec2 = g.run_steps(nsteps - 10, dts)
+    rec2 = g.run_steps(7, dts)
+    rec3 = g.run_steps(nsteps - 17, dts)
     for i, s in enumerate(members):
         q, t = s.get_state()
         qr, recr, tr = ref[i]
         assert abs(t - tr) < 1e-12
-        rec = np.concatenate([rec1[i], rec2[i]])
+        rec = np.concatenate([rec1[i], rec2[i], rec3[i]])
         assert np.array_equal(q, qr), (i, rel(q, qr), np.abs(q - qr).max())
         assert np.array_equal(rec, recr), (i, rel(rec, recr))
     g.close()
@@ -121,4 +126,34 @@ def test_small_mixed_group_matches_oracle():
         perr = rel(rec, rec_ref)
         assert err < 1e-5, err
         assert perr < 1e-5, perr
+        s.close()
+
+
+def test_l2_clusters_equal_single_runs():
+    """A member whose per-step data exceeds half the L2 (20^3 x 6 tets, N = 3,
+    PML) with three small ones: the group advances them in L2 clusters (the
+    small members together, the large one on its own), which changes only the
+    order in time, so every member still equals its own run_steps bit for
+    bit; a later call reuses the clusters."""
+    from paper_2006_02551_gb300 import Group
+    members_spec = [(3, 20, True, 1), (2, 3, True, 1), (3, 3, False, 2), (4, 2, True, 1)]
+    nsteps = 9
+    singles = [make(*m) for m in members_spec]
+    dts = [0.8 * s.stable_dt(1.0) for s in singles]
+    ref = []
+    for s, dt in zip(singles, dts):
+        rec = s.run_steps(nsteps, dt)
+        ref.append((s.get_state()[0], rec))
+        s.close()
+    members = [make(*m) for m in members_spec]
+    g = Group(members)
+    rec1 = g.run_steps(4, dts)
+    assert g.info()["clusters"] >= 2
+    rec2 = g.run_steps(nsteps - 4, dts)
+    for i, s in enumerate(members):
+        q, _ = s.get_state()
+        assert np.array_equal(q, ref[i][0]), (i, rel(q, ref[i][0]))
+        assert np.array_equal(np.concatenate([rec1[i], rec2[i]]), ref[i][1]), i
+    g.close()
+    for s in members:
         s.close()
