@@ -72,6 +72,10 @@ struct wadg_ctx {
   int nb = 1;
   int device = 0;
   cudaStream_t stream = nullptr;
+  // branch of the step graphs: the non-PML class of a stage runs on it, beside
+  // the PML class on `stream` (created at the first capture)
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool own_stream = false;
   std::string err;
   RefOps ref;
@@ -738,10 +742,41 @@ wadg_status issue_stage(wadg_ctx* ctx, int stage, double dt, double t, bool use_
   return WADG_OK;
 }
 
+// one stage of a step graph with the two element classes on parallel
+// branches: the PML class on the context's stream, the non-PML class on the
+// branch (they write disjoint elements and read the same stage input), so
+// one class's blocks take the SMs the other's leave at its tail
+template <typename Real>
+wadg_status issue_stage_branches(wadg_ctx* ctx, int stage, double dt) {
+  CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
+  CK(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
+  if (ctx->tc) {
+    StageParams<float> B = stage_params<float>(ctx, stage, dt, 0.0, true, true);
+    CK(launch_pml_class<float>(ctx, B));
+    StageParams<float> A = stage_params<float>(ctx, stage, dt, 0.0, true, false);
+    CK(launch_stage_tc(ctx->N, false, A, ctx->nb, ctx->aux, ctx->bf16, ctx->qc));
+  } else {
+    StageParams<Real> B = stage_params<Real>(ctx, stage, dt, 0.0, true, true);
+    CK(launch_pml_class<Real>(ctx, B));
+    StageParams<Real> A = stage_params<Real>(ctx, stage, dt, 0.0, true, false);
+    CK(launch_stage<Real>(ctx->N, false, false, A, ctx->nb, ctx->aux));
+  }
+  CK(cudaEventRecord(ctx->ev_join, ctx->aux));
+  CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+  ctx->cur ^= 1;
+  return WADG_OK;
+}
+
 wadg_status issue_step(wadg_ctx* ctx, double dt) {
+  const bool branches = ctx->K1 > 0 && ctx->K0 > 0 && ctx->aux;
   for (int s = 0; s < 5; ++s) {
-    wadg_status st = ctx->rs == 8 ? issue_stage<double>(ctx, s, dt, 0.0, true)
-                                  : issue_stage<float>(ctx, s, dt, 0.0, true);
+    wadg_status st;
+    if (branches)
+      st = ctx->rs == 8 ? issue_stage_branches<double>(ctx, s, dt)
+                        : issue_stage_branches<float>(ctx, s, dt);
+    else
+      st = ctx->rs == 8 ? issue_stage<double>(ctx, s, dt, 0.0, true)
+                        : issue_stage<float>(ctx, s, dt, 0.0, true);
     if (st != WADG_OK) return st;
   }
   if (ctx->nprobe > 0) {
@@ -764,6 +799,11 @@ wadg_status issue_step(wadg_ctx* ctx, double dt) {
 
 wadg_status capture_graphs(wadg_ctx* ctx, double dt) {
   invalidate_graphs(ctx);
+  if (ctx->K1 > 0 && ctx->K0 > 0 && !ctx->aux) {   // the branch of the two element classes
+    CK(cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+  }
   const int start = ctx->cur;
   for (int g = 0; g < 2; ++g) {
     ctx->cur = g;
@@ -996,6 +1036,9 @@ wadg_status wadg_destroy(wadg_ctx* ctx) {
                     &ctx->pr_out, &ctx->obj, &ctx->tdev, &ctx->stepdev, &ctx->flag,
                     &ctx->tcops, &ctx->errflag, &ctx->stored, &ctx->dperm})
     dfree(*d);
+  if (ctx->aux) cudaStreamDestroy(ctx->aux);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return WADG_OK;
