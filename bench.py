@@ -413,7 +413,7 @@ def t_end_accuracy(w, precision, sh, local, rule):
         dt = s.stable_dt(1.0)
         s.set_state(None, 0.0)
         rec = s.run_steps(w.steps, dt)
-        q = torch.empty(s._state_shape(), dtype=torch.float64, device=f"cuda:{local}")
+        q = torch.empty(s.state_shape(), dtype=torch.float64, device=f"cuda:{local}")
         s.get_state(q)
         s.synchronize()
         res[prec] = (q[:, :, 0:6].contiguous(), rec, s.objective()[0])
@@ -458,7 +458,7 @@ def accuracy_runs(sh, local, rule):
         t0 = time.perf_counter()
         rec = s.run_steps(steps, dt)
         wall = time.perf_counter() - t0
-        q = torch.empty(s._state_shape(), dtype=torch.float64, device=f"cuda:{local}")
+        q = torch.empty(s.state_shape(), dtype=torch.float64, device=f"cuda:{local}")
         s.get_state(q)
         s.synchronize()
         J = s.objective()

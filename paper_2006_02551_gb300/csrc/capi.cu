@@ -948,6 +948,46 @@ static wadg_status get_state_dev(wadg_ctx* ctx, double* q) {
   return WADG_OK;
 }
 
+// exchange through host memory: the caller's array moves as it is, in one
+// copy, through a device staging buffer that the exchange kernel converts
+// (instead of a per-element conversion loop on one host thread); when the
+// staging buffer cannot be had (a memory cap), the host loops above convert
+template <typename Real>
+static wadg_status set_state_host(wadg_ctx* ctx, const double* q) {
+  const size_t ub = (size_t)ctx->nb * ctx->K * 12 * ctx->ref.Np * sizeof(double);
+  DevPtr st;
+  if (q && dalloc(st, ub) == cudaSuccess) {
+    wadg_status s = WADG_OK;
+    cudaError_t e = cudaMemcpyAsync(st.p, q, ub, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) s = set_state_dev<Real>(ctx, static_cast<const double*>(st.p));
+    if (e == cudaSuccess && s == WADG_OK) e = cudaStreamSynchronize(ctx->stream);
+    dfree(st);
+    if (e != cudaSuccess) return fail(ctx, WADG_ECUDA, "state upload: %s", cudaGetErrorString(e));
+    if (s == WADG_OK) ctx->h2d += ub;
+    return s;
+  }
+  cudaGetLastError();   // a refused allocation must not be read as a later launch's error
+  return set_state_t<Real>(ctx, q);
+}
+
+template <typename Real>
+static wadg_status get_state_host(wadg_ctx* ctx, double* q) {
+  const size_t ub = (size_t)ctx->nb * ctx->K * 12 * ctx->ref.Np * sizeof(double);
+  DevPtr st;
+  if (dalloc(st, ub) == cudaSuccess) {
+    wadg_status s = get_state_dev<Real>(ctx, static_cast<double*>(st.p));
+    cudaError_t e = cudaSuccess;
+    if (s == WADG_OK) e = cudaMemcpyAsync(q, st.p, ub, cudaMemcpyDeviceToHost, ctx->stream);
+    if (s == WADG_OK && e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    dfree(st);
+    if (e != cudaSuccess) return fail(ctx, WADG_ECUDA, "state download: %s", cudaGetErrorString(e));
+    if (s == WADG_OK) ctx->d2h += ub;
+    return s;
+  }
+  cudaGetLastError();   // a refused allocation must not be read as a later launch's error
+  return get_state_t<Real>(ctx, q);
+}
+
 }  // namespace
 
 extern "C" {
@@ -1314,7 +1354,7 @@ wadg_status wadg_set_state(wadg_ctx* ctx, const void* q, double t, int on_device
   if (on_device)
     s = ctx->rs == 8 ? set_state_dev<double>(ctx, qd) : set_state_dev<float>(ctx, qd);
   else
-    s = ctx->rs == 8 ? set_state_t<double>(ctx, qd) : set_state_t<float>(ctx, qd);
+    s = ctx->rs == 8 ? set_state_host<double>(ctx, qd) : set_state_host<float>(ctx, qd);
   if (s == WADG_OK) ctx->t = t;
   return s;
 }
@@ -1328,7 +1368,7 @@ wadg_status wadg_get_state(wadg_ctx* ctx, void* q, double* t, int on_device) {
     if (on_device)
       s = ctx->rs == 8 ? get_state_dev<double>(ctx, qd) : get_state_dev<float>(ctx, qd);
     else
-      s = ctx->rs == 8 ? get_state_t<double>(ctx, qd) : get_state_t<float>(ctx, qd);
+      s = ctx->rs == 8 ? get_state_host<double>(ctx, qd) : get_state_host<float>(ctx, qd);
     if (s != WADG_OK) return s;
   }
   if (t) *t = ctx->t;

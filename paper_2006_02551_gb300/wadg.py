@@ -235,9 +235,13 @@ class Solver:
                                         C.byref(Nq)))
         return dict(K=K.value, K_pml=K1.value, Np=Np.value, Nq=Nq.value)
 
-    def _state_shape(self):
+    def state_shape(self):
+        """Shape of the state array of set_state / get_state: [n_batch][K][12][Np]
+        (E, H, P^E, P^H per element in the caller's element order)."""
         inf = self.info()
         return (self.n_batch, inf["K"], 12, inf["Np"])
+
+    _state_shape = state_shape
 
     def _device_ptr(self, x):
         """Address of a contiguous float64 device tensor of the state's shape

@@ -99,3 +99,31 @@ def test_bound_state_steps_as_owned_state(precision):
     assert np.array_equal(b.get_state()[0], qa)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16"])
+def test_host_exchange_staged_equals_host_loop(precision):
+    """The host-memory exchange converts on the device through a staging
+    buffer; capped at the bytes it holds, a context converts on the host
+    instead.  Both give the same internal state and the same array back, bit
+    for bit, and each moves the whole state across the host boundary."""
+    a, q0 = solver(precision)
+    b, _ = solver(precision)
+    dt = a.stable_dt(1.0)
+    b.set_memory_limit(b.set_memory_limit(0))     # no room for a staging buffer
+    for s in (a, b):
+        h0 = s.transfer_bytes()
+        s.set_state(q0, 0.25)
+        assert s.transfer_bytes()[0] - h0[0] >= q0.size * (8 if precision == "fp64" else 4) // 2
+    qa, _ = a.get_state()
+    qb, _ = b.get_state()
+    assert np.array_equal(qa, qb)
+    b.set_memory_limit(0)                          # room for the probe records
+    a.run_steps(5, dt, record=False)
+    b.run_steps(5, dt, record=False)
+    b.set_memory_limit(b.set_memory_limit(0))     # the read back converts on the host
+    qa, ta = a.get_state()
+    qb, tb = b.get_state()
+    assert ta == tb and np.array_equal(qa, qb)
+    a.close()
+    b.close()
