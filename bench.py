@@ -229,17 +229,19 @@ def mesh_dofs(s):
     return i["Np"] * 6 * (i["K"] + i["K_pml"]) * s.n_batch
 
 
-def group_vs_sequential(meshes, pml, sh, local, stream, nst):
+def group_vs_sequential(meshes, pml, sh, local, stream, nst, precision="fp32", rule="default"):
     """The meshes [(n_hex, N)] advanced one after the other (run_steps each)
     and together (per stage one grouped launch per (order, element class)
     variant, on parallel graph branches; autotuned): DOF-updates/s."""
     import torch
     from paper_2006_02551_gb300 import Group, Solver
-    from synthetic import cube_tet_mesh
+    from synthetic import compact_rule, cube_tet_mesh
     ss = []
     for n, N in meshes:
         v, e = cube_tet_mesh(n, 0.2, 100 + n)
-        s = Solver(N, "fp32", device=local, stream=sh)
+        s = Solver(N, precision, device=local, stream=sh)
+        if rule == "compact":
+            s.set_quadrature(compact_rule(N))
         s.set_mesh(v, e)
         s.set_pml(pml)
         s.set_state(None, 0.0)
@@ -282,8 +284,8 @@ def group_vs_sequential(meshes, pml, sh, local, stream, nst):
 def batching_runs(sh, local, stream):
     """The batching form: 64 independent excitations on one 162,000-tet N=3
     mesh (FP32, one launch per class and stage), and meshes of uneven size and
-    order in one grouped launch per stage against one launch sequence per
-    mesh (FP32)."""
+    order advanced as one group against one launch sequence per mesh (FP32,
+    and the mixed set also as TF32 tensor-core contexts)."""
     import torch
     from synthetic import workload
     w = workload("cube30_n3_batch64")
@@ -306,6 +308,10 @@ def batching_runs(sh, local, stream):
         recipe="16 meshes n^3 x 6 tets, n = 8 + round(16 i/15), N = 2 + (i mod 3), jitter 0.2h, "
                "PML as the benchmark workload, FP32",
         **group_vs_sequential(mixed, w.pml, sh, local, stream, 20))
+    out["mixed_meshes_tf32"] = dict(
+        recipe="the same 16 meshes as TF32 tensor-core contexts with the compact rule "
+               "(grouped: per-item launches)",
+        **group_vs_sequential(mixed, w.pml, sh, local, stream, 20, "tf32", "compact"))
     small = [(4 + (i % 3), 2 + (i % 3)) for i in range(48)]
     out["small_meshes"] = dict(
         recipe="48 meshes n^3 x 6 tets, n = 4 + (i mod 3), N = 2 + (i mod 3), FP32",

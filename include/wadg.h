@@ -377,27 +377,31 @@ const char* wadg_last_error(const wadg_ctx* ctx);
 
 /* ---------------------------------------------------------------- groups
  * Several contexts advanced together (the batching form: meshes of uneven
- * size and order).  A Runge-Kutta stage of every member and element class is
- * one launch per variant (order N, element class) present in the group, of a
- * grouped CUDA-core kernel compiled for that variant alone.  A variant's
- * blocks start on its (member, class) items in proportion to their
- * algorithmic flops and then take tiles from per-item counters until none
- * are left, so the load balances itself; the variants' launches of a stage
- * run on parallel branches, so the SMs one variant's blocks leave as its
- * tiles run out go to the others.  One step (the stage launches and each
- * member's probe and clock kernels) is captured in a CUDA graph.  Each
- * member advances exactly as wadg_run_steps advances it (the stage of
- * eqs. 10, 11 and 26-29 with the time marching of Section II.B); the grouping
- * itself has no counterpart in the paper.  Members: FP32 contexts (WADG_FP32)
- * with a mesh, the weight-adjusted or element-constant PML scheme, on one
- * device; the group runs on the first member's stream.  Each member keeps its
- * own state, time, probes and records.  The group refers to its members:
- * destroy the group before any member. */
+ * size, order and precision).  A Runge-Kutta stage of the whole group is one
+ * of two launch patterns, chosen by wadg_group_autotune or fixed by
+ * wadg_group_set_tuning:
+ *  - grouped variant kernels: one launch per variant (order N, element class)
+ *    present, of a CUDA-core kernel compiled for that variant alone, whose
+ *    blocks start on the variant's (member, class) items in proportion to
+ *    their algorithmic flops and then take tiles from per-item counters until
+ *    none are left.  Only for FP32 members (WADG_FP32) with the (N+1)^3 rule
+ *    and the weight-adjusted or element-constant PML;
+ *  - per-item launches: every (member, class) item as the member's own stage
+ *    kernel (any precision, volume rule and PML scheme: tensor-core members
+ *    included).  A group with any member outside the first kind uses this.
+ * The launches of a stage run in turn or on parallel branches, so the SMs one
+ * launch leaves at its tail go to the others.  One step (the stage launches
+ * and each member's probe and clock kernels) is captured in a CUDA graph.
+ * Each member advances exactly as wadg_run_steps advances it (the stage of
+ * eqs. 10, 11 and 26-29 with the time marching of Section II.B), bit for bit;
+ * the grouping itself has no counterpart in the paper.  Members: contexts
+ * with a mesh on one device; the group runs on the first member's stream.
+ * Each member keeps its own state, time, probes and records.  The group
+ * refers to its members: destroy the group before any member. */
 typedef struct wadg_group wadg_group;
 
 /* EINVAL for a null or repeated member or members on different devices,
- * ESTATE for a member without a mesh, EUNSUPPORTED for a member that is not an
- * FP32 context or uses the stored-matrix scheme. */
+ * ESTATE for a member without a mesh or with an incomplete set-up. */
 wadg_status wadg_group_create(int32_t n, wadg_ctx* const* ctxs, wadg_group** out);
 wadg_status wadg_group_destroy(wadg_group* g);
 
@@ -418,7 +422,9 @@ wadg_status wadg_group_autotune(wadg_group* g, const double* dt, int32_t reps, d
  * chooses among): per_item (1: every item as its single-context kernel),
  * parallel (1: a stage's launches on parallel branches), share (1: each
  * variant's grid its share of the GPU), tile_divisor (1..64), blocks_per_sm
- * (1..8, capped by each variant's occupancy).  EINVAL out of range. */
+ * (1..8, capped by each variant's occupancy).  EINVAL out of range;
+ * EUNSUPPORTED for per_item = 0 in a group whose members the grouped variant
+ * kernels do not serve. */
 wadg_status wadg_group_set_tuning(wadg_group* g, int32_t per_item, int32_t parallel,
                                   int32_t share, int32_t tile_divisor, int32_t blocks_per_sm);
 

@@ -708,16 +708,43 @@ StageParams<Real> stage_params(wadg_ctx* ctx, int stage, double dt, double t, bo
 // the PML-class launch of a stage: the stored-matrix kernel, the tensor-core
 // kernel (TF32 contexts) or the CUDA-core kernel
 template <typename Real>
-cudaError_t launch_pml_class(wadg_ctx* ctx, const StageParams<Real>& P) {
-  if (ctx->scheme == WADG_PML_STORED) return launch_stage_stored<Real>(ctx->N, P, ctx->nb, ctx->stream);
+cudaError_t launch_pml_class(wadg_ctx* ctx, const StageParams<Real>& P, cudaStream_t s) {
+  if (ctx->scheme == WADG_PML_STORED) return launch_stage_stored<Real>(ctx->N, P, ctx->nb, s);
   if constexpr (std::is_same<Real, float>::value) {
     if (ctx->tc) {
       // compact volume rules: the row-owned kernel; (N+1)^3 rules: the other
-      if (ctx->qc == 1) return launch_pml_tc_rows(ctx->N, P, ctx->nb, ctx->stream, ctx->bf16);
-      return launch_stage_tc(ctx->N, true, P, ctx->nb, ctx->stream, ctx->bf16, ctx->qc);
+      if (ctx->qc == 1) return launch_pml_tc_rows(ctx->N, P, ctx->nb, s, ctx->bf16);
+      return launch_stage_tc(ctx->N, true, P, ctx->nb, s, ctx->bf16, ctx->qc);
     }
   }
-  return launch_stage<Real>(ctx->N, true, ctx->kappa, P, ctx->nb, ctx->stream, ctx->qc);
+  return launch_stage<Real>(ctx->N, true, ctx->kappa, P, ctx->nb, s, ctx->qc);
+}
+template <typename Real>
+cudaError_t launch_pml_class(wadg_ctx* ctx, const StageParams<Real>& P) {
+  return launch_pml_class<Real>(ctx, P, ctx->stream);
+}
+
+// the non-PML class of a stage on stream s (the kernel of the context's kind)
+template <typename Real>
+cudaError_t launch_std_class(wadg_ctx* ctx, const StageParams<Real>& P, cudaStream_t s) {
+  if constexpr (std::is_same<Real, float>::value)
+    if (ctx->tc) return launch_stage_tc(ctx->N, false, P, ctx->nb, s, ctx->bf16, ctx->qc);
+  return launch_stage<Real>(ctx->N, false, false, P, ctx->nb, s);
+}
+
+// one element class of one stage of a context, on stream s, with the device
+// clock (graph replays); tile: elements per tile of the CUDA-core kernels
+// (0: the largest)
+cudaError_t launch_member_class(wadg_ctx* x, int st, double dt, bool pml, int tile,
+                                cudaStream_t s) {
+  if (x->rs == 8) {
+    StageParams<double> P = stage_params<double>(x, st, dt, 0.0, true, pml);
+    P.tile_elems = tile;
+    return pml ? launch_pml_class<double>(x, P, s) : launch_std_class<double>(x, P, s);
+  }
+  StageParams<float> P = stage_params<float>(x, st, dt, 0.0, true, pml);
+  P.tile_elems = x->tc ? 0 : tile;
+  return pml ? launch_pml_class<float>(x, P, s) : launch_std_class<float>(x, P, s);
 }
 
 template <typename Real>
@@ -2011,6 +2038,12 @@ struct wadg_group {
   int sms = 1;
   int blocks_per_sm = 1;   // autotuned
   int tile_div = 1;        // autotuned: tile = largest tile / tile_div
+  // the grouped variant kernels serve FP32 CUDA-core members with the
+  // (N+1)^3 rule and a weight-adjusted or element-constant PML; any other
+  // member (FP64, TF32, BF16, a compact rule, the stored scheme) makes the
+  // group launch per item
+  bool variants_ok = true;
+  std::vector<double> dt_now;   // the members' steps of the current tables
   bool per_item = false;   // autotuned: each (member, class) item launched as its
                            // single-context kernel (else one grouped kernel per variant)
   bool parallel = true;    // autotuned: a stage's launches on parallel branches
@@ -2025,7 +2058,6 @@ struct wadg_group {
   std::vector<Variant> vars;
   std::vector<int> first;
   DevPtr dparams, dfirst;          // params [2 parities][5 stages][items]
-  std::vector<StageParams<float>> hparams;   // the same on the host (per-item launches)
   DevPtr dntiles, dcounter;        // tiles per item, tile counters (zeroed per launch)
   // streams and events of the parallel branches (variant v > 0 on aux[v - 1])
   std::vector<cudaStream_t> aux;
@@ -2111,7 +2143,7 @@ void group_plan(wadg_group* g) {
       it.c = c;
       it.pml = pml;
       it.code = x->N * 4 + (pml ? (x->kappa ? 2 : 1) : 0);
-      const int tmax = group_tile_max(x->N, pml);
+      const int tmax = g->variants_ok ? group_tile_max(x->N, pml) : 1;
       it.tile = std::max(1, tmax / g->tile_div);
       it.tiles = (ne + it.tile - 1) / it.tile * x->nb;
       it.work = item_cost(x->N, pml) * (double)ne * x->nb;
@@ -2128,6 +2160,11 @@ void group_plan(wadg_group* g) {
   g->vars.clear();
   g->first.clear();
   g->nblocks = 0;
+  if (!g->variants_ok) {   // per-item launches only; tiles as each kernel chooses
+    g->per_item = true;
+    for (auto& it : g->items) it.tile = 0;
+    return;
+  }
   double all = 0.0;
   for (auto& it : g->items) all += it.work;
   all = std::max(all, 1.0);
@@ -2221,6 +2258,8 @@ void group_drop_clusters(wadg_group* g);
 
 // stage parameters of every item for both step parities and all 5 stages
 wadg_status group_upload(wadg_group* g, const double* dt) {
+  g->dt_now.assign(dt, dt + g->ctx.size());
+  if (!g->variants_ok) return group_branches(g);
   const int ni = (int)g->items.size();
   std::vector<StageParams<float>> hp((size_t)2 * 5 * ni);
   std::vector<int> cur0(g->ctx.size());
@@ -2238,7 +2277,6 @@ wadg_status group_upload(wadg_group* g, const double* dt) {
         hp[((size_t)par * 5 + st) * ni + i] = P;
         x->cur = cur0[it.c];
       }
-  g->hparams = hp;
   std::vector<int> ntiles(ni);
   for (int i = 0; i < ni; ++i) ntiles[i] = (int)g->items[i].tiles;
   GCK(dalloc(g->dntiles, ntiles.size() * sizeof(int)));
@@ -2277,11 +2315,14 @@ cudaError_t group_launch_items(wadg_group* g, int par, int st) {
   }
   for (size_t i = 0; i < ni; ++i) {
     const auto& it = g->items[i];
-    const wadg_ctx* x = g->ctx[it.c];
+    wadg_ctx* x = g->ctx[it.c];
     const size_t k = i % nbr;
     cudaStream_t s = k == 0 ? g->stream : g->aux[k - 1];
-    const StageParams<float>& P = g->hparams[((size_t)par * 5 + st) * ni + i];
-    e = launch_stage<float>(x->N, it.pml, it.code % 4 == 2, P, x->nb, s, x->qc);
+    // the buffers of this parity and stage (each stage flips them, a step once)
+    const int cur0 = x->cur;
+    x->cur = cur0 ^ par ^ (st & 1);
+    e = launch_member_class(x, st, g->dt_now[it.c], it.pml, it.tile, s);
+    x->cur = cur0;
     if (e != cudaSuccess) return e;
   }
   for (size_t k = 1; k < nbr; ++k) {
@@ -2336,7 +2377,7 @@ wadg_status group_issue_step(wadg_group* g, int par, const double* dt) {
       pp.out = (double*)x->pr_out.p;
       pp.obj = (double*)x->obj.p;
       pp.step = (const int64_t*)x->stepdev.p;
-      GCK(launch_probes(false, pp, g->stream));
+      GCK(launch_probes(x->rs == 8, pp, g->stream));
     }
     GCK(launch_advance((double*)x->tdev.p, (int64_t*)x->stepdev.p, dt[c], g->stream));
   }
@@ -2371,13 +2412,6 @@ wadg_status wadg_group_create(int32_t n, wadg_ctx* const* ctxs, wadg_group** out
     if (!x) return fail(nullptr, WADG_EINVAL, "null context %d", i);
     if (!x->has_mesh || !x->ready || !x->src_ok || !x->probes_ok || !x->ops_ok)
       return fail(nullptr, WADG_ESTATE, "context %d has no mesh or an incomplete set-up", i);
-    if (x->prec != WADG_FP32 || x->tc)
-      return fail(nullptr, WADG_EUNSUPPORTED, "groups run the FP32 CUDA-core kernels (context %d)", i);
-    if (x->qc != 0)
-      return fail(nullptr, WADG_EUNSUPPORTED,
-                  "groups run the default (N+1)^3-point volume rule (context %d)", i);
-    if (x->scheme == WADG_PML_STORED)
-      return fail(nullptr, WADG_EUNSUPPORTED, "groups run the weight-adjusted kernels (context %d)", i);
     if (x->device != ctxs[0]->device)
       return fail(nullptr, WADG_EINVAL, "group members must share a device");
     for (int j = 0; j < i; ++j)
@@ -2385,6 +2419,11 @@ wadg_status wadg_group_create(int32_t n, wadg_ctx* const* ctxs, wadg_group** out
   }
   wadg_group* g = new wadg_group();
   g->ctx.assign(ctxs, ctxs + n);
+  for (int i = 0; i < n; ++i) {
+    const wadg_ctx* x = ctxs[i];
+    if (x->prec != WADG_FP32 || x->tc || x->qc != 0 || x->scheme == WADG_PML_STORED)
+      g->variants_ok = false;
+  }
   g->device = ctxs[0]->device;
   g->stream = ctxs[0]->stream;
   cudaSetDevice(g->device);
@@ -2428,10 +2467,11 @@ wadg_status wadg_group_autotune(wadg_group* g, const double* dt, int32_t reps, d
   double best = 1e300;
   int best_bps = 1, best_div = 1;
   bool best_par = true, best_share = false, best_item = false;
-  for (int item = 0; item < 2; ++item)
+  for (int item = g->variants_ok ? 0 : 1; item < 2; ++item)
   for (int par = 1; par >= 0; --par)
   for (int shr = 0; shr < (item ? 1 : 2); ++shr)
   for (int div : {1, 2, 4}) {
+    if (!g->variants_ok && div > 1) continue;   // per-item launches keep each kernel's tile
     g->per_item = item != 0;
     g->parallel = par != 0;
     g->share = shr != 0;
@@ -2477,6 +2517,10 @@ wadg_status wadg_group_set_tuning(wadg_group* g, int32_t per_item, int32_t paral
   if (!g) return WADG_EINVAL;
   if (tile_divisor < 1 || tile_divisor > 64 || blocks_per_sm < 1 || blocks_per_sm > 8)
     return gfail(g, WADG_EINVAL, "tile divisor must be 1..64 and blocks per SM 1..8");
+  if (!per_item && !g->variants_ok)
+    return gfail(g, WADG_EUNSUPPORTED,
+                 "the grouped variant kernels serve FP32 CUDA-core members with the (N+1)^3 "
+                 "rule and a weight-adjusted or element-constant PML only");
   group_drop_graphs(g);
   g->per_item = per_item != 0;
   g->parallel = parallel != 0;

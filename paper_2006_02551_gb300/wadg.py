@@ -366,10 +366,10 @@ class Solver:
 
 
 class Group:
-    """Several FP32 solvers advanced together: per stage one grouped launch
-    per (order, element class) variant present, the launches of a stage on
-    parallel graph branches (wadg_group_*).  Refers to the solvers: close it
-    before them."""
+    """Several solvers advanced together (wadg_group_*): per stage one grouped
+    launch per (order, element class) variant (FP32 CUDA-core members), or
+    every member's own kernels (any precision), in turn or on parallel graph
+    branches.  Refers to the solvers: close it before them."""
 
     def __init__(self, solvers):
         self.lib = load()

@@ -88,16 +88,66 @@ def test_group_equals_single_runs(tune):
         s.close()
 
 
-def test_group_rejects_unsupported_members():
+def test_group_rejects_repeated_members_and_variants_it_cannot_serve():
     from paper_2006_02551_gb300 import Group, WadgError
+    from paper_2006_02551_gb300.wadg import WADG_EUNSUPPORTED
     a = make(3, 3, True, 1)
     b = make(3, 3, True, 1, prec="tf32")
     with pytest.raises(WadgError):
-        Group([a, b])
-    with pytest.raises(WadgError):
         Group([a, a])
+    g = Group([a, b])                 # a tensor-core member: per-item launches only
+    assert g.info()["per_item"]
+    with pytest.raises(WadgError) as err:
+        g.set_tuning(per_item=False)
+    assert err.value.status == WADG_EUNSUPPORTED
+    g.close()
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("parallel", [True, False])
+def test_mixed_precision_group_equals_single_runs(parallel):
+    """Members of every kind in one group — TF32 and BF16 tensor-core
+    contexts with the compact rule, an FP64 context, an FP32 context with the
+    stored-matrix scheme — launched per item: each equals its own run_steps
+    bit for bit over two calls."""
+    from paper_2006_02551_gb300 import Group, Solver
+    from synthetic import compact_rule
+
+    def member(kind):
+        N, n_hex, prec = {"tf32": (4, 3, "tf32"), "bf16": (3, 4, "bf16"),
+                          "fp64": (2, 3, "fp64"), "stored": (3, 3, "fp32")}[kind]
+        v, e = cube_tet_mesh(n_hex, 0.15, 30 + N)
+        s = Solver(N, prec)
+        if prec in ("tf32", "bf16"):
+            s.set_quadrature(compact_rule(N))
+        s.set_mesh(v, e)
+        s.set_pml(PML, "stored" if kind == "stored" else "waa")
+        s.set_sources([Dipole(x=(0.05, -0.02, 0.03), dir=(0.0, 0.0, 1.0), t0=0.4, width=0.15)])
+        s.set_probes(PROBES)
+        s.set_state(None, 0.0)
+        return s
+
+    kinds = ["tf32", "bf16", "fp64", "stored"]
+    singles = [member(k) for k in kinds]
+    dts = [0.8 * s.stable_dt(1.0) for s in singles]
+    ref = []
+    for s, dt in zip(singles, dts):
+        rec = s.run_steps(11, dt)
+        ref.append((s.get_state()[0], rec))
+        s.close()
+    members = [member(k) for k in kinds]
+    g = Group(members)
+    g.set_tuning(per_item=True, parallel=parallel)
+    rec1 = g.run_steps(6, dts)
+    rec2 = g.run_steps(5, dts)
+    for i, s in enumerate(members):
+        q, _ = s.get_state()
+        assert np.array_equal(q, ref[i][0]), (kinds[i], rel(q, ref[i][0]))
+        assert np.array_equal(np.concatenate([rec1[i], rec2[i]]), ref[i][1]), kinds[i]
+    g.close()
+    for s in members:
+        s.close()
 
 
 def test_small_mixed_group_matches_oracle():
