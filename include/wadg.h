@@ -72,13 +72,15 @@ typedef enum { WADG_FP64 = 0, WADG_FP32 = 1, WADG_TF32 = 2, WADG_BF16 = 3 } wadg
  *   WAA     eqs. 26-29, the weight-adjusted terms with the coefficients
  *           sampled at the volume quadrature nodes (the paper's method).
  *   STORED  eqs. 10-13 with per-element weighted mass matrices (eq. 15):
- *           for kappa = 1 the library stores M_k^-1 M_k^{b_u}, M_k^-1 M_k^{c_u}
- *           and M_k^-1 M_k^{d_u} per PML element and axis (9 N_p^2 values;
- *           (M^a)^-1 M_k and M_k^-1 M^{1/kappa} are the identity), built in
- *           double by a Stroud rule with N + 6 points per direction.  The
- *           reference "exact" scheme the WAA approximates; CUDA-core kernels
- *           in every precision (a TF32/BF16 context runs its PML class on the FP32
- *           CUDA-core kernel).  EUNSUPPORTED when kappa_max != 1.
+ *           the library stores M_k^-1 M_k^{b_u}, M_k^-1 M_k^{c_u} and
+ *           M_k^-1 M_k^{d_u} per PML element and axis, and with kappa_max != 1
+ *           also M_k^-1 M_k^{1/kappa_u} and (M_k^{a_u})^-1 M_k (15 N_p^2
+ *           values, the paper's count; with kappa = 1 the last two are the
+ *           identity and 9 N_p^2 are stored), built in double by a Stroud
+ *           rule with N + 6 points per direction, (M^a)^-1 M_k by Gauss-Jordan
+ *           elimination in double.  The reference "exact" scheme the WAA
+ *           approximates; CUDA-core kernels in every precision (a TF32/BF16
+ *           context runs its PML class on the FP32 CUDA-core kernel).
  *   EC      the WAA kernels with element-constant coefficients: every
  *           quadrature node of an element takes the profile's value at the
  *           element centroid (the piecewise-constant paving the paper
@@ -155,8 +157,8 @@ wadg_status wadg_set_materials(wadg_ctx* ctx, const double* eps_r, const double*
  * stored per element as sigma_u (and kappa_u when kappa_max != 1); the
  * stored-matrix scheme holds its operators instead (see wadg_pml_scheme).
  * Pass NULL to remove the PML.  EINVAL for an unknown scheme, EUNSUPPORTED
- * for kappa_max != 1 with the stored scheme or with a TF32/BF16 context.  Resets
- * the state and re-maps sources and probes. */
+ * for kappa_max != 1 with the weight-adjusted or element-constant scheme in a
+ * TF32/BF16 context.  Resets the state and re-maps sources and probes. */
 wadg_status wadg_set_pml_profile(wadg_ctx* ctx, const wadg_pml_profile* prof,
                                  wadg_pml_scheme scheme);
 

@@ -353,16 +353,25 @@ wadg_status build_stored_ops(wadg_ctx* ctx, const double* dprof) {
   CK(cudaMemcpy(drh.p, rh.data(), rh.size() * 8, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(dVh.p, Vh.data(), Vh.size() * 8, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(dPh.p, Ph.data(), Ph.size() * 8, cudaMemcpyHostToDevice));
-  const size_t bytes = (size_t)ctx->K1 * 9 * Np * NpP * sizeof(Real);
+  // 3 operators per axis with kappa = 1 (B, C, D), 5 otherwise (+ K, A^-1)
+  const int NB = ctx->kappa ? 5 : 3;
+  const size_t bytes = (size_t)ctx->K1 * 3 * NB * Np * NpP * sizeof(Real);
+  DevPtr dbad;
   CK(dalloc(ctx->stored, bytes));
+  CK(dalloc(dbad, sizeof(int)));
   CK(cudaMemsetAsync(ctx->stored.p, 0, bytes, ctx->stream));
+  CK(cudaMemsetAsync(dbad.p, 0, sizeof(int), ctx->stream));
   CK((launch_stored_ops<Real>(R.N, (int)ctx->K1, (int)ctx->K0, (const double*)ctx->verts.p, dprof,
                               (const double*)drh.p, (const double*)dPh.p, (const double*)dVh.p,
-                              Nh, (Real*)ctx->stored.p, ctx->stream)));
+                              Nh, ctx->kappa, (Real*)ctx->stored.p, (int*)dbad.p, ctx->stream)));
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, dbad.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   dfree(drh);
   dfree(dVh);
   dfree(dPh);
+  dfree(dbad);
+  if (bad) return fail(ctx, WADG_EINVAL, "an a_u operator of the stored scheme is singular");
   return WADG_OK;
 }
 
@@ -709,7 +718,8 @@ StageParams<Real> stage_params(wadg_ctx* ctx, int stage, double dt, double t, bo
 // kernel (TF32 contexts) or the CUDA-core kernel
 template <typename Real>
 cudaError_t launch_pml_class(wadg_ctx* ctx, const StageParams<Real>& P, cudaStream_t s) {
-  if (ctx->scheme == WADG_PML_STORED) return launch_stage_stored<Real>(ctx->N, P, ctx->nb, s);
+  if (ctx->scheme == WADG_PML_STORED)
+    return launch_stage_stored<Real>(ctx->N, ctx->kappa, P, ctx->nb, s);
   if constexpr (std::is_same<Real, float>::value) {
     if (ctx->tc) {
       // compact volume rules: the row-owned kernel; (N+1)^3 rules: the other
@@ -1284,8 +1294,6 @@ wadg_status wadg_set_pml_profile(wadg_ctx* ctx, const wadg_pml_profile* prof,
     if (ctx->tc && scheme != WADG_PML_STORED && !tc_supported(ctx->N, false, ctx->bf16, ctx->qc))
       return fail(ctx, WADG_EUNSUPPORTED,
                   "TF32 operands at N = 5 need a compact volume rule (wadg_set_quadrature)");
-    if (kap && scheme == WADG_PML_STORED)
-      return fail(ctx, WADG_EUNSUPPORTED, "the stored-matrix scheme is built for kappa = 1");
     ctx->has_prof = true;
     ctx->prof = *prof;
     ctx->kappa = kap;

@@ -106,40 +106,61 @@ template cudaError_t launch_stage<float>(int, bool, bool, const StageParams<floa
                                          cudaStream_t, int);
 
 // ------------------------------------------------------- stored-matrix scheme
+template <typename Real, int N>
+static cudaError_t configure_stored_n() {
+  cudaError_t e = configure_one<Real, N, true, false, true>();
+  if (e == cudaSuccess) e = configure_one<Real, N, true, true, true>();
+  return e;
+}
+
 template <typename Real>
 cudaError_t configure_stored_kernels(int N) {
   switch (N) {
-    case 1: return configure_one<Real, 1, true, false, true>();
-    case 2: return configure_one<Real, 2, true, false, true>();
-    case 3: return configure_one<Real, 3, true, false, true>();
-    case 4: return configure_one<Real, 4, true, false, true>();
-    case 5: return configure_one<Real, 5, true, false, true>();
+    case 1: return configure_stored_n<Real, 1>();
+    case 2: return configure_stored_n<Real, 2>();
+    case 3: return configure_stored_n<Real, 3>();
+    case 4: return configure_stored_n<Real, 4>();
+    case 5: return configure_stored_n<Real, 5>();
     default: return cudaErrorInvalidValue;
   }
 }
 template cudaError_t configure_stored_kernels<double>(int);
 template cudaError_t configure_stored_kernels<float>(int);
 
+template <typename Real, int N>
+static cudaError_t launch_stored_n(bool kappa, const StageParams<Real>& P, int nb, cudaStream_t s) {
+  return kappa ? launch_one<Real, N, true, true, true>(P, nb, s)
+               : launch_one<Real, N, true, false, true>(P, nb, s);
+}
+
 template <typename Real>
-cudaError_t launch_stage_stored(int N, const StageParams<Real>& P, int nb, cudaStream_t s) {
+cudaError_t launch_stage_stored(int N, bool kappa, const StageParams<Real>& P, int nb,
+                                cudaStream_t s) {
   switch (N) {
-    case 1: return launch_one<Real, 1, true, false, true>(P, nb, s);
-    case 2: return launch_one<Real, 2, true, false, true>(P, nb, s);
-    case 3: return launch_one<Real, 3, true, false, true>(P, nb, s);
-    case 4: return launch_one<Real, 4, true, false, true>(P, nb, s);
-    case 5: return launch_one<Real, 5, true, false, true>(P, nb, s);
+    case 1: return launch_stored_n<Real, 1>(kappa, P, nb, s);
+    case 2: return launch_stored_n<Real, 2>(kappa, P, nb, s);
+    case 3: return launch_stored_n<Real, 3>(kappa, P, nb, s);
+    case 4: return launch_stored_n<Real, 4>(kappa, P, nb, s);
+    case 5: return launch_stored_n<Real, 5>(kappa, P, nb, s);
     default: return cudaErrorInvalidValue;
   }
 }
-template cudaError_t launch_stage_stored<double>(int, const StageParams<double>&, int, cudaStream_t);
-template cudaError_t launch_stage_stored<float>(int, const StageParams<float>&, int, cudaStream_t);
+template cudaError_t launch_stage_stored<double>(int, bool, const StageParams<double>&, int,
+                                                 cudaStream_t);
+template cudaError_t launch_stage_stored<float>(int, bool, const StageParams<float>&, int,
+                                                cudaStream_t);
 
-// Stored operators M_k^-1 M_k^{alpha} = P_h diag(alpha(x_h)) V_h for alpha in
-// {b_u, c_u, d_u} of eq. 9 (kappa = 1), u = x, y, z, of TE elements per block,
-// in double precision.  The rule's points are processed in chunks staged in
-// shared memory (P_h and V_h columns, the nine coefficient samples of each
-// element); every thread accumulates ENT entries (i, j) of the nine operators
-// of each of its block's elements in registers.
+// Stored operators M_k^-1 M_k^{alpha} = P_h diag(alpha(x_h)) V_h of eq. 15 for
+// the coefficients alpha of eq. 9 on each axis u = x, y, z, of TE elements per
+// block, in double precision.  Kinds per axis: 0 b_u, 1 c_u, 2 d_u, and with
+// kappa != 1 also 3 kappa_u^-1 and 4 a_u (the last is inverted in place by
+// stored_invert_kernel).  A launch computes the kinds of one set (0: b, c, d;
+// 1: kappa^-1, a).  The rule's points are processed in chunks staged in shared
+// memory (P_h and V_h columns, the coefficient samples of each element); every
+// thread accumulates ENT entries (i, j) of the set's operators of each of its
+// block's elements in registers.  Layout: block (e, u, kind) at
+// ((e * 3 + u) * NB + kind) * Np * NpP, transposed (entry (i, j) at j NpP + i),
+// NB = 3 kinds (kappa = 1) or 5.
 template <int N>
 struct StoredSetup {
   static constexpr int Np = (N + 1) * (N + 2) * (N + 3) / 6;
@@ -150,22 +171,25 @@ struct StoredSetup {
   static constexpr int HC = 32;
 };
 
-template <typename Real, int N>
+template <typename Real, int N, int SET>
 __global__ void __launch_bounds__(StoredSetup<N>::THREADS)
 stored_ops_kernel(int K1, int K0, int Nh, const double* verts, const double* prof,
-                  const double* rh, const double* Ph, const double* Vh, Real* out) {
+                  const double* rh, const double* Ph, const double* Vh, int NB, Real* out) {
   using S = StoredSetup<N>;
   constexpr int Np = S::Np, NpP = S::NpP, NT = S::THREADS, ENT = S::ENT, TE = S::TE, HC = S::HC;
+  constexpr int NK = SET == 0 ? 3 : 2;   // kinds of this set
+  constexpr int K0K = SET == 0 ? 0 : 3;  // first kind of this set
+  constexpr int NM = 3 * NK;
   __shared__ double PhC[Np][HC];
   __shared__ double VhC[HC][Np];
-  __shared__ double al[TE][9][HC];   // [element][3 u + kind][point]: b_u, c_u, d_u
+  __shared__ double al[TE][NM][HC];   // [element][NK u + kind][point]
   const int tid = threadIdx.x;
   const int e0 = blockIdx.x * TE;
-  double acc[TE][9][ENT];
+  double acc[TE][NM][ENT];
 #pragma unroll
   for (int t = 0; t < TE; ++t)
 #pragma unroll
-    for (int m = 0; m < 9; ++m)
+    for (int m = 0; m < NM; ++m)
 #pragma unroll
       for (int k = 0; k < ENT; ++k) acc[t][m][k] = 0.0;
   const double ie0 = 1.0 / prof[15];
@@ -181,7 +205,7 @@ stored_ops_kernel(int K1, int K0, int Nh, const double* verts, const double* pro
     }
     for (int idx = tid; idx < TE * HC; idx += NT) {
       const int t = idx / HC, hh = idx - t * HC;
-      double sg[3] = {0.0, 0.0, 0.0};
+      double sg[3] = {0.0, 0.0, 0.0}, kp[3] = {1.0, 1.0, 1.0};
       if (e0 + t < K1 && h0 + hh < Nh) {
         const double* v = verts + (int64_t)(K0 + e0 + t) * 12;
         const double r = rh[(h0 + hh) * 3], s_ = rh[(h0 + hh) * 3 + 1], tt = rh[(h0 + hh) * 3 + 2];
@@ -190,15 +214,25 @@ stored_ops_kernel(int K1, int K0, int Nh, const double* verts, const double* pro
         for (int u = 0; u < 3; ++u) {
           const double x = l0 * v[u] + l1 * v[3 + u] + l2 * v[6 + u] + l3 * v[9 + u];
           const double d = (fabs(x) - prof[u]) / prof[3 + u];
-          sg[u] = d > 0 ? prof[6 + u] * pow(d, prof[9 + u]) : 0.0;
+          const double g = d > 0 ? pow(d, prof[9 + u]) : 0.0;
+          sg[u] = d > 0 ? prof[6 + u] * g : 0.0;
+          kp[u] = 1.0 + (prof[12 + u] - 1.0) * g;   // 1 exactly where d <= 0 or kappa_max = 1
         }
       }
       for (int u = 0; u < 3; ++u) {
-        const double su = sg[u], sv = sg[(u + 1) % 3], sw = sg[(u + 2) % 3];
-        const double b = (sv + sw - su) * ie0;              // eq. 9, kappa = 1
-        al[t][3 * u][hh] = b;
-        al[t][3 * u + 1][hh] = sv * sw * ie0 * ie0 - b * su * ie0;
-        al[t][3 * u + 2][hh] = su * ie0;
+        const int v_ = (u + 1) % 3, w_ = (u + 2) % 3;
+        const double su = sg[u], sv = sg[v_], sw = sg[w_];
+        const double ku = kp[u], kv = kp[v_], kw = kp[w_];
+        const double a = kv * kw / ku;                       // eq. 9
+        if (SET == 0) {
+          const double b = (sv * kw + sw * kv - a * su) * ie0 / ku;
+          al[t][3 * u][hh] = b;
+          al[t][3 * u + 1][hh] = sv * sw * ie0 * ie0 - b * su * ie0;
+          al[t][3 * u + 2][hh] = su * ie0 / ku;
+        } else {
+          al[t][2 * u][hh] = 1.0 / ku;
+          al[t][2 * u + 1][hh] = a;
+        }
       }
     }
     __syncthreads();
@@ -212,7 +246,7 @@ stored_ops_kernel(int K1, int K0, int Nh, const double* verts, const double* pro
 #pragma unroll
         for (int t = 0; t < TE; ++t)
 #pragma unroll
-          for (int m = 0; m < 9; ++m) acc[t][m][k] += w * al[t][m][hh];
+          for (int m = 0; m < NM; ++m) acc[t][m][k] += w * al[t][m][hh];
       }
     }
   }
@@ -225,22 +259,110 @@ stored_ops_kernel(int K1, int K0, int Nh, const double* verts, const double* pro
       if (ent >= Np * Np) continue;
       const int i = ent / Np, j = ent - i * Np;
 #pragma unroll
-      for (int m = 0; m < 9; ++m)   // transposed: row j of the stored block is column j
-        out[(((int64_t)(e0 + t) * 9 + m) * Np + j) * NpP + i] = (Real)acc[t][m][k];
+      for (int m = 0; m < NM; ++m) {   // transposed: row j of the stored block is column j
+        const int u = m / NK, kind = K0K + m % NK;
+        out[((((int64_t)(e0 + t) * 3 + u) * NB + kind) * Np + j) * NpP + i] = (Real)acc[t][m][k];
+      }
     }
+  }
+}
+
+// In place, the inverse of the stored a_u operator A = M_k^-1 M_k^{a_u} (kind
+// 4) of every element and axis, so that the stage applies A^-1 =
+// (M_k^{a_u})^-1 M_k of eqs. 10, 11: Gauss-Jordan elimination with partial
+// pivoting on [A | I] in double precision, one block per (element, axis).
+// A zero pivot (A is similar to a positive definite matrix, so none should
+// occur) sets *bad.
+template <typename Real, int N>
+__global__ void __launch_bounds__(128) stored_invert_kernel(int K1, Real* ops, int* bad) {
+  constexpr int Np = (N + 1) * (N + 2) * (N + 3) / 6;
+  constexpr int NpP = (Np + 3) & ~3;
+  constexpr int W = 2 * Np;
+  constexpr int NT = 128;
+  extern __shared__ double Msh[];   // [Np][W]
+  __shared__ double fac[Np];
+  __shared__ int piv;
+  __shared__ double pivv;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int64_t eu = blockIdx.x;    // element * 3 + axis
+  if (eu >= 3 * (int64_t)K1) return;
+  Real* blk = ops + (eu * 5 + 4) * Np * NpP;
+  for (int idx = tid; idx < Np * Np; idx += NT) {
+    const int i = idx / Np, j = idx - i * Np;
+    Msh[i * W + j] = (double)blk[j * NpP + i];
+    Msh[i * W + Np + j] = i == j ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int k = 0; k < Np; ++k) {
+    if (tid < 32) {   // pivot: the largest |A[i][k]|, i >= k (the first of equals)
+      double best = -1.0;
+      int bi = k;
+      for (int i = k + lane; i < Np; i += 32) {
+        const double v = fabs(Msh[i * W + k]);
+        if (v > best) { best = v; bi = i; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) piv = bi;
+    }
+    __syncthreads();
+    const int pk = piv;
+    if (pk != k)
+      for (int j = tid; j < W; j += NT) {
+        const double t = Msh[k * W + j];
+        Msh[k * W + j] = Msh[pk * W + j];
+        Msh[pk * W + j] = t;
+      }
+    __syncthreads();
+    if (tid == 0) {
+      pivv = Msh[k * W + k];
+      if (!(fabs(pivv) > 1e-300)) {
+        atomicExch(bad, 1);
+        pivv = 1.0;
+      }
+    }
+    __syncthreads();
+    for (int j = tid; j < W; j += NT) Msh[k * W + j] /= pivv;
+    for (int i = tid; i < Np; i += NT) fac[i] = i == k ? 0.0 : Msh[i * W + k];
+    __syncthreads();
+    for (int idx = tid; idx < Np * W; idx += NT) {
+      const int i = idx / W, j = idx - i * W;
+      Msh[idx] -= fac[i] * Msh[k * W + j];
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < Np * Np; idx += NT) {
+    const int i = idx / Np, j = idx - i * Np;
+    blk[j * NpP + i] = (Real)Msh[i * W + Np + j];
   }
 }
 
 template <typename Real>
 cudaError_t launch_stored_ops(int N, int K1, int K0, const double* verts, const double* prof,
                               const double* rh, const double* Ph, const double* Vh, int Nh,
-                              Real* out, cudaStream_t s) {
+                              bool kappa, Real* out, int* bad, cudaStream_t s) {
   if (K1 <= 0) return cudaSuccess;
+  const int NB = kappa ? 5 : 3;
 #define WADG_STORED_CASE(NN)                                                              \
   case NN: {                                                                              \
     using S = StoredSetup<NN>;                                                            \
-    stored_ops_kernel<Real, NN><<<(K1 + S::TE - 1) / S::TE, S::THREADS, 0, s>>>(          \
-        K1, K0, Nh, verts, prof, rh, Ph, Vh, out);                                        \
+    const int grid = (K1 + S::TE - 1) / S::TE;                                            \
+    stored_ops_kernel<Real, NN, 0><<<grid, S::THREADS, 0, s>>>(K1, K0, Nh, verts, prof,   \
+                                                               rh, Ph, Vh, NB, out);      \
+    if (kappa) {                                                                          \
+      stored_ops_kernel<Real, NN, 1><<<grid, S::THREADS, 0, s>>>(K1, K0, Nh, verts, prof, \
+                                                                 rh, Ph, Vh, NB, out);    \
+      constexpr int Np = S::Np;                                                           \
+      const size_t sm = (size_t)Np * 2 * Np * sizeof(double);                             \
+      cudaError_t e = cudaFuncSetAttribute(stored_invert_kernel<Real, NN>,                \
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                           (int)sm);                                      \
+      if (e != cudaSuccess) return e;                                                     \
+      stored_invert_kernel<Real, NN><<<3 * K1, 128, sm, s>>>(K1, out, bad);               \
+    }                                                                                     \
     return cudaGetLastError();                                                            \
   }
   switch (N) {
@@ -255,10 +377,10 @@ cudaError_t launch_stored_ops(int N, int K1, int K0, const double* verts, const 
 }
 template cudaError_t launch_stored_ops<double>(int, int, int, const double*, const double*,
                                                const double*, const double*, const double*, int,
-                                               double*, cudaStream_t);
+                                               bool, double*, int*, cudaStream_t);
 template cudaError_t launch_stored_ops<float>(int, int, int, const double*, const double*,
                                               const double*, const double*, const double*, int,
-                                              float*, cudaStream_t);
+                                              bool, float*, int*, cudaStream_t);
 
 // ------------------------------------------------------------------ probes
 template <typename Real>

@@ -173,18 +173,21 @@ template <typename Real>
 cudaError_t launch_pml_samples(int Nq, int K1, int K0, const double* verts,
                                const double* rq /*[Nq][3]*/, const double* prof /*16*/,
                                Real* sig, Real* kap, bool element_constant, cudaStream_t s);
-// kappa = 1 stored-matrix scheme: the PML class with the per-element
-// operators, and their construction in double precision from the sigma
-// profile at the points of a high-degree rule (rh [Nh][3] reference points,
-// Ph [Np][Nh] = M^-1 V_h^T W_h, Vh [Nh][Np]; prof as for launch_pml_samples)
+// stored-matrix scheme: the PML class with the per-element operators (3 per
+// axis with kappa = 1: B, C, D; 5 otherwise: B, C, D, K = M^-1 M^{1/kappa},
+// A^-1 = (M^a)^-1 M), and their construction in double precision from the
+// sigma and kappa profiles at the points of a high-degree rule (rh [Nh][3]
+// reference points, Ph [Np][Nh] = M^-1 V_h^T W_h, Vh [Nh][Np]; prof as for
+// launch_pml_samples; *bad set if an a_u operator has a zero pivot)
 template <typename Real>
-cudaError_t launch_stage_stored(int N, const StageParams<Real>& P, int nb, cudaStream_t s);
+cudaError_t launch_stage_stored(int N, bool kappa, const StageParams<Real>& P, int nb,
+                                cudaStream_t s);
 template <typename Real>
 cudaError_t configure_stored_kernels(int N);
 template <typename Real>
 cudaError_t launch_stored_ops(int N, int K1, int K0, const double* verts, const double* prof,
                               const double* rh, const double* Ph, const double* Vh, int Nh,
-                              Real* out, cudaStream_t s);
+                              bool kappa, Real* out, int* bad, cudaStream_t s);
 // grouped launch (FP32 CUDA-core kernels): item i runs order code[i] / 4 with
 // class code[i] % 4 (0 non-PML, 1 PML, 2 PML with kappa); blocks
 // [first[i], first[i+1]) start on item i, and every block takes tiles from

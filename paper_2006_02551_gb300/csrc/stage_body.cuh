@@ -383,27 +383,32 @@ __device__ __forceinline__ void stage_body(const StageParams<Real>& P, unsigned 
   if (PML && STORED) {
   __syncthreads();   // RS complete
 
-  // ---- stored-matrix scheme (eqs. 10-13 with kappa = 1, so (M^a)^-1 M_k and
-  // M_k^-1 M^{1/kappa} are the identity): per axis u, 4 nodes per task,
-  //   rhs_E = r_E - B_u E_u - C_u P^E_u     rhs_P^E = E_u - D_u P^E_u
-  //   rhs_H = r_H - B_u H_u - C_u P^H_u     rhs_P^H = H_u - D_u P^H_u
-  // with B_u, C_u, D_u = M_k^-1 M_k^{b_u, c_u, d_u} read from global memory
+  // ---- stored-matrix scheme (eqs. 10-13): per axis u, 4 nodes per task,
+  //   r_E = Cbar(H)/eps - B_u E_u - C_u P^E_u     rhs_P^E = K_u E_u - D_u P^E_u
+  //   r_H = -Cbar(E)/mu - B_u H_u - C_u P^H_u     rhs_P^H = K_u H_u - D_u P^H_u
+  //   rhs_E = A_u^-1 r_E,  rhs_H = A_u^-1 r_H
+  // with B_u, C_u, D_u = M_k^-1 M_k^{b_u, c_u, d_u}, K_u = M_k^-1 M_k^{1/kappa_u}
+  // and A_u^-1 = (M_k^{a_u})^-1 M_k read from global memory; with kappa = 1,
+  // K_u and A_u^-1 are the identity and are not stored
+  constexpr int NBK = KAPPA ? 5 : 3;
   for (int task = tid; task < ne * 3 * NIQ; task += NT) {
     const int e = task / (3 * NIQ), r = task - e * 3 * NIQ, u = r / NIQ, iq = r - u * NIQ;
     const int eg = eg0 + e;
-    const Real* Bm = P.stored + ((int64_t)(ep0 + e) * 9 + u * 3) * Np * NpP + 4 * iq;
+    const Real* Bm = P.stored + ((int64_t)(ep0 + e) * 3 + u) * NBK * Np * NpP + 4 * iq;
     const Real* Cm = Bm + Np * NpP;
     const Real* Dm = Cm + Np * NpP;
-    Real aE[4], aH[4], dE[4], dH[4];
+    const Real* Km = Dm + Np * NpP;   // kappa != 1 only
+    Real aE[4], aH[4], dE[4], dH[4], kE[4], kH[4];
 #pragma unroll
-    for (int n = 0; n < 4; ++n) aE[n] = aH[n] = dE[n] = dH[n] = 0;
+    for (int n = 0; n < 4; ++n) aE[n] = aH[n] = dE[n] = dH[n] = kE[n] = kH[n] = 0;
     const Real* fe = F + e * Np * 12;
 #pragma unroll 5
     for (int j = 0; j < Np; ++j) {
-      Real bb[4], cc[4], dd[4];
+      Real bb[4], cc[4], dd[4], kk[4];
       ld4(Bm + j * NpP, bb);
       ld4(Cm + j * NpP, cc);
       ld4(Dm + j * NpP, dd);
+      if (KAPPA) ld4(Km + j * NpP, kk);
       const Real Ej = fe[j * 12 + u], Hj = fe[j * 12 + 3 + u];
       const Real PEj = fe[j * 12 + 6 + u], PHj = fe[j * 12 + 9 + u];
 #pragma unroll
@@ -412,6 +417,10 @@ __device__ __forceinline__ void stage_body(const StageParams<Real>& P, unsigned 
         aH[n] += bb[n] * Hj + cc[n] * PHj;
         dE[n] += dd[n] * PEj;
         dH[n] += dd[n] * PHj;
+        if (KAPPA) {
+          kE[n] += kk[n] * Ej;
+          kH[n] += kk[n] * Hj;
+        }
       }
     }
 #pragma unroll
@@ -420,13 +429,18 @@ __device__ __forceinline__ void stage_body(const StageParams<Real>& P, unsigned 
       if (i >= Np) continue;
       const Real* Fi = F + (e * Np + i) * 12;
       const Real rhs[4] = {RS[(e * NpP + i) * 6 + u] - aE[n], RS[(e * NpP + i) * 6 + 3 + u] - aH[n],
-                           Fi[u] - dE[n], Fi[3 + u] - dH[n]};
+                           (KAPPA ? kE[n] : Fi[u]) - dE[n], (KAPPA ? kH[n] : Fi[3 + u]) - dH[n]};
+      if (KAPPA) {   // r_E, r_H of node i, for A_u^-1 below
+        RS[(e * NpP + i) * 6 + u] = rhs[0];
+        RS[(e * NpP + i) * 6 + 3 + u] = rhs[1];
+      } else {
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {   // E_u, H_u
-        const int64_t gi = ((int64_t)eg * 6 + 3 * h + u) * Np + i;
-        const Real rr = rka * resq[gi] + rdt * rhs[h];
-        resq[gi] = rr;
-        qout[gi] = Fi[3 * h + u] + rkb * rr;
+        for (int h = 0; h < 2; ++h) {   // E_u, H_u
+          const int64_t gi = ((int64_t)eg * 6 + 3 * h + u) * Np + i;
+          const Real rr = rka * resq[gi] + rdt * rhs[h];
+          resq[gi] = rr;
+          qout[gi] = Fi[3 * h + u] + rkb * rr;
+        }
       }
 #pragma unroll
       for (int h = 0; h < 2; ++h) {   // P^E_u, P^H_u
@@ -437,6 +451,40 @@ __device__ __forceinline__ void stage_body(const StageParams<Real>& P, unsigned 
       }
     }
   }
+  if (KAPPA) {
+  __syncthreads();   // every r_E, r_H of the tile is in RS
+  for (int task = tid; task < ne * 3 * NIQ; task += NT) {
+    const int e = task / (3 * NIQ), r = task - e * 3 * NIQ, u = r / NIQ, iq = r - u * NIQ;
+    const int eg = eg0 + e;
+    const Real* Am = P.stored + (((int64_t)(ep0 + e) * 3 + u) * NBK + 4) * Np * NpP + 4 * iq;
+    Real sE[4] = {0, 0, 0, 0}, sH[4] = {0, 0, 0, 0};
+#pragma unroll 5
+    for (int j = 0; j < Np; ++j) {
+      Real aa[4];
+      ld4(Am + j * NpP, aa);
+      const Real rEj = RS[(e * NpP + j) * 6 + u], rHj = RS[(e * NpP + j) * 6 + 3 + u];
+#pragma unroll
+      for (int n = 0; n < 4; ++n) {
+        sE[n] += aa[n] * rEj;
+        sH[n] += aa[n] * rHj;
+      }
+    }
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+      const int i = 4 * iq + n;
+      if (i >= Np) continue;
+      const Real* Fi = F + (e * Np + i) * 12;
+      const Real rhs[2] = {sE[n], sH[n]};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {   // E_u, H_u
+        const int64_t gi = ((int64_t)eg * 6 + 3 * h + u) * Np + i;
+        const Real rr = rka * resq[gi] + rdt * rhs[h];
+        resq[gi] = rr;
+        qout[gi] = Fi[3 * h + u] + rkb * rr;
+      }
+    }
+  }
+  }  // KAPPA
   }  // stored
   if (PML && !STORED) {
   __syncthreads();   // FL is reused as TZ below
