@@ -201,8 +201,9 @@ __global__ void __launch_bounds__(RPlan<N, PML, BF>::THREADS, 1)
   const uint32_t sbase = saddr(smem);
   // mbarriers of slot s at mbar + 12 s: [0], [1] early buffer 0 / 1 landed,
   // [2] late registers landed, [3] sigma landed, [4] F/P operands ready,
-  // [5] flux ready, [6] V_q products done, [7] derivative and LIFT products
-  // done, [8] T/Z ready, [9] P_q done, [10] results staged, [11] final drain
+  // [5] flux ready, [6] V_q and derivative products done (the F and P
+  // operands are free), [7] derivative and LIFT products done, [8] T/Z
+  // ready, [9] P_q done, [10] results staged, [11] final drain
   enum { B_E0 = 0, B_LATE = 2, B_SIG = 3, B_FP = 4, B_FLUX = 5, B_V = 6, B_L = 7, B_TZ = 8,
          B_PQ = 9, B_OUT = 10, B_DRAIN = 11 };
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + PL::oMisc);
@@ -334,12 +335,14 @@ __global__ void __launch_bounds__(RPlan<N, PML, BF>::THREADS, 1)
         if (!mbar_wait_sleep(saddr(mb + B_FP), ph)) { mfail = true; break; }
         fence_after();
         issued = true;
-        if constexpr (PML) {   // V_q first: eq. 9 waits for these alone
+        if constexpr (PML) {   // V_q first, then the derivatives
           product(PL::cVF, PL::oAF, PL::SBF, PL::oBV, PL::SBF, NpK, idV);
           product(PL::cVP, PL::oAP, PL::SBF, PL::oBV, PL::SBF, NpK, idV);
-          mma_commit(saddr(mb + B_V));
         }
         product(PL::cD, PL::oAF, PL::SBF, PL::oBD, PL::SBF, NpK, idD);
+        // eq. 9 writes its T and Z rows over the F and P operands: it waits
+        // until every product reading them (V_q and the derivatives) is done
+        if constexpr (PML) mma_commit(saddr(mb + B_V));
         if (!mbar_wait_sleep(saddr(mb + B_FLUX), ph)) { mfail = true; break; }
         fence_after();
         product(PL::cL, PL::oAL, PL::SBL, PL::oBL, PL::SBL, NFK, idL);

@@ -149,3 +149,27 @@ def test_rule_checks_and_capacities():
     t.set_pml(PML3)
     assert status(lambda: t.set_quadrature(None)) == wadg.WADG_EUNSUPPORTED
     t.close()
+
+
+@pytest.mark.parametrize("N", [4, 5])
+def test_tensor_core_stage_is_repeatable(N):
+    """One TF32 stage on the row-owned PML kernel gives the same state bit for
+    bit every time (the kernel has no atomics: a difference is a race between
+    its roles), and matches the oracle."""
+    src = (Dipole(x=(0.1, -0.05, 0.2), dir=(0.0, 0.6, 0.8), t0=0.3, width=0.2),)
+    s, sim, mask = pair(N, "tf32", PML3, n_hex=4 if N < 5 else 3, sources=src)
+    st = round_states(random_states(sim.K, sim.Np, 1, 60 + N, mask), "tf32")
+    q0 = to_lib(st)
+    dt, t = 0.01, 0.27
+    outs = []
+    for _ in range(6):
+        s.set_state(q0, 0.0)
+        s.rk_stage(1, t, dt)
+        outs.append(s.get_state()[0])
+    s.close()
+    for o in outs[1:]:
+        assert np.array_equal(outs[0], o)
+    rhs = sim.rhs(st[0], t + lserk.RK_C[1] * dt, 0)
+    for f in st[0]:
+        st[0][f] = st[0][f] + lserk.RK_B[1] * dt * rhs[f]
+    assert increment_err(outs[0], st, q0, mask) < TOL["tf32"]
