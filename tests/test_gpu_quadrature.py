@@ -151,14 +151,16 @@ def test_rule_checks_and_capacities():
     t.close()
 
 
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
 @pytest.mark.parametrize("N", [4, 5])
-def test_tensor_core_stage_is_repeatable(N):
-    """One TF32 stage on the row-owned PML kernel gives the same state bit for
-    bit every time (the kernel has no atomics: a difference is a race between
-    its roles), and matches the oracle."""
+def test_tensor_core_stage_is_repeatable(N, prec):
+    """One stage on the tensor-core kernels (row-owned PML class, non-PML
+    class) gives the same state bit for bit every time (they have no
+    atomics: a difference is a race between their roles), and matches the
+    oracle."""
     src = (Dipole(x=(0.1, -0.05, 0.2), dir=(0.0, 0.6, 0.8), t0=0.3, width=0.2),)
-    s, sim, mask = pair(N, "tf32", PML3, n_hex=4 if N < 5 else 3, sources=src)
-    st = round_states(random_states(sim.K, sim.Np, 1, 60 + N, mask), "tf32")
+    s, sim, mask = pair(N, prec, PML3, n_hex=4 if N < 5 else 3, sources=src)
+    st = round_states(random_states(sim.K, sim.Np, 1, 60 + N, mask), prec)
     q0 = to_lib(st)
     dt, t = 0.01, 0.27
     outs = []
@@ -172,4 +174,4 @@ def test_tensor_core_stage_is_repeatable(N):
     rhs = sim.rhs(st[0], t + lserk.RK_C[1] * dt, 0)
     for f in st[0]:
         st[0][f] = st[0][f] + lserk.RK_B[1] * dt * rhs[f]
-    assert increment_err(outs[0], st, q0, mask) < TOL["tf32"]
+    assert increment_err(outs[0], st, q0, mask) < TOL[prec]

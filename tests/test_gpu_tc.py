@@ -130,3 +130,22 @@ def test_tc_blocks_off_16_byte_boundaries(precision, bound, drop):
     assert (K0 % 2 == 1) if drop == "interior" else (K1 % 2 == 1)
     err = increment_error(4, PML3, n_batch=2, precision=precision, mesh=(v, e))
     assert err < bound, err
+
+
+@pytest.mark.parametrize("precision", ["tf32", "bf16"])
+def test_tc_stage_is_repeatable_with_the_conical_rule(precision):
+    """With the (N+1)^3-point rule both classes run tc_stage_kernel: one stage
+    gives the same state bit for bit every time (no atomics in the kernel, so
+    a difference would be a race between its warp roles)."""
+    prof = PmlProfile(u0=0.75, L=0.25, sigma_max=20.0, p_sigma=3.0)
+    s, sim, mask = make_pair(4, 4, 0.15, 2, prof, precision,
+                             sources=[Dipole(x=(0.1, -0.05, 0.2), t0=0.3, width=0.2)])
+    q0 = to_lib(random_states(sim.K, sim.Np, 1, 71, mask))
+    outs = []
+    for _ in range(6):
+        s.set_state(q0, 0.0)
+        s.rk_stage(2, 0.3, 0.01)
+        outs.append(s.get_state()[0])
+    s.close()
+    for o in outs[1:]:
+        assert np.array_equal(outs[0], o)
