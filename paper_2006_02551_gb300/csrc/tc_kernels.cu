@@ -953,17 +953,17 @@ bool tc_supported(int N, bool kappa, bool bf16, int qc) {
   return bf16 || N <= 4 || qc == 1;
 }
 
+// The PML class with a compact rule runs tc_rows_kernel (tc_rows.cu); here:
+// the non-PML class (no quadrature) and the PML class with the (N+1)^3 rule.
 template <int N, bool BF>
 cudaError_t configure_tc_n() {
   cudaError_t e = cudaSuccess;
-  // the non-PML kernel has no quadrature; the PML kernels of both classes
   if constexpr (BF || N <= 4) {
     e = tc::configure_n<N, false, BF, 0>();
     if (e == cudaSuccess) e = tc::configure_n<N, true, BF, 0>();
   } else {
     e = tc::configure_n<N, false, BF, 1>();
   }
-  if (e == cudaSuccess) e = tc::configure_n<N, true, BF, 1>();
   return e;
 }
 
@@ -990,9 +990,8 @@ cudaError_t launch_tc_n(bool pml, const StageParams<float>& P, int nb, cudaStrea
     if (qc == 0) return tc::launch_n<N, true, BF, 0>(P, nb, s);
   } else {
     if (!pml) return tc::launch_n<N, false, BF, 1>(P, nb, s);
-    if (qc == 0) return cudaErrorInvalidValue;
   }
-  return tc::launch_n<N, true, BF, 1>(P, nb, s);
+  return cudaErrorInvalidValue;   // compact-rule PML classes run tc_rows_kernel
 }
 
 template <bool BF>
