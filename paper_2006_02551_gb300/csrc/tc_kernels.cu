@@ -115,7 +115,12 @@ struct Plan {
   // every warp can share the per-node work.  PML: the volume/LIFT columns go
   // to the field-operand buffers (free once the first products are done), the
   // P_q columns to the (t, z) buffer (free once P_q is done).
-  static constexpr uint32_t DV_BYTES = T * 24 * Np * 4;
+  // [T][6][4][Np] (component, d/dr d/ds d/dt LIFT, node) with an element
+  // stride DVE = Np (mod 32): a warp's stores (consecutive derivative-node
+  // pairs of one element) and its loads (consecutive element-node pairs) both
+  // fall on 32 distinct banks
+  static constexpr int DVE = 24 * Np + ((Np - 24 * Np) % 32 + 32) % 32;
+  static constexpr uint32_t DV_BYTES = T * DVE * 4;
   // (BF16 operand buffers are too small for the volume/LIFT dump: it gets its
   // own region)
   static constexpr bool DV_ALIAS = PML && !BF;
@@ -729,7 +734,8 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF, QC>::threads,
 
     // ---- derivative and LIFT columns -> shared memory.  Lane d Np + i holds
     // the d-th derivative at node i, lane i the LIFT term at node i.
-    float* DV = reinterpret_cast<float*>(smem + PL::oDV);   // [T][24][Np]
+    float* DV = reinterpret_cast<float*>(smem + PL::oDV);   // [T][DVE]
+    constexpr int DVE = PL::DVE;
     if constexpr (PL::VT == 1) {
       if (quad * 32 < 3 * Np) {
         const int L = quad * 32 + lane;
@@ -747,11 +753,11 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF, QC>::threads,
           if (e >= ne) continue;
           if (L < 3 * Np) {
 #pragma unroll
-            for (int c = 0; c < 6; ++c) DV[(e * 24 + d * 6 + c) * Np + i] = v[c];
+            for (int c = 0; c < 6; ++c) DV[e * DVE + (c * 4 + d) * Np + i] = v[c];
           }
           if (quad * 32 < Np && L < Np) {
 #pragma unroll
-            for (int c = 0; c < 6; ++c) DV[(e * 24 + 18 + c) * Np + i] = v[6 + c];
+            for (int c = 0; c < 6; ++c) DV[e * DVE + (c * 4 + 3) * Np + i] = v[6 + c];
           }
         }
       }
@@ -771,15 +777,15 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF, QC>::threads,
           if (e >= ne) continue;
           if (L < R0) {
 #pragma unroll
-            for (int c = 0; c < 6; ++c) DV[(e * 24 + d0 * 6 + c) * Np + i0] = v[c];
+            for (int c = 0; c < 6; ++c) DV[e * DVE + (c * 4 + d0) * Np + i0] = v[c];
           }
           if (quad * 32 < R1 && L < R1) {
 #pragma unroll
-            for (int c = 0; c < 6; ++c) DV[(e * 24 + d1 * 6 + c) * Np + i0] = w[c];
+            for (int c = 0; c < 6; ++c) DV[e * DVE + (c * 4 + d1) * Np + i0] = w[c];
           }
           if (quad * 32 < Np && L < Np) {
 #pragma unroll
-            for (int c = 0; c < 6; ++c) DV[(e * 24 + 18 + c) * Np + L] = l[c];
+            for (int c = 0; c < 6; ++c) DV[e * DVE + (c * 4 + 3) * Np + L] = l[c];
           }
         }
       }
@@ -792,19 +798,19 @@ __global__ void __launch_bounds__(TcWarps<N, PML, BF, QC>::threads,
     for (int task = tid; task < ne * Np; task += kTcThreads) {
       const int e = task / Np, i = task - e * Np;
       const int eg = eg0 + e;
-      const float* dv = DV + e * 24 * Np + i;
+      const float* dv = DV + e * DVE + i;
       const float* g = geoM + e * 12;
       float dx[6], dy[6], dz[6];
 #pragma unroll
       for (int c = 0; c < 6; ++c) {
-        const float r = dv[c * Np], sd_ = dv[(6 + c) * Np], t_ = dv[(12 + c) * Np];
+        const float r = dv[4 * c * Np], sd_ = dv[(4 * c + 1) * Np], t_ = dv[(4 * c + 2) * Np];
         dx[c] = g[0] * r + g[3] * sd_ + g[6] * t_;
         dy[c] = g[1] * r + g[4] * sd_ + g[7] * t_;
         dz[c] = g[2] * r + g[5] * sd_ + g[8] * t_;
       }
       float lf[6];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) lf[c] = dv[(18 + c) * Np];
+      for (int c = 0; c < 6; ++c) lf[c] = dv[(4 * c + 3) * Np];
       // Cbar(H) (E rows) and Cbar(E) (H rows)
       float CH[3], CE[3];
       CH[0] = dy[5] - dz[4] + lf[0];

@@ -84,6 +84,12 @@ struct RPlan {
   // K-adjacent core matrices 128 bytes apart, 8-row groups SB(K) apart
   __host__ __device__ static constexpr uint32_t SB(int K) { return (uint32_t)(K / CW) * 128u; }
   static constexpr uint32_t SBF = SB(NpK), SBT = SB(NqK), SBL = SB(NFK);
+  // the flux operand (A of LIFT) is written one face node (K) per lane.
+  // TF32: a 144-byte step between K-adjacent core matrices puts a warp's 32
+  // consecutive K on distinct banks (128 bytes puts them on four: 8-way
+  // conflicts).  BF16 keeps 128 (its lanes share words: 4-way), measured
+  // faster there.
+  static constexpr uint32_t LBA = BF ? 128 : 144, SBLA = (uint32_t)(NFK / CW) * LBA;
   // B operands (the reference operators, staged once per block)
   static constexpr uint32_t oBD = 0;
   static constexpr uint32_t oBL = oBD + (ND / 8) * SBF;
@@ -96,7 +102,7 @@ struct RPlan {
   // before its buffers so that its live rows are rows 64-127 (lanes 64-127)
   static constexpr uint32_t AFB = 8 * (PML && SBT > SBF ? SBT : SBF);
   static constexpr uint32_t oAF = 0, oAP = AFB, oAL = oAP + (PML ? AFB : 0);
-  static constexpr uint32_t ASLOT = oAL + 8 * SBL;
+  static constexpr uint32_t ASLOT = oAL + 8 * SBLA;
   // staging of a slot, each block copied as the 16-byte-aligned cover of its
   // data.  Early blocks (E,H, P, geometry: needed from the start of a tile)
   // have EB buffers, so the next tile's land while this one computes; late
@@ -136,7 +142,7 @@ struct RPlan {
     return oA + o + 16 * sb <= bytes &&
            (SLOTS == 1 || (oA + ASLOT + o >= 8 * sb && oA + ASLOT + o + 8 * sb <= bytes));
   }
-  static_assert(span_ok(oAF, SBF) && span_ok(oAL, SBL), "F / flux operand span");
+  static_assert(span_ok(oAF, SBF) && span_ok(oAL, SBLA), "F / flux operand span");
   static_assert(!PML || (span_ok(oAP, SBF) && span_ok(oAF, SBT) && span_ok(oAP, SBT)),
                 "P / T / Z operand span");
   static_assert(bytes <= 227 * 1024, "shared memory");
@@ -321,8 +327,9 @@ __global__ void __launch_bounds__(RPlan<N, PML, BF>::THREADS, 1)
       auto product = [&](uint32_t col, uint32_t aoff, uint32_t sba, uint32_t boff, uint32_t sbb,
                          int K, uint32_t id) {
         const uint32_t a0 = sbase + sA + aoff - (sl ? 8 * sba : 0);
+        const uint32_t lba = aoff == PL::oAL ? PL::LBA : 128u;
         for (int k = 0; k < K / KS; ++k)
-          mma(tcol + col, make_desc(a0 + 256 * k, 128, sba),
+          mma(tcol + col, make_desc(a0 + 2 * lba * k, lba, sba),
               make_desc(sbase + boff + 256 * k, 128, sbb), id, k > 0);
       };
       bool withhold = false;
@@ -345,7 +352,7 @@ __global__ void __launch_bounds__(RPlan<N, PML, BF>::THREADS, 1)
         if constexpr (PML) mma_commit(saddr(mb + B_V));
         if (!mbar_wait_sleep(saddr(mb + B_FLUX), ph)) { mfail = true; break; }
         fence_after();
-        product(PL::cL, PL::oAL, PL::SBL, PL::oBL, PL::SBL, NFK, idL);
+        product(PL::cL, PL::oAL, PL::SBLA, PL::oBL, PL::SBL, NFK, idL);
         if (!withhold) mma_commit(saddr(mb + B_L));   // derivatives and LIFT
         withhold = false;
         if constexpr (PML) {
@@ -617,6 +624,14 @@ __global__ void __launch_bounds__(RPlan<N, PML, BF>::THREADS, 1)
         const float ie0 = 1.f / (float)P.eps0;
         const int u = c % 3;
         const int ee = e < ne ? e : 0;
+        // the lanes of one element need the axes in the orders (u, v, w) =
+        // (0,1,2), (1,2,0), (2,0,1).  Where rows 0 and 2 (2 NqP floats
+        // apart) fall on the same banks, the TF32 kernel has every lane read
+        // the rows in axis order (one address per element and load) and
+        // permute them in registers; otherwise, and in the BF16 kernel
+        // (measured faster there), each lane reads its own order.
+        constexpr bool ordered = !BF && (2 * NqP) % 32 == 0;
+        const float* s0_p = sg + (ee * 3) * NqP;
         const float* su_p = sg + (ee * 3 + u) * NqP;
         const float* sv_p = sg + (ee * 3 + (u == 2 ? 0 : u + 1)) * NqP;
         const float* sw_p = sg + (ee * 3 + (u == 0 ? 2 : u - 1)) * NqP;
@@ -637,9 +652,18 @@ __global__ void __launch_bounds__(RPlan<N, PML, BF>::THREADS, 1)
             const int qb = qq + 4 * j4;
             sgu[j4] = sgv[j4] = sgw[j4] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (qb < NqP && qb < q1) {
-              sgu[j4] = *reinterpret_cast<const float4*>(su_p + qb);
-              sgv[j4] = *reinterpret_cast<const float4*>(sv_p + qb);
-              sgw[j4] = *reinterpret_cast<const float4*>(sw_p + qb);
+              if constexpr (!ordered) {
+                sgu[j4] = *reinterpret_cast<const float4*>(su_p + qb);
+                sgv[j4] = *reinterpret_cast<const float4*>(sv_p + qb);
+                sgw[j4] = *reinterpret_cast<const float4*>(sw_p + qb);
+              } else {
+                const float4 a0 = *reinterpret_cast<const float4*>(s0_p + qb);
+                const float4 a1 = *reinterpret_cast<const float4*>(s0_p + NqP + qb);
+                const float4 a2 = *reinterpret_cast<const float4*>(s0_p + 2 * NqP + qb);
+                sgu[j4] = u == 0 ? a0 : (u == 1 ? a1 : a2);
+                sgv[j4] = u == 0 ? a1 : (u == 1 ? a2 : a0);
+                sgw[j4] = u == 0 ? a2 : (u == 1 ? a0 : a1);
+              }
             }
           }
           tmem_wait_ld();
@@ -900,7 +924,7 @@ __global__ void __launch_bounds__(RPlan<N, PML, BF>::THREADS, 1)
         fo[3] = sE * (YP * cEx + al * (nx * ndH - dHx));
         fo[4] = sE * (YP * cEy + al * (ny * ndH - dHy));
         fo[5] = sE * (YP * cEz + al * (nz * ndH - dHz));
-        const uint32_t o = cofs<BF>(8 * e, fm, PL::SBL, 128);
+        const uint32_t o = cofs<BF>(8 * e, fm, PL::SBLA, PL::LBA);
 #pragma unroll
         for (int cc = 0; cc < 6; ++cc) {
           unsigned char* dst = smem + sA + PL::oAL + o + 16 * cc;
