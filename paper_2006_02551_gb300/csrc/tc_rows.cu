@@ -84,12 +84,11 @@ struct RPlan {
   // K-adjacent core matrices 128 bytes apart, 8-row groups SB(K) apart
   __host__ __device__ static constexpr uint32_t SB(int K) { return (uint32_t)(K / CW) * 128u; }
   static constexpr uint32_t SBF = SB(NpK), SBT = SB(NqK), SBL = SB(NFK);
-  // the flux operand (A of LIFT) is written one face node (K) per lane.
-  // TF32: a 144-byte step between K-adjacent core matrices puts a warp's 32
-  // consecutive K on distinct banks (128 bytes puts them on four: 8-way
-  // conflicts).  BF16 keeps 128 (its lanes share words: 4-way), measured
-  // faster there.
-  static constexpr uint32_t LBA = BF ? 128 : 144, SBLA = (uint32_t)(NFK / CW) * LBA;
+  // the flux operand (A of LIFT) is written one face node (K) per lane: a
+  // 144-byte step between K-adjacent core matrices puts a warp's 32
+  // consecutive K on distinct banks (128 bytes puts them on four banks: 8-way
+  // conflicts for TF32, 4-way for BF16, whose lanes share words)
+  static constexpr uint32_t LBA = 144, SBLA = (uint32_t)(NFK / CW) * LBA;
   // B operands (the reference operators, staged once per block)
   static constexpr uint32_t oBD = 0;
   static constexpr uint32_t oBL = oBD + (ND / 8) * SBF;
@@ -104,7 +103,8 @@ struct RPlan {
   static constexpr uint32_t oAF = 0, oAP = AFB, oAL = oAP + (PML ? AFB : 0);
   static constexpr uint32_t ASLOT = oAL + 8 * SBLA;
   // staging of a slot, each block copied as the 16-byte-aligned cover of its
-  // data.  Early blocks (E,H, P, geometry: needed from the start of a tile)
+  // data.  Early blocks (E,H, P, geometry, neighbour tables: needed from the
+  // start of a tile, the tables by the flux warps one tile earlier)
   // have EB buffers, so the next tile's land while this one computes; late
   // blocks (the Runge-Kutta registers, needed at the update, and the sigma
   // samples, needed at eq. 9) have one, refilled once this tile is past them.
@@ -115,7 +115,10 @@ struct RPlan {
   static constexpr uint32_t GMAT = ((T * 12 + 15) & ~15) + 16;
   static constexpr uint32_t oEQ = 0, oEP = FB, oEFN = oEP + (PML ? FB : 0);
   static constexpr uint32_t oEMET = oEFN + GFN, oEMAT = oEMET + GMET;
-  static constexpr uint32_t EBUF = (oEMAT + GMAT + 127) & ~127u;   // one early buffer
+  // the tile's face neighbours (int) and orientation codes (byte), [T][4]
+  static constexpr uint32_t GNB = ((T * 16 + 15) & ~15) + 16, GCD = ((T * 4 + 15) & ~15) + 16;
+  static constexpr uint32_t oENB = oEMAT + GMAT, oECD = oENB + GNB;
+  static constexpr uint32_t EBUF = (oECD + GCD + 127) & ~127u;   // one early buffer
   static constexpr uint32_t oLR = 0, oLRP = FB, oLSG = oLRP + (PML ? FB : 0);
   static constexpr uint32_t LBUF = (oLSG + SGB + 127) & ~127u;     // the late buffer
   __host__ __device__ static constexpr uint32_t misc_bytes() {
@@ -391,19 +394,23 @@ __global__ void __launch_bounds__(RPlan<N, PML, BF>::THREADS, 1)
       auto early_in = [&](int tile, int it) {
         const Tile t = tile_at(tile);
         const uint32_t eb = ebuf(sl, it), fb = t.ne * 6 * Np * 4;
-        const void* src[5] = {P.qin + t.oq, PML ? (const void*)(P.p + t.op) : nullptr,
-                              P.fnrm + t.eg0 * 16, P.geof + t.eg0 * 9, P.mat + t.eg0 * 3};
-        const uint32_t len[5] = {fb, fb, (uint32_t)t.ne * 64, (uint32_t)t.ne * 36,
-                                 (uint32_t)t.ne * 12};
-        const uint32_t dst[5] = {eb + PL::oEQ, eb + PL::oEP, eb + PL::oEFN, eb + PL::oEMET,
-                                 eb + PL::oEMAT};
+        const void* src[7] = {P.qin + t.oq, PML ? (const void*)(P.p + t.op) : nullptr,
+                              P.fnrm + t.eg0 * 16, P.geof + t.eg0 * 9, P.mat + t.eg0 * 3,
+                              P.nbr + t.eg0 * 4, P.code + t.eg0 * 4};
+        const uint32_t len[7] = {fb, fb, (uint32_t)t.ne * 64, (uint32_t)t.ne * 36,
+                                 (uint32_t)t.ne * 12, (uint32_t)t.ne * 16, (uint32_t)t.ne * 4};
+        const uint32_t dst[7] = {eb + PL::oEQ, eb + PL::oEP, eb + PL::oEFN, eb + PL::oEMET,
+                                 eb + PL::oEMAT, eb + PL::oENB, eb + PL::oECD};
+        // the neighbour tables travel with the early blocks when there are two
+        // early buffers (the flux warps read them a tile ahead)
+        constexpr int NBK = EB == 2 ? 7 : 5;
         if constexpr (PML) {
-          copy_in(src, len, dst, 5, mb + B_E0 + (EB == 2 ? (it & 1) : 0));
+          copy_in(src, len, dst, NBK, mb + B_E0 + (EB == 2 ? (it & 1) : 0));
         } else {
-          const void* s2[4] = {src[0], src[2], src[3], src[4]};
-          const uint32_t l2[4] = {len[0], len[2], len[3], len[4]};
-          const uint32_t d2[4] = {dst[0], dst[2], dst[3], dst[4]};
-          copy_in(s2, l2, d2, 4, mb + B_E0 + (EB == 2 ? (it & 1) : 0));
+          const void* s2[6] = {src[0], src[2], src[3], src[4], src[5], src[6]};
+          const uint32_t l2[6] = {len[0], len[2], len[3], len[4], len[5], len[6]};
+          const uint32_t d2[6] = {dst[0], dst[2], dst[3], dst[4], dst[5], dst[6]};
+          copy_in(s2, l2, d2, NBK - 1, mb + B_E0 + (EB == 2 ? (it & 1) : 0));
         }
       };
       auto late_in = [&](int tile) {
@@ -843,11 +850,21 @@ __global__ void __launch_bounds__(RPlan<N, PML, BF>::THREADS, 1)
     const int ft = fidx * 32 + lane;   // flux thread of the slot
     constexpr int NFT = 32 * PL::FLUXW;
     constexpr int FT = (T * NF + NFT - 1) / NFT;    // tasks per thread
-    // neighbour traces of a tile (global memory), loaded one tile ahead
+    // neighbour traces of a tile (global memory), loaded one tile ahead; the
+    // tile's neighbour and code tables come from its early buffer
     float Ep[FT][3], Hp[FT][3], ZPv[FT];
-    auto load_nbr = [&](int tile) {
+    // (with two early buffers the tile's neighbour tables come from its
+    // early buffer, iteration itn: false if that wait gave up)
+    auto load_nbr = [&](int tile, int itn) -> bool {
       const Tile t = tile_at(tile);
       const float* qin = P.qin + (int64_t)t.b * P.strideQ;
+      const int* nbs = P.nbr + t.eg0 * 4;
+      const unsigned char* cds = P.code + t.eg0 * 4;
+      if constexpr (EB == 2) {
+        if (!mbar_wait_sleep(saddr(mb + B_E0 + (itn & 1)), eparity(itn))) return false;
+        nbs = reinterpret_cast<const int*>(staged(ebuf(sl, itn) + PL::oENB, nbs));
+        cds = staged(ebuf(sl, itn) + PL::oECD, cds);
+      }
 #pragma unroll
       for (int u = 0; u < FT; ++u) {
         const int task = ft + u * NFT;
@@ -856,9 +873,9 @@ __global__ void __launch_bounds__(RPlan<N, PML, BF>::THREADS, 1)
         for (int cc = 0; cc < 3; ++cc) { Ep[u][cc] = 0.f; Hp[u][cc] = 0.f; }
         if (task < t.ne * NF) {
           const int e = task / NF, fm = task - e * NF, f = fm / Nfp, m = fm - f * Nfp;
-          const int nb = P.nbr[(t.eg0 + e) * 4 + f];
+          const int nb = nbs[e * 4 + f];
           if (nb >= 0) {
-            const int code = P.code[(t.eg0 + e) * 4 + f];
+            const int code = cds[e * 4 + f];
             if (!WADG_INDEX_OK(nb < P.strideQ / (6 * Np) && code < 24, P.err)) continue;
             const int np2 = fperm[(f * 24 + code) * Nfp + m];
             if (!WADG_INDEX_OK(np2 < Np, P.err)) continue;
@@ -869,9 +886,10 @@ __global__ void __launch_bounds__(RPlan<N, PML, BF>::THREADS, 1)
           }
         }
       }
+      return true;
     };
     const int first = blockIdx.x * SLOTS + sl;
-    if (first < ntiles) load_nbr(first);
+    if (first < ntiles && !load_nbr(first, 0)) failed = true;
     int it = 0;
     for (int tile = first; tile < ntiles && !failed; tile += nworkers, ++it) {
       const uint32_t ph = it & 1;
@@ -936,7 +954,10 @@ __global__ void __launch_bounds__(RPlan<N, PML, BF>::THREADS, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(saddr(mb + B_FLUX));
       // the next tile's neighbour traces load while this tile's epilogue runs
-      if (tile + nworkers < ntiles) load_nbr(tile + nworkers);
+      if (tile + nworkers < ntiles && !load_nbr(tile + nworkers, it + 1)) {
+        failed = true;
+        break;
+      }
     }
     if (failed && lane == 0) atomicExch(P.err, 1);
   }
